@@ -1,0 +1,241 @@
+/*
+ * fvgb.h - C ABI of the GB300 finite-volume library (libfvgb.so).
+ *
+ * The library implements, on one GPU, the per-step hot path of the cell-centred
+ * finite-volume method of Manapy (Kissami & Ratnani, arXiv 2203.00925):
+ * least-squares cell gradients (Algorithm "grad"), least-squares vertex
+ * interpolation (Algorithm "ls"), upwind convective fluxes (eq. 15 with psi = 0),
+ * diamond-scheme diffusive fluxes (eq. "diamond"), the face-to-cell gather of eq. 4
+ * with the explicit update of eq. 6, and the same face operator used matrix-free as
+ * the Poisson operator of eq. 7 / eq. "laplace" inside an iterative solve. The
+ * streamer step couples them as in eq. 10.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every call returns an fvgb_status; nothing throws or aborts across the ABI.
+ *   fvgb_last_error() gives a message for the last failing call of the thread.
+ * - Device arrays (suffix _dev) are owned by the caller, live on the device the mesh
+ *   was uploaded on, and are laid out in the mesh's INTERNAL cell order (cells are
+ *   reordered for locality at upload). fvgb_mesh_cell_perm / fvgb_permute convert
+ *   to and from the caller's order. Vector fields are structure-of-arrays:
+ *   [dim][n] with component stride n.
+ * - The element type of per-cell transport arrays ("real") is double for a mesh
+ *   uploaded with FVGB_FP64 and float for FVGB_FP32 / FVGB_MIXED. Poisson data
+ *   (right-hand side f, potential phi) are always double.
+ * - stream is a cudaStream_t (NULL = the legacy default stream). Calls are
+ *   stream-ordered; a call returns once its work is enqueued, except where it says
+ *   that it synchronises the stream.
+ * - A mesh handle is not thread-safe: use one handle from one host thread and one
+ *   stream at a time.
+ * - Sizes are int64_t; element indices inside the library are int32 (meshes up to
+ *   2^31 - 1 cells, faces and neighbour entries).
+ */
+#ifndef FVGB_H
+#define FVGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fvgb_mesh_s* fvgb_mesh;
+
+typedef enum {
+  FVGB_OK = 0,
+  FVGB_EINVAL = 1,        /* bad argument (null pointer, size, index, option) */
+  FVGB_EMESH = 2,         /* malformed mesh: bad index, non-positive cell, non-manifold
+                             face, boundary list not matching the mesh boundary,
+                             boundary tag without a condition */
+  FVGB_ENOMEM = 3,        /* device or host allocation failed */
+  FVGB_ECUDA = 4,         /* a CUDA runtime call failed */
+  FVGB_ENOCONV = 5,       /* iterative solve stopped at its iteration limit */
+  FVGB_ENONFINITE = 6,    /* NaN or Inf met in a solve */
+  FVGB_ETIMEOUT = 7,      /* a bounded device-side wait gave up */
+  FVGB_EUNSUPPORTED = 8   /* valid request this build does not implement */
+} fvgb_status;
+
+typedef enum { FVGB_FP64 = 0, FVGB_FP32 = 1, FVGB_MIXED = 2 } fvgb_prec;
+
+/* Boundary-condition kinds (Section 4, boundary conditions; annex):
+ *  WALL      - no flux of any kind through the face;
+ *  DIRICHLET - ghost value g = value at the face centroid (also a least-squares
+ *              point of the cells around the face, and the vertex value of every
+ *              vertex of the face);
+ *  NEUMANN   - homogeneous Neumann: the ghost copies the interior cell (its value
+ *              and velocity), no diffusive flux. */
+typedef enum { FVGB_BC_WALL = 0, FVGB_BC_DIRICHLET = 1, FVGB_BC_NEUMANN = 2 } fvgb_bc_kind;
+
+typedef struct {
+  int32_t tag;      /* boundary tag as given in bface_tag */
+  int32_t kind;     /* fvgb_bc_kind */
+  double value;     /* Dirichlet value (ignored otherwise) */
+} fvgb_bc;
+
+/* One set of boundary conditions: one entry per tag present on the boundary. */
+typedef struct {
+  int32_t n_bc;
+  const fvgb_bc* bc;
+} fvgb_bcset;
+
+/* Upload a simplicial mesh and precompute its geometry (Section 2.1: cell centres of
+ * gravity, measures mu_i, face area vectors |sigma| n, least-squares matrices and
+ * weights of Algorithms "grad" and "ls", diamond coefficients of eq. "diamond").
+ *
+ *  dim         2 (triangles) or 3 (tetrahedra)
+ *  xyz         host, [n_vert][dim] row-major, FP64 coordinates
+ *  cell_vert   host, [n_cell][dim+1] vertex ids, positively oriented
+ *              (det[x1-x0, x2-x0(, x3-x0)] > 0)
+ *  bface_vert  host, [n_bface][dim] vertex ids of every boundary face, any order
+ *  bface_tag   host, [n_bface] positive tags
+ *  bcsets      n_bcset >= 1 boundary-condition sets; operators name one by index
+ *  reorder     0 keep the caller's order, 2 Morton (Z-order) order of cell centres
+ *  prec        fvgb_prec of the transport arrays (see conventions)
+ *  stream      stream for the uploads; the call synchronises it before returning
+ *  out         receives the handle (owned by the caller, release with fvgb_mesh_free)
+ * Errors: FVGB_EINVAL, FVGB_EMESH (nothing allocated), FVGB_ENOMEM, FVGB_ECUDA. */
+fvgb_status fvgb_mesh_upload(int32_t dim, int64_t n_vert, const double* xyz,
+                             int64_t n_cell, const int32_t* cell_vert,
+                             int64_t n_bface, const int32_t* bface_vert,
+                             const int32_t* bface_tag, int32_t n_bcset,
+                             const fvgb_bcset* bcsets, int32_t reorder, int32_t prec,
+                             void* stream, fvgb_mesh* out);
+
+/* Release every device and host allocation of the mesh (synchronises the device). */
+fvgb_status fvgb_mesh_free(fvgb_mesh m);
+
+/* Mesh sizes: cells, faces, vertices and node-neighbour entries (sum over cells of
+ * the number of cells sharing a vertex with the cell). Any pointer may be NULL. */
+fvgb_status fvgb_mesh_info(fvgb_mesh m, int64_t* n_cell, int64_t* n_face,
+                           int64_t* n_vert, int64_t* n_nbr);
+
+/* perm_host[internal index] = caller's cell index (host array of n_cell int32). */
+fvgb_status fvgb_mesh_cell_perm(fvgb_mesh m, int32_t* perm_host);
+
+/* perm_host[internal index] = caller's vertex index (host array of n_vert int32); vertex
+ * arrays such as the output of fvgb_vertex_values are in this internal order. */
+fvgb_status fvgb_mesh_vert_perm(fvgb_mesh m, int32_t* perm_host);
+
+/* Reorder n_comp per-cell arrays of elem_bytes-sized elements (4 or 8) between the
+ * caller's order and the internal order. src_dev and dst_dev must not overlap.
+ * to_internal = 1: dst[i] = src[perm[i]]; 0: dst[perm[i]] = src[i]. */
+fvgb_status fvgb_permute(fvgb_mesh m, const void* src_dev, void* dst_dev, int32_t n_comp,
+                         int32_t elem_bytes, int32_t to_internal, void* stream);
+
+/* Least-squares cell gradient of Algorithm "grad" (Section 2.1): for every cell,
+ * grad u_i = M_i^{-1} sum_j d_ij (u_j - u_i) over the set of cells sharing a vertex
+ * with cell i, plus the face centroids of Dirichlet faces of set bcset that share a
+ * vertex with it (value g), d = x_j - x_i, M_i = sum d d^T.
+ *  u_dev     [n_cell] real      grad_dev [dim][n_cell] real */
+fvgb_status fvgb_gradient(fvgb_mesh m, int32_t bcset, const void* u_dev, void* grad_dev,
+                          void* stream);
+
+/* Least-squares vertex values of Algorithm "ls": u_A = sum_c alpha_{A,c} u_c over the
+ * cells around vertex A (linear least-squares fit; mean when the fit is degenerate);
+ * vertices on a Dirichlet face of set bcset take g.
+ *  u_dev [n_cell] real   uv_dev [n_vert] real (internal vertex order) */
+fvgb_status fvgb_vertex_values(fvgb_mesh m, int32_t bcset, const void* u_dev, void* uv_dev,
+                               void* stream);
+
+/* Transport coefficients of eq. 1: velocity (a per-cell field [dim][n_cell] real when
+ * vel_dev is not NULL, else the constant vel_const), diffusivity D >= 0, source
+ * S_i ([n_cell] real or NULL), boundary conditions bcset. recon must be 0 (first-order
+ * upwind, eq. 15 with psi = 0). */
+typedef struct {
+  const void* vel_dev;
+  double vel_const[3];
+  double diff;
+  const void* src_dev;
+  int32_t bcset;
+  int32_t recon;
+} fvgb_tcoef;
+
+/* Residual of eq. 4: res_i = (sum over faces entering i - leaving i of F_f) / mu_i + S_i,
+ * F_f = (V_f . S_f) u_up - D grad u_f . S_f, V_f = (V_L + V_R)/2,
+ * u_up = u_L if V_f . S_f >= 0 else u_R (eq. 15).
+ *  u_dev, res_dev: [n_cell] real, distinct buffers. */
+fvgb_status fvgb_fv_residual(fvgb_mesh m, const fvgb_tcoef* tc, const void* u_dev,
+                             void* res_dev, void* stream);
+
+/* nsteps explicit time steps of eq. 6 in place on u_dev: per step
+ * u^(k) = u^n + stage_alpha[k] dt Res(u^(k-1)), k = 0..nstage-1, u^{n+1} = u^(last).
+ * nstage = 1 with stage_alpha = {1} (or stage_alpha = NULL) is explicit Euler;
+ * {0.5, 0.5, 1} is the paper's three-stage scheme. nstage <= 8. When tc->src_dev is
+ * set it is held fixed over the steps. */
+fvgb_status fvgb_fv_step(fvgb_mesh m, const fvgb_tcoef* tc, void* u_dev, double dt,
+                         int32_t nsteps, const double* stage_alpha, int32_t nstage,
+                         void* stream);
+
+/* Poisson operator of eq. 7 / eq. "laplace" in FP64, integrated form with positive
+ * sign: y = A x = -mu Lap_h(x) with homogeneous boundary values of set bcset
+ * (Dirichlet faces and vertices take 0; Neumann and wall faces carry no flux).
+ *  x_dev, y_dev: [n_cell] double, distinct. */
+fvgb_status fvgb_poisson_apply(fvgb_mesh m, int32_t bcset, const double* x_dev,
+                               double* y_dev, void* stream);
+
+/* Right-hand side of the Poisson system for Lap phi = f: b = -mu f + mu Lap_h(0; g).
+ *  f_dev, b_dev: [n_cell] double. f_dev may be NULL (f = 0). */
+fvgb_status fvgb_poisson_rhs(fvgb_mesh m, int32_t bcset, const double* f_dev, double* b_dev,
+                             void* stream);
+
+typedef struct {
+  double rtol;          /* stop when ||b - A phi||_2 <= rtol ||b||_2 (FP64) */
+  double inner_rtol;    /* inner CG reduces its residual by this factor (e.g. 0.1) */
+  int32_t maxit_inner;  /* per inner solve */
+  int32_t maxit_outer;  /* outer FP64 refinement steps */
+  int32_t prec;         /* inner CG arithmetic: FVGB_FP64 or FVGB_FP32 (mixed) */
+} fvgb_solve_opts;
+
+typedef struct {
+  int32_t outer_its;
+  int32_t inner_its_total;
+  double rel_res;       /* final ||b - A phi|| / ||b|| in FP64 */
+  double bnorm;         /* ||b||_2 */
+} fvgb_solve_info;
+
+/* Solve Lap phi = f (eq. 1.1 discretised by eq. 7) for phi on set bcset.
+ * Outer loop in FP64 (defect correction / iterative refinement on the full diamond
+ * operator A): r = b - A phi, stop when ||r|| <= rtol ||b||; otherwise an inner
+ * conjugate-gradient solve of A_T delta = r on the symmetric positive definite
+ * two-point part A_T of A (coefficient |S_f|^2 / ((x_R - x_L) . S_f) per face), in
+ * opts->prec arithmetic with FP64 dot products, then phi += delta.
+ *  f_dev    [n_cell] double (NULL = 0)
+ *  phi_dev  [n_cell] double, in: initial guess, out: solution
+ *  info     host, may be NULL
+ * The call synchronises the stream once per outer step (to read the FP64 residual).
+ * Returns FVGB_ENOCONV (with info filled and phi the last iterate) if rtol is not met
+ * within maxit_outer steps, FVGB_ENONFINITE on NaN/Inf, FVGB_ETIMEOUT if a grid-wide
+ * barrier of the persistent CG kernel gave up. */
+fvgb_status fvgb_poisson_solve(fvgb_mesh m, int32_t bcset, const double* f_dev,
+                               double* phi_dev, const fvgb_solve_opts* opts,
+                               fvgb_solve_info* info, void* stream);
+
+/* Electron drift-diffusion + Poisson step of eq. 10 with the synthetic coefficients:
+ * v = -mu E, alpha = A exp(-B/|E|) (0 at |E| = 0), S = alpha |v| n_e, constant D_e,
+ * Lap phi = -(e/eps0)(n_i - n_e). Per step: solve for phi (warm start from phi_dev),
+ * E = -grad phi (least-squares gradient, set bcset_phi), then
+ * n_e += dt Res(n_e) (set bcset_ne, velocity field v, diffusivity D_e, source S) and
+ * n_i += dt S. */
+typedef struct {
+  double mu, A, B, De;
+  double dt;
+  int32_t bcset_ne;
+  int32_t bcset_phi;
+  fvgb_solve_opts solve;
+} fvgb_streamer_params;
+
+/* ne_dev, ni_dev: [n_cell] real; phi_dev: [n_cell] double (in: guess, out: last
+ * potential); E_dev: [dim][n_cell] real or NULL (out: last field).
+ * info: host, [nsteps] entries or NULL. Returns the first failing solve's status. */
+fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void* ne_dev,
+                               void* ni_dev, double* phi_dev, void* E_dev, int32_t nsteps,
+                               fvgb_solve_info* info, void* stream);
+
+/* Message of the last failing call in this thread ("" if none). */
+const char* fvgb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FVGB_H */

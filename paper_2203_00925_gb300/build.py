@@ -1,0 +1,70 @@
+"""Build libfvgb.so in-tree for sm_103a (GB300).
+
+The CUDA translation units and the host mesh preprocessing compile in parallel into
+``_build/`` and link into ``libfvgb.so`` next to this file. Run ``python -m
+paper_2203_00925_gb300.build`` or call :func:`build`.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libfvgb.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+CU_SOURCES = ["ops.cu", "solver.cu", "api.cu"]
+CPP_SOURCES = ["mesh_host.cpp"]
+
+
+def _nvcc():
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libfvgb")
+
+
+def _run(cmd):
+    p = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+    if p.returncode != 0:
+        raise RuntimeError("build step failed:\n" + " ".join(cmd) + "\n" + p.stdout)
+    return p.stdout
+
+
+def build(verbose: bool = False, force: bool = False) -> str:
+    """Compile every source (in parallel) and link libfvgb.so; returns its path."""
+    nvcc = _nvcc()
+    os.makedirs(BUILD, exist_ok=True)
+    srcs = [os.path.join(CSRC, s) for s in CU_SOURCES + CPP_SOURCES]
+    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
+    headers.append(os.path.join(os.path.dirname(HERE), "include", "fvgb.h"))
+    newest_in = max(os.path.getmtime(p) for p in srcs + headers + [__file__])
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest_in:
+        return LIB
+    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp"]
+    jobs = []
+    for s in CU_SOURCES:
+        obj = os.path.join(BUILD, s + ".o")
+        jobs.append(([nvcc, *ARCH, *common, "-Xptxas", "-v" if verbose else "-O3", "-c",
+                      os.path.join(CSRC, s), "-o", obj], obj))
+    for s in CPP_SOURCES:
+        obj = os.path.join(BUILD, s + ".o")
+        jobs.append(([nvcc, *common, "-x", "c++", "-c", os.path.join(CSRC, s), "-o", obj], obj))
+    with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        outs = list(ex.map(lambda j: _run(j[0]), jobs))
+    if verbose:
+        for o in outs:
+            sys.stdout.write(o)
+    tmp = LIB + ".tmp"
+    _run([nvcc, *ARCH, "-shared", "-o", tmp, *[o for _, o in jobs], "-Xcompiler", "-fopenmp"])
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv))

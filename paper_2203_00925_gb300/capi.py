@@ -1,0 +1,256 @@
+"""ctypes binding of libfvgb (include/fvgb.h): the same entry points under the same
+names, argument marshalling only. Device arrays are passed as torch CUDA tensors (or
+raw integer addresses); every computation runs in the library's kernels.
+
+Importing this module loads ``libfvgb.so`` from the package directory and raises if
+it is missing: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfvgb.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -m paper_2203_00925_gb300.build` "
+        "(the library has no CPU fallback)")
+lib = C.CDLL(LIB_PATH)
+
+FVGB_OK, FVGB_EINVAL, FVGB_EMESH, FVGB_ENOMEM, FVGB_ECUDA = 0, 1, 2, 3, 4
+FVGB_ENOCONV, FVGB_ENONFINITE, FVGB_ETIMEOUT, FVGB_EUNSUPPORTED = 5, 6, 7, 8
+FVGB_FP64, FVGB_FP32, FVGB_MIXED = 0, 1, 2
+FVGB_BC_WALL, FVGB_BC_DIRICHLET, FVGB_BC_NEUMANN = 0, 1, 2
+STATUS_NAMES = {0: "FVGB_OK", 1: "FVGB_EINVAL", 2: "FVGB_EMESH", 3: "FVGB_ENOMEM",
+                4: "FVGB_ECUDA", 5: "FVGB_ENOCONV", 6: "FVGB_ENONFINITE",
+                7: "FVGB_ETIMEOUT", 8: "FVGB_EUNSUPPORTED"}
+
+EXPORTED = [
+    "fvgb_mesh_upload", "fvgb_mesh_free", "fvgb_mesh_info", "fvgb_mesh_cell_perm",
+    "fvgb_mesh_vert_perm",
+    "fvgb_permute", "fvgb_gradient", "fvgb_vertex_values", "fvgb_fv_residual",
+    "fvgb_fv_step", "fvgb_poisson_apply", "fvgb_poisson_rhs", "fvgb_poisson_solve",
+    "fvgb_streamer_step", "fvgb_last_error",
+]
+
+
+class fvgb_bc(C.Structure):
+    _fields_ = [("tag", C.c_int32), ("kind", C.c_int32), ("value", C.c_double)]
+
+
+class fvgb_bcset(C.Structure):
+    _fields_ = [("n_bc", C.c_int32), ("bc", C.POINTER(fvgb_bc))]
+
+
+class fvgb_tcoef(C.Structure):
+    _fields_ = [("vel_dev", C.c_void_p), ("vel_const", C.c_double * 3), ("diff", C.c_double),
+                ("src_dev", C.c_void_p), ("bcset", C.c_int32), ("recon", C.c_int32)]
+
+
+class fvgb_solve_opts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("inner_rtol", C.c_double), ("maxit_inner", C.c_int32),
+                ("maxit_outer", C.c_int32), ("prec", C.c_int32)]
+
+
+class fvgb_solve_info(C.Structure):
+    _fields_ = [("outer_its", C.c_int32), ("inner_its_total", C.c_int32),
+                ("rel_res", C.c_double), ("bnorm", C.c_double)]
+
+    def as_dict(self):
+        return {"outer_its": self.outer_its, "inner_its_total": self.inner_its_total,
+                "rel_res": self.rel_res, "bnorm": self.bnorm}
+
+
+class fvgb_streamer_params(C.Structure):
+    _fields_ = [("mu", C.c_double), ("A", C.c_double), ("B", C.c_double), ("De", C.c_double),
+                ("dt", C.c_double), ("bcset_ne", C.c_int32), ("bcset_phi", C.c_int32),
+                ("solve", fvgb_solve_opts)]
+
+
+_vp, _i32, _i64, _d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+_sig = {
+    "fvgb_mesh_upload": (C.c_int, [_i32, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _i32,
+                                   C.POINTER(fvgb_bcset), _i32, _i32, _vp, C.POINTER(_vp)]),
+    "fvgb_mesh_free": (C.c_int, [_vp]),
+    "fvgb_mesh_info": (C.c_int, [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64),
+                                 C.POINTER(_i64)]),
+    "fvgb_mesh_cell_perm": (C.c_int, [_vp, _vp]),
+    "fvgb_mesh_vert_perm": (C.c_int, [_vp, _vp]),
+    "fvgb_permute": (C.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp]),
+    "fvgb_gradient": (C.c_int, [_vp, _i32, _vp, _vp, _vp]),
+    "fvgb_vertex_values": (C.c_int, [_vp, _i32, _vp, _vp, _vp]),
+    "fvgb_fv_residual": (C.c_int, [_vp, C.POINTER(fvgb_tcoef), _vp, _vp, _vp]),
+    "fvgb_fv_step": (C.c_int, [_vp, C.POINTER(fvgb_tcoef), _vp, _d, _i32, _vp, _i32, _vp]),
+    "fvgb_poisson_apply": (C.c_int, [_vp, _i32, _vp, _vp, _vp]),
+    "fvgb_poisson_rhs": (C.c_int, [_vp, _i32, _vp, _vp, _vp]),
+    "fvgb_poisson_solve": (C.c_int, [_vp, _i32, _vp, _vp, C.POINTER(fvgb_solve_opts),
+                                     C.POINTER(fvgb_solve_info), _vp]),
+    "fvgb_streamer_step": (C.c_int, [_vp, C.POINTER(fvgb_streamer_params), _vp, _vp, _vp, _vp,
+                                     _i32, C.POINTER(fvgb_solve_info), _vp]),
+    "fvgb_last_error": (C.c_char_p, []),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class FvgbError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = lib.fvgb_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+def _check(status, where):
+    if status != FVGB_OK:
+        raise FvgbError(status, where)
+    return status
+
+
+def ptr(x):
+    """Device (or host) address of a tensor / numpy array / integer / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---- entry points under their C names -----------------------------------------------------
+def fvgb_mesh_upload(dim, xyz, cell_vert, bface_vert, bface_tag, bcsets, reorder=2,
+                     prec=FVGB_FP64, stream=None):
+    """Upload a mesh; ``bcsets`` is a list of {tag: (kind, value)} dicts. Host arrays are
+    numpy (FP64 coordinates, int32 indices). Returns the opaque handle (an integer)."""
+    import numpy as np
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    cell_vert = np.ascontiguousarray(cell_vert, dtype=np.int32)
+    bface_vert = np.ascontiguousarray(bface_vert, dtype=np.int32)
+    bface_tag = np.ascontiguousarray(bface_tag, dtype=np.int32)
+    sets = (fvgb_bcset * len(bcsets))()
+    keep = []
+    for k, bc in enumerate(bcsets):
+        arr = (fvgb_bc * len(bc))()
+        for j, (tag, (kind, value)) in enumerate(sorted(bc.items())):
+            arr[j] = fvgb_bc(int(tag), int(kind), float(value))
+        keep.append(arr)
+        sets[k] = fvgb_bcset(len(bc), C.cast(arr, C.POINTER(fvgb_bc)))
+    out = _vp()
+    _check(lib.fvgb_mesh_upload(dim, xyz.shape[0], ptr(xyz), cell_vert.shape[0], ptr(cell_vert),
+                                bface_vert.shape[0], ptr(bface_vert), ptr(bface_tag), len(bcsets),
+                                sets, reorder, prec, stream_handle(stream), C.byref(out)),
+           "fvgb_mesh_upload")
+    return out.value
+
+
+def fvgb_mesh_free(m):
+    return _check(lib.fvgb_mesh_free(m), "fvgb_mesh_free")
+
+
+def fvgb_mesh_info(m):
+    n = [_i64() for _ in range(4)]
+    _check(lib.fvgb_mesh_info(m, *[C.byref(x) for x in n]), "fvgb_mesh_info")
+    return {"n_cell": n[0].value, "n_face": n[1].value, "n_vert": n[2].value, "n_nbr": n[3].value}
+
+
+def fvgb_mesh_cell_perm(m, n_cell):
+    import numpy as np
+    perm = np.empty(n_cell, dtype=np.int32)
+    _check(lib.fvgb_mesh_cell_perm(m, ptr(perm)), "fvgb_mesh_cell_perm")
+    return perm
+
+
+def fvgb_mesh_vert_perm(m, n_vert):
+    import numpy as np
+    perm = np.empty(n_vert, dtype=np.int32)
+    _check(lib.fvgb_mesh_vert_perm(m, ptr(perm)), "fvgb_mesh_vert_perm")
+    return perm
+
+
+def fvgb_permute(m, src, dst, n_comp, elem_bytes, to_internal, stream=None):
+    return _check(lib.fvgb_permute(m, ptr(src), ptr(dst), n_comp, elem_bytes, int(to_internal),
+                                   stream_handle(stream)), "fvgb_permute")
+
+
+def fvgb_gradient(m, bcset, u, grad, stream=None):
+    return _check(lib.fvgb_gradient(m, bcset, ptr(u), ptr(grad), stream_handle(stream)), "fvgb_gradient")
+
+
+def fvgb_vertex_values(m, bcset, u, uv, stream=None):
+    return _check(lib.fvgb_vertex_values(m, bcset, ptr(u), ptr(uv), stream_handle(stream)),
+                  "fvgb_vertex_values")
+
+
+def tcoef(vel=None, vel_const=(0.0, 0.0, 0.0), diff=0.0, src=None, bcset=0, recon=0):
+    vc = (C.c_double * 3)(*[float(v) for v in list(vel_const) + [0.0] * (3 - len(vel_const))])
+    return fvgb_tcoef(ptr(vel), vc, float(diff), ptr(src), int(bcset), int(recon))
+
+
+def fvgb_fv_residual(m, tc, u, res, stream=None):
+    return _check(lib.fvgb_fv_residual(m, C.byref(tc), ptr(u), ptr(res), stream_handle(stream)),
+                  "fvgb_fv_residual")
+
+
+def fvgb_fv_step(m, tc, u, dt, nsteps, stage_alpha=None, stream=None):
+    arr = None
+    n = 0
+    if stage_alpha is not None:
+        n = len(stage_alpha)
+        arr = (C.c_double * n)(*stage_alpha)
+    return _check(lib.fvgb_fv_step(m, C.byref(tc), ptr(u), float(dt), int(nsteps),
+                                   C.cast(arr, _vp) if arr is not None else None, n,
+                                   stream_handle(stream)), "fvgb_fv_step")
+
+
+def fvgb_poisson_apply(m, bcset, x, y, stream=None):
+    return _check(lib.fvgb_poisson_apply(m, bcset, ptr(x), ptr(y), stream_handle(stream)),
+                  "fvgb_poisson_apply")
+
+
+def fvgb_poisson_rhs(m, bcset, f, b, stream=None):
+    return _check(lib.fvgb_poisson_rhs(m, bcset, ptr(f), ptr(b), stream_handle(stream)),
+                  "fvgb_poisson_rhs")
+
+
+def solve_opts(rtol=1e-8, inner_rtol=0.1, maxit_inner=20000, maxit_outer=200, prec=FVGB_FP64):
+    return fvgb_solve_opts(float(rtol), float(inner_rtol), int(maxit_inner), int(maxit_outer), int(prec))
+
+
+def fvgb_poisson_solve(m, bcset, f, phi, opts, stream=None, check=True):
+    info = fvgb_solve_info()
+    st = lib.fvgb_poisson_solve(m, bcset, ptr(f), ptr(phi), C.byref(opts), C.byref(info),
+                                stream_handle(stream))
+    if check:
+        _check(st, "fvgb_poisson_solve")
+    return st, info
+
+
+def streamer_params(mu=0.0382, A=4332.0, B=2.0e5, De=0.1, dt=1e-9, bcset_ne=0, bcset_phi=1,
+                    solve=None):
+    return fvgb_streamer_params(mu, A, B, De, dt, bcset_ne, bcset_phi,
+                                solve if solve is not None else solve_opts())
+
+
+def fvgb_streamer_step(m, params, ne, ni, phi, E, nsteps, stream=None):
+    infos = (fvgb_solve_info * max(nsteps, 1))()
+    _check(lib.fvgb_streamer_step(m, C.byref(params), ptr(ne), ptr(ni), ptr(phi), ptr(E),
+                                  int(nsteps), infos, stream_handle(stream)), "fvgb_streamer_step")
+    return [infos[i].as_dict() for i in range(nsteps)]
+
+
+def fvgb_last_error():
+    return lib.fvgb_last_error().decode(errors="replace")

@@ -1,0 +1,163 @@
+// Internal declarations shared by the CUDA translation units of libfvgb.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fvgb.h"
+
+namespace fvgb {
+
+// Sliced-ELL (SELL-32) list: rows grouped in slices of 32 consecutive rows; slice s
+// stores its entries column-major from ptr[s], width ptr[s+1]-ptr[s] over 32, so one
+// warp reads 128 contiguous bytes per column.
+struct Sell {
+  int64_t* ptr = nullptr;   // [n_slice + 1] element offsets
+  int32_t* idx = nullptr;   // padded entries
+};
+
+template <typename T>
+struct BCDev {
+  int8_t* bkind = nullptr;   // [Fb]
+  T* bval = nullptr;         // [Fb]
+  T* minv = nullptr;         // [nsym][N]
+  int32_t* gptr = nullptr;   // [N+1]
+  int32_t* gface = nullptr;  // ghost faces
+  T* vdir = nullptr;         // [V] NaN = not Dirichlet
+  int32_t* at_nbr = nullptr; // [nv][N]
+  T* at_coef = nullptr;      // [nv][N]
+  T* at_diag = nullptr;      // [N]
+};
+
+// Real-valued geometry in one precision.
+template <typename T>
+struct GeoDev {
+  T* cen = nullptr;      // [d][N] (high part in FP32)
+  T* cen_lo = nullptr;   // [d][N] low part (FP32 only): cen_true = cen + cen_lo
+  T* vol = nullptr;      // [N]
+  T* inv_vol = nullptr;  // [N]
+  T* S = nullptr;        // [d][F]
+  T* xf = nullptr;       // [d][F]
+  T* xf_lo = nullptr;    // [d][F] (FP32 only)
+  T* coef = nullptr;     // [d][F]
+  T* valpha = nullptr;   // SELL-padded weights, aligned with vsell.idx
+  std::vector<BCDev<T>> bc;
+};
+
+struct TopoDev {
+  int dim = 0;
+  int64_t N = 0, V = 0, F = 0, Fi = 0, n_nbr = 0;
+  int32_t* fL = nullptr;
+  int32_t* fR = nullptr;
+  int32_t* fvert = nullptr;      // [d][F]
+  int32_t* cell_face = nullptr;  // [d+1][N]
+  int32_t* cell_perm = nullptr;  // [N] internal -> caller
+  Sell nsell;                    // node neighbours of each cell (padded with the cell)
+  Sell vsell;                    // cells around each vertex (padded, weight 0)
+};
+
+// Scratch of one precision.
+template <typename T>
+struct Work {
+  T* flux = nullptr;   // [F]
+  T* uv = nullptr;     // [V]
+  T* stage = nullptr;  // [N] Runge-Kutta stage value
+  T* tmp = nullptr;    // [N]
+  T* vel = nullptr;    // [d][N]
+  T* src = nullptr;    // [N]
+  T* grad = nullptr;   // [d][N]
+  T* cg_r = nullptr;   // [N]
+  T* cg_p = nullptr;
+  T* cg_q = nullptr;
+  T* cg_x = nullptr;
+};
+
+struct Barrier {
+  unsigned int count;
+  unsigned int gen;
+  int status;      // 0 ok, 1 timeout
+  int pad;
+};
+
+}  // namespace fvgb
+
+struct fvgb_mesh_s {
+  int device = 0;
+  int num_sms = 0;
+  fvgb_prec prec = FVGB_FP64;
+  fvgb::TopoDev topo;
+  fvgb::GeoDev<double> g64;
+  fvgb::GeoDev<float> g32;
+  fvgb::Work<double> w64;
+  fvgb::Work<float> w32;
+  std::vector<int32_t> cell_perm_host;
+  std::vector<int32_t> vert_perm_host;
+  double* d_scal = nullptr;             // reduction partials / results (FP64)
+  double* h_scal = nullptr;             // pinned host mirror
+  double* dphi_tmp = nullptr;           // [N] FP64 scratch (residual r)
+  double* dphi_tmp2 = nullptr;          // [N] FP64 scratch (rhs b)
+  double* dzero = nullptr;              // [N] zeros
+  fvgb::Barrier* barrier = nullptr;
+  int* d_cg_info = nullptr;             // [4] iterations, status
+  int cg_grid64 = 0, cg_grid32 = 0;     // cooperative grid sizes
+  std::vector<void*> allocs;
+};
+
+namespace fvgb {
+
+template <typename T>
+inline GeoDev<T>& geo_of(fvgb_mesh_s* m);
+template <>
+inline GeoDev<double>& geo_of<double>(fvgb_mesh_s* m) { return m->g64; }
+template <>
+inline GeoDev<float>& geo_of<float>(fvgb_mesh_s* m) { return m->g32; }
+template <typename T>
+inline Work<T>& work_of(fvgb_mesh_s* m);
+template <>
+inline Work<double>& work_of<double>(fvgb_mesh_s* m) { return m->w64; }
+template <>
+inline Work<float>& work_of<float>(fvgb_mesh_s* m) { return m->w32; }
+
+constexpr int kRedBlocks = 1024;   // fixed grid of the deterministic reductions
+
+void set_error(const std::string& msg);
+fvgb_status cuda_status(cudaError_t e, const char* what);
+
+// ops.cu -------------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_gradient(fvgb_mesh_s* m, int bcset, const T* u, T* grad, cudaStream_t s);
+template <typename T>
+cudaError_t launch_vertex(fvgb_mesh_s* m, int bcset, const T* u, T* uv, bool homog, cudaStream_t s);
+// face kernel: conv (use velocity), D (diffusion coefficient; -1 gives F = q)
+template <typename T>
+cudaError_t launch_face(fvgb_mesh_s* m, int bcset, const T* u, const T* uv, const T* vel,
+                        const double* vel_const, bool conv, double D, bool homog, T* flux,
+                        cudaStream_t s);
+enum UpdateMode { kResidual = 0, kStep = 1, kPoissonApply = 2, kPoissonResidual = 3, kPoissonRhs = 4 };
+template <typename T>
+cudaError_t launch_update(fvgb_mesh_s* m, int mode, const T* flux, const T* src, const T* base,
+                          double adt, const T* aux, T* out, T* out2, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cell_physics(fvgb_mesh_s* m, const T* grad, const T* ne, double mu, double A,
+                                double B, T* E, T* vel, T* src, cudaStream_t s);
+cudaError_t launch_poisson_source(fvgb_mesh_s* m, const void* ne, const void* ni, bool fp32,
+                                  double* f, cudaStream_t s);
+cudaError_t launch_sumsq(fvgb_mesh_s* m, const double* x, int64_t n, double* out, cudaStream_t s);
+cudaError_t launch_axpy_d(const double* x, double a, double* y, int64_t n, cudaStream_t s);
+cudaError_t launch_add_to_double(const void* x, bool fp32, double* y, int64_t n, cudaStream_t s);
+cudaError_t launch_convert(const double* x, float* y, int64_t n, cudaStream_t s);
+cudaError_t launch_convert_back(const float* x, double* y, int64_t n, cudaStream_t s);
+cudaError_t launch_permute(const void* src, void* dst, const int32_t* perm, int64_t n, int ncomp,
+                           int elem_bytes, bool to_internal, cudaStream_t s);
+cudaError_t launch_nonfinite_check(const double* x, int64_t n, int* flag, cudaStream_t s);
+
+// solver.cu ----------------------------------------------------------------------------
+int cg_grid_size(fvgb_mesh_s* m, bool fp32);
+template <typename T>
+cudaError_t launch_cg(fvgb_mesh_s* m, int bcset, const double* rhs, double rtol, int maxit,
+                      cudaStream_t s);
+
+}  // namespace fvgb

@@ -1,0 +1,440 @@
+// Finite-volume kernels of the hot path (Section 2.1 of arXiv 2203.00925):
+// least-squares cell gradient (Algorithm "grad"), least-squares vertex values
+// (Algorithm "ls"), face fluxes (eq. 4, eq. 15 with psi = 0, eq. "diamond"), the
+// face-to-cell gather with the explicit update (eq. 4, eq. 6), and the same face
+// operator in the integrated Poisson form (eq. 7 / eq. "laplace").
+//
+// Every kernel is a gather: each output element is written by one thread that sums
+// its inputs in a fixed order, so results are bitwise reproducible run to run (no
+// floating-point atomics).
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "internal.h"
+
+namespace fvgb {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(int64_t n, int threads = kThreads) {
+  return (unsigned)((n + threads - 1) / threads);
+}
+
+// Difference of two centre coordinates. FP32 keeps each coordinate as a (high, low)
+// pair of floats so that the difference of nearby centres keeps FP32 relative accuracy.
+__device__ __forceinline__ double cdiff(const double* a, const double*, int64_t ia,
+                                        const double* b, const double*, int64_t ib) {
+  return a[ia] - b[ib];
+}
+__device__ __forceinline__ float cdiff(const float* a, const float* alo, int64_t ia,
+                                       const float* b, const float* blo, int64_t ib) {
+  return (a[ia] - b[ib]) + (alo[ia] - blo[ib]);
+}
+
+// ---- Algorithm "grad": grad u_i = M_i^{-1} sum_j d_ij (u_j - u_i) ------------------------
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads)
+k_gradient(int64_t N, int64_t F, int64_t Fi, const int64_t* __restrict__ sptr,
+           const int32_t* __restrict__ sidx, const T* __restrict__ cen,
+           const T* __restrict__ cen_lo, const T* __restrict__ xf, const T* __restrict__ xf_lo,
+           const T* __restrict__ u, const T* __restrict__ minv, const int32_t* __restrict__ gptr,
+           const int32_t* __restrict__ gface, const T* __restrict__ bval, T* __restrict__ grad) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t sl = i >> 5;
+  const int lane = (int)(i & 31);
+  const int64_t b0 = sptr[sl], b1 = sptr[sl + 1];
+  const T ui = u[i];
+  T J[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) J[a] = T(0);
+  for (int64_t p = b0 + lane; p < b1; p += 32) {
+    const int32_t j = __ldg(sidx + p);
+    const T du = u[j] - ui;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const T dx = cdiff(cen + a * N, cen_lo ? cen_lo + a * N : nullptr, j, cen + a * N,
+                         cen_lo ? cen_lo + a * N : nullptr, i);
+      J[a] += dx * du;
+    }
+  }
+  for (int32_t t = gptr[i]; t < gptr[i + 1]; ++t) {
+    const int32_t f = gface[t];
+    const T du = bval[f - Fi] - ui;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const T dx = cdiff(xf + a * F, xf_lo ? xf_lo + a * F : nullptr, f, cen + a * N,
+                         cen_lo ? cen_lo + a * N : nullptr, i);
+      J[a] += dx * du;
+    }
+  }
+  if constexpr (D == 3) {
+    const T m0 = minv[i], m1 = minv[N + i], m2 = minv[2 * N + i], m3 = minv[3 * N + i],
+            m4 = minv[4 * N + i], m5 = minv[5 * N + i];
+    grad[i] = m0 * J[0] + m1 * J[1] + m2 * J[2];
+    grad[N + i] = m1 * J[0] + m3 * J[1] + m4 * J[2];
+    grad[2 * N + i] = m2 * J[0] + m4 * J[1] + m5 * J[2];
+  } else {
+    const T m0 = minv[i], m1 = minv[N + i], m2 = minv[2 * N + i];
+    grad[i] = m0 * J[0] + m1 * J[1];
+    grad[N + i] = m1 * J[0] + m2 * J[1];
+  }
+}
+
+// ---- Algorithm "ls": u_A = sum_c alpha_{A,c} u_c; Dirichlet vertices take g --------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_vertex(int64_t V, const int64_t* __restrict__ sptr, const int32_t* __restrict__ sidx,
+         const T* __restrict__ alpha, const T* __restrict__ u, const T* __restrict__ vdir,
+         int homog, T* __restrict__ uv) {
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const int64_t sl = v >> 5;
+  const int lane = (int)(v & 31);
+  const int64_t b0 = sptr[sl], b1 = sptr[sl + 1];
+  T s = T(0);
+  for (int64_t p = b0 + lane; p < b1; p += 32) s += alpha[p] * u[__ldg(sidx + p)];
+  const T g = vdir[v];
+  if (g == g) s = homog ? T(0) : g;  // Dirichlet vertex (vdir is NaN elsewhere)
+  uv[v] = s;
+}
+
+// ---- face flux: F = (V_f . S_f) u_up - D grad u_f . S_f (eq. 4, eq. 15, eq. "diamond") ----
+template <typename T, int D, bool CONV, bool VFIELD>
+__global__ void __launch_bounds__(kThreads)
+k_face(int64_t F, int64_t Fi, int64_t N, const int32_t* __restrict__ fL,
+       const int32_t* __restrict__ fR, const int32_t* __restrict__ fvert,
+       const T* __restrict__ S, const T* __restrict__ coef, const T* __restrict__ u,
+       const T* __restrict__ uv, const T* __restrict__ vel, T vc0, T vc1, T vc2, T Dcoef,
+       const int8_t* __restrict__ bkind, const T* __restrict__ bval, int homog,
+       T* __restrict__ flux) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  const int32_t L = fL[f];
+  const T uL = u[L];
+  int kind = 3;  // interior
+  int32_t R = -1;
+  T uR;
+  if (f < Fi) {
+    R = fR[f];
+    uR = u[R];
+  } else {
+    kind = bkind[f - Fi];
+    if (kind == FVGB_BC_WALL) { flux[f] = T(0); return; }
+    uR = kind == FVGB_BC_DIRICHLET ? (homog ? T(0) : bval[f - Fi]) : uL;
+  }
+  T Ff = T(0);
+  if (CONV) {
+    T vf[3];
+    if (VFIELD) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const T vl = vel[a * N + L];
+        const T vr = R >= 0 ? vel[a * N + R] : vl;
+        vf[a] = T(0.5) * (vl + vr);
+      }
+    } else {
+      vf[0] = vc0; vf[1] = vc1; vf[2] = vc2;
+    }
+    T vn = vf[0] * S[f] + vf[1] * S[F + f];
+    if (D == 3) vn += vf[2] * S[2 * F + f];
+    Ff = vn * (vn >= T(0) ? uL : uR);
+  }
+  if (Dcoef != T(0) && (kind == 3 || kind == FVGB_BC_DIRICHLET)) {
+    T q;
+    if constexpr (D == 3) {
+      const T ua = uv[fvert[f]], ub = uv[fvert[F + f]], uc = uv[fvert[2 * F + f]];
+      q = coef[f] * (uR - uL) + coef[F + f] * (ua - uc) + coef[2 * F + f] * (ub - uc);
+    } else {
+      const T ua = uv[fvert[f]], ub = uv[fvert[F + f]];
+      q = coef[f] * (uR - uL) + coef[F + f] * (ub - ua);
+    }
+    Ff -= Dcoef * q;
+  }
+  flux[f] = Ff;
+}
+
+// ---- gather of the face fluxes of every cell (eq. 4) and what follows from it ---------------
+template <typename T, int NV, int MODE>
+__global__ void __launch_bounds__(kThreads)
+k_update(int64_t N, const int32_t* __restrict__ cell_face, const T* __restrict__ flux,
+         const T* __restrict__ inv_vol, const T* __restrict__ vol, const T* __restrict__ src,
+         const T* base, T adt, const T* __restrict__ aux, T* out, T* out2) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  T acc = T(0);  // sum over faces entering i minus faces leaving i
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    const int32_t e = cell_face[k * N + i];
+    acc += e >= 0 ? -flux[e] : flux[~e];
+  }
+  if constexpr (MODE == kResidual) {
+    out[i] = acc * inv_vol[i] + (src ? src[i] : T(0));
+  } else if constexpr (MODE == kStep) {
+    const T s = src ? src[i] : T(0);
+    const T r = acc * inv_vol[i] + s;
+    out[i] = base[i] + adt * r;
+    if (out2) out2[i] += adt * s;
+  } else if constexpr (MODE == kPoissonApply) {
+    out[i] = acc;                       // A x = -mu Lap_h x
+  } else if constexpr (MODE == kPoissonResidual) {
+    out[i] = aux[i] - acc;              // r = b - A x
+  } else {
+    out[i] = -vol[i] * (aux ? aux[i] : T(0)) - acc;   // b = -mu f + mu Lap_h(0; g)
+  }
+}
+
+// ---- streamer cell physics (eq. 10 with v = -mu E, alpha = A exp(-B/|E|)) --------------------
+template <typename T, int D>
+__global__ void __launch_bounds__(kThreads)
+k_cell_physics(int64_t N, const T* __restrict__ grad, const T* __restrict__ ne, T mu, T A, T B,
+               T* __restrict__ E, T* __restrict__ vel, T* __restrict__ src) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  T e[3], en2 = T(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) { e[a] = -grad[a * N + i]; en2 += e[a] * e[a]; }
+  const T en = sqrt(en2);
+  const T alpha = en > T(0) ? A * exp(-B / en) : T(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    vel[a * N + i] = -mu * e[a];
+    if (E) E[a * N + i] = e[a];
+  }
+  src[i] = alpha * mu * en * ne[i];
+}
+
+template <typename T>
+__global__ void k_poisson_source(int64_t N, const T* __restrict__ ne, const T* __restrict__ ni,
+                                 double* __restrict__ f) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  constexpr double kEoverEps0 = 1.602176634e-19 / 8.8541878128e-12;
+  f[i] = -kEoverEps0 * ((double)ni[i] - (double)ne[i]);
+}
+
+// ---- deterministic FP64 reduction: fixed grid, fixed per-thread order, fixed tree ----------
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  return s;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256) k_sumsq_partial(const double* __restrict__ x, int64_t n,
+                                                       double* __restrict__ part) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += x[i] * x[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_sum_final(const double* __restrict__ part, int n,
+                                                    double* __restrict__ out) {
+  __shared__ double sh[32];
+  double s = threadIdx.x < n ? part[threadIdx.x] : 0.0;
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[0] = s;
+}
+
+__global__ void k_axpy_d(const double* __restrict__ x, double a, double* __restrict__ y, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] += a * x[i];
+}
+
+template <typename T>
+__global__ void k_add_to_double(const T* __restrict__ x, double* __restrict__ y, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] += (double)x[i];
+}
+
+__global__ void k_convert(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+
+__global__ void k_convert_back(const float* __restrict__ x, double* __restrict__ y, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (double)x[i];
+}
+
+template <typename E>
+__global__ void k_permute(const E* __restrict__ src, E* __restrict__ dst,
+                          const int32_t* __restrict__ perm, int64_t n, int ncomp, int to_internal) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t p = perm[i];
+  for (int c = 0; c < ncomp; ++c) {
+    if (to_internal) dst[c * n + i] = src[c * n + p];
+    else dst[c * n + p] = src[c * n + i];
+  }
+}
+
+__global__ void k_nonfinite(const double* __restrict__ x, int64_t n, int* flag) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n && !isfinite(x[i])) *flag = 1;  // benign race: every writer stores 1
+}
+
+}  // namespace
+
+// ---- launchers -------------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_gradient(fvgb_mesh_s* m, int bcset, const T* u, T* grad, cudaStream_t s) {
+  const TopoDev& t = m->topo;
+  GeoDev<T>& g = geo_of<T>(m);
+  const BCDev<T>& b = g.bc[bcset];
+  if (t.dim == 3)
+    k_gradient<T, 3><<<grid_for(t.N), kThreads, 0, s>>>(t.N, t.F, t.Fi, t.nsell.ptr, t.nsell.idx,
+        g.cen, g.cen_lo, g.xf, g.xf_lo, u, b.minv, b.gptr, b.gface, b.bval, grad);
+  else
+    k_gradient<T, 2><<<grid_for(t.N), kThreads, 0, s>>>(t.N, t.F, t.Fi, t.nsell.ptr, t.nsell.idx,
+        g.cen, g.cen_lo, g.xf, g.xf_lo, u, b.minv, b.gptr, b.gface, b.bval, grad);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_vertex(fvgb_mesh_s* m, int bcset, const T* u, T* uv, bool homog, cudaStream_t s) {
+  const TopoDev& t = m->topo;
+  GeoDev<T>& g = geo_of<T>(m);
+  k_vertex<T><<<grid_for(t.V), kThreads, 0, s>>>(t.V, t.vsell.ptr, t.vsell.idx, g.valpha, u,
+                                                  g.bc[bcset].vdir, homog ? 1 : 0, uv);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_face(fvgb_mesh_s* m, int bcset, const T* u, const T* uv, const T* vel,
+                        const double* vc, bool conv, double D, bool homog, T* flux, cudaStream_t s) {
+  const TopoDev& t = m->topo;
+  GeoDev<T>& g = geo_of<T>(m);
+  const BCDev<T>& b = g.bc[bcset];
+  const T v0 = vc ? (T)vc[0] : T(0), v1 = vc ? (T)vc[1] : T(0), v2 = vc ? (T)vc[2] : T(0);
+  const unsigned gr = grid_for(t.F);
+#define FVGB_FACE(DD, CV, VF)                                                                   \
+  k_face<T, DD, CV, VF><<<gr, kThreads, 0, s>>>(t.F, t.Fi, t.N, t.fL, t.fR, t.fvert, g.S, g.coef, \
+                                                u, uv, vel, v0, v1, v2, (T)D, b.bkind, b.bval,  \
+                                                homog ? 1 : 0, flux)
+  if (t.dim == 3) {
+    if (!conv) FVGB_FACE(3, false, false);
+    else if (vel) FVGB_FACE(3, true, true);
+    else FVGB_FACE(3, true, false);
+  } else {
+    if (!conv) FVGB_FACE(2, false, false);
+    else if (vel) FVGB_FACE(2, true, true);
+    else FVGB_FACE(2, true, false);
+  }
+#undef FVGB_FACE
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_update(fvgb_mesh_s* m, int mode, const T* flux, const T* src, const T* base,
+                          double adt, const T* aux, T* out, T* out2, cudaStream_t s) {
+  const TopoDev& t = m->topo;
+  GeoDev<T>& g = geo_of<T>(m);
+  const unsigned gr = grid_for(t.N);
+#define FVGB_UPD(NV, MD)                                                                 \
+  k_update<T, NV, MD><<<gr, kThreads, 0, s>>>(t.N, t.cell_face, flux, g.inv_vol, g.vol, src, \
+                                              base, (T)adt, aux, out, out2)
+#define FVGB_UPD_MODES(NV)                                       \
+  switch (mode) {                                                \
+    case kResidual: FVGB_UPD(NV, kResidual); break;              \
+    case kStep: FVGB_UPD(NV, kStep); break;                      \
+    case kPoissonApply: FVGB_UPD(NV, kPoissonApply); break;      \
+    case kPoissonResidual: FVGB_UPD(NV, kPoissonResidual); break; \
+    default: FVGB_UPD(NV, kPoissonRhs); break;                   \
+  }
+  if (t.dim == 3) { FVGB_UPD_MODES(4) } else { FVGB_UPD_MODES(3) }
+#undef FVGB_UPD_MODES
+#undef FVGB_UPD
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cell_physics(fvgb_mesh_s* m, const T* grad, const T* ne, double mu, double A,
+                                double B, T* E, T* vel, T* src, cudaStream_t s) {
+  const TopoDev& t = m->topo;
+  if (t.dim == 3)
+    k_cell_physics<T, 3><<<grid_for(t.N), kThreads, 0, s>>>(t.N, grad, ne, (T)mu, (T)A, (T)B, E, vel, src);
+  else
+    k_cell_physics<T, 2><<<grid_for(t.N), kThreads, 0, s>>>(t.N, grad, ne, (T)mu, (T)A, (T)B, E, vel, src);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_poisson_source(fvgb_mesh_s* m, const void* ne, const void* ni, bool fp32,
+                                  double* f, cudaStream_t s) {
+  const int64_t N = m->topo.N;
+  if (fp32)
+    k_poisson_source<float><<<grid_for(N), kThreads, 0, s>>>(N, (const float*)ne, (const float*)ni, f);
+  else
+    k_poisson_source<double><<<grid_for(N), kThreads, 0, s>>>(N, (const double*)ne, (const double*)ni, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq(fvgb_mesh_s* m, const double* x, int64_t n, double* out, cudaStream_t s) {
+  k_sumsq_partial<<<kRedBlocks, 256, 0, s>>>(x, n, m->d_scal + 8);
+  k_sum_final<<<1, 1024, 0, s>>>(m->d_scal + 8, kRedBlocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_d(const double* x, double a, double* y, int64_t n, cudaStream_t s) {
+  k_axpy_d<<<grid_for(n), kThreads, 0, s>>>(x, a, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_to_double(const void* x, bool fp32, double* y, int64_t n, cudaStream_t s) {
+  if (fp32) k_add_to_double<float><<<grid_for(n), kThreads, 0, s>>>((const float*)x, y, n);
+  else k_add_to_double<double><<<grid_for(n), kThreads, 0, s>>>((const double*)x, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const double* x, float* y, int64_t n, cudaStream_t s) {
+  k_convert<<<grid_for(n), kThreads, 0, s>>>(x, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_back(const float* x, double* y, int64_t n, cudaStream_t s) {
+  k_convert_back<<<grid_for(n), kThreads, 0, s>>>(x, y, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute(const void* src, void* dst, const int32_t* perm, int64_t n, int ncomp,
+                           int elem_bytes, bool to_internal, cudaStream_t s) {
+  if (elem_bytes == 8)
+    k_permute<double><<<grid_for(n), kThreads, 0, s>>>((const double*)src, (double*)dst, perm, n,
+                                                        ncomp, to_internal ? 1 : 0);
+  else
+    k_permute<float><<<grid_for(n), kThreads, 0, s>>>((const float*)src, (float*)dst, perm, n,
+                                                       ncomp, to_internal ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nonfinite_check(const double* x, int64_t n, int* flag, cudaStream_t s) {
+  k_nonfinite<<<grid_for(n), kThreads, 0, s>>>(x, n, flag);
+  return cudaGetLastError();
+}
+
+#define FVGB_INST(T)                                                                          \
+  template cudaError_t launch_gradient<T>(fvgb_mesh_s*, int, const T*, T*, cudaStream_t);     \
+  template cudaError_t launch_vertex<T>(fvgb_mesh_s*, int, const T*, T*, bool, cudaStream_t); \
+  template cudaError_t launch_face<T>(fvgb_mesh_s*, int, const T*, const T*, const T*,        \
+                                      const double*, bool, double, bool, T*, cudaStream_t);  \
+  template cudaError_t launch_update<T>(fvgb_mesh_s*, int, const T*, const T*, const T*,      \
+                                        double, const T*, T*, T*, cudaStream_t);              \
+  template cudaError_t launch_cell_physics<T>(fvgb_mesh_s*, const T*, const T*, double,       \
+                                              double, double, T*, T*, T*, cudaStream_t);
+FVGB_INST(double)
+FVGB_INST(float)
+#undef FVGB_INST
+
+}  // namespace fvgb
