@@ -1,0 +1,342 @@
+"""Benchmark of the GPU finite-volume hot path: one streamer step = one Poisson solve to
+relative residual 1e-8 + least-squares field + upwind/diamond transport update of n_e
+and n_i, on the 3D electron drift-diffusion + Poisson workload (unit cube, 50^3
+jittered hexes x 6 Kuhn tetrahedra = 750,000 cells, FP64 plain method).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0). --impl reference times the CPU oracle (the plain FP64
+reference implementation of the method) on a bounded sample of the same workload.
+Multi-GPU runs are independent replicas (the path does not shard; no collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per FV step + Poisson, learned vs plain CG at rel. residual 1e-8"
+UNIT = "cell-updates/s"
+K_MESH = 50                 # 6 * 50^3 = 750,000 cells
+MESH_SEED = 201
+RTOL = 1e-8
+ORACLE_SAMPLE_K = 12        # 10,368 cells, same recipe
+WORKLOAD = ("3D electron drift-diffusion + Poisson, FP64 plain method: unit cube, 50^3 "
+            "jittered hexes x 6 Kuhn tets (750,000 cells), seed at (0.5,0.5,0.9), V = 12.5 kV, "
+            "Poisson to rel. residual 1e-8 each step (FP64 defect correction + FP64 inner CG "
+            "on the two-point operator, warm start from the previous potential)")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle (baseline leg and the reference arm): a plain single-threaded FP64 run
+# ---------------------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from synth.workloads import StreamerCase, streamer_mesh
+from oracle.geometry import Geometry
+from oracle import streamer
+k, steps, warm = {k}, {steps}, {warm}
+m = streamer_mesh(k, seed={seed}); c = StreamerCase()
+g = Geometry(m.dim, m.xyz, m.cells, m.bface_vert, m.bface_tag)
+p = streamer.Params(V=c.V, mu=c.mu, A=c.A, B=c.B, De=c.De, centre=c.centre, sigma=c.sigma,
+                    peak=c.peak, background=c.background)
+ne, ni = c.initial(m); dt = c.dt(1.0 / k)
+times = []
+for s in range(warm + steps):
+    t0 = time.perf_counter()
+    ne, ni, phi, E, S = streamer.step(g, p, ne, ni, dt)
+    t1 = time.perf_counter()
+    if s >= warm:
+        times.append(t1 - t0)
+print(json.dumps({{"cells": int(g.n_cell), "times": times}}))
+"""
+
+
+def run_oracle(k, steps, warm):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    code = ORACLE_SNIPPET.format(root=ROOT, k=k, steps=steps, warm=warm, seed=MESH_SEED)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def oracle_sample_text(k, steps, cells):
+    return (f"{steps} streamer step(s) of the same recipe on the k={k} mesh ({cells} cells) "
+            f"by the CPU oracle (numpy/scipy FP64, SuperLU Poisson solve), one thread")
+
+
+def reference_arm(args, world, rank):
+    if rank != 0:
+        return
+    res = run_oracle(ORACLE_SAMPLE_K, args.steps, args.warmup)
+    total = sum(res["times"])
+    value = res["cells"] * len(res["times"]) / total
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / len(res["times"]),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "sample_cells": res["cells"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": oracle_sample_text(ORACLE_SAMPLE_K, args.steps, res["cells"])},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}",
+                                          f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.fh.close()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1])); smax.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def source_hash(*names):
+    h = hashlib.sha256()
+    for n in names:
+        h.update(open(os.path.join(ROOT, "paper_2203_00925_gb300", "csrc", n), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel, shash):
+    """Per-launch DRAM bytes from the committed ncu summary, if it is for this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+        e = d.get(kernel)
+        if e and e.get("source_hash") == shash:
+            return e
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def gpu_arm(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2203_00925_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2203_00925_gb300 import capi, device
+    from synth.workloads import StreamerCase, streamer_mesh
+
+    case = StreamerCase()
+    mesh = streamer_mesh(K_MESH, MESH_SEED)
+    dm = device.DeviceMesh(mesh, [case.bc_ne(), case.bc_phi()], prec="fp64")
+    N = dm.n_cell
+    ne0, ni0 = case.initial(mesh)
+    dt = case.dt(1.0 / K_MESH)
+    sp = capi.streamer_params(mu=case.mu, A=case.A, B=case.B, De=case.De, dt=dt,
+                              solve=capi.solve_opts(rtol=RTOL, inner_rtol=0.1, prec=capi.FVGB_FP64))
+    ne, ni = dm.to_device(ne0), dm.to_device(ni0)
+    phi = torch.zeros(N, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        capi.fvgb_streamer_step(dm.handle, sp, ne, ni, phi, None, 1)
+    capi.fvgb_stats_enable(dm.handle, True)
+    capi.fvgb_stats_get(dm.handle, reset=True)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    infos = []
+    for s in range(args.steps):
+        flush.zero_()                                   # evict L2 between steps (not timed)
+        ev[s][0].record(stream)
+        infos += capi.fvgb_streamer_step(dm.handle, sp, ne, ni, phi, None, 1)
+        ev[s][1].record(stream)
+    barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    stats = capi.fvgb_stats_get(dm.handle, reset=True)
+    # the CG launches do not include the L2 flush: the library syncs inside the step
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * N * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through the public API with host buffers ------------------------------
+    e2e = None
+    if not args.no_e2e:
+        hne = torch.from_numpy(ne0.copy()).pin_memory()
+        hni = torch.from_numpy(ni0.copy()).pin_memory()
+        hphi = torch.zeros(N, dtype=torch.float64).pin_memory()
+        u_ne, u_ni, u_phi = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(3))
+        i_ne, i_ni, i_phi = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(3))
+
+        def e2e_step():
+            for h, u, i in ((hne, u_ne, i_ne), (hni, u_ni, i_ni), (hphi, u_phi, i_phi)):
+                u.copy_(h, non_blocking=True)
+                capi.fvgb_permute(dm.handle, u, i, 1, 8, True)
+            capi.fvgb_streamer_step(dm.handle, sp, i_ne, i_ni, i_phi, None, 1)
+            for h, u, i in ((hne, u_ne, i_ne), (hni, u_ni, i_ni), (hphi, u_phi, i_phi)):
+                capi.fvgb_permute(dm.handle, i, u, 1, 8, False)
+                h.copy_(u, non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        barrier()
+        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for s in range(args.steps):
+            flush.zero_()
+            ev2[s][0].record(stream)
+            e2e_step()
+            ev2[s][1].record(stream)
+        barrier()
+        e2e_ms = sum(a.elapsed_time(b) for a, b in ev2)
+        if world > 1:
+            t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * N * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": 3 * N * 8, "d2h_bytes_per_step": 3 * N * 8}
+
+    # ---- roofline of the dominant kernel: the persistent CG kernel ------------------------
+    w = 8
+    its, launches = stats["cg_iterations"], max(stats["cg_launches"], 1)
+    bytes_per_launch = N * ((its / launches) * (16 * w + 16) + 10 * w + 24)
+    avg_launch_s = stats["cg_ms"] / 1e3 / launches
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    peak = float(peaks["hbm_gbs"])
+    achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else None
+    kname = "k_cg<double,4>"
+    prof = profile_traffic(kname, source_hash("solver.cu"))
+    traffic = None
+    if prof:
+        traffic = prof["dram_bytes_per_iteration"] * (its / launches) + prof.get("dram_bytes_fixed", 0)
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak if achieved else None,
+                "traffic": traffic, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
+                "cg_share_of_step": stats["cg_ms"] / total_ms if world == 1 else None,
+                "iterations_per_launch": its / launches}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        steps_cpu = 5
+        res = run_oracle(ORACLE_SAMPLE_K, steps_cpu, 0)
+        v = res["cells"] * len(res["times"]) / sum(res["times"])
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": oracle_sample_text(ORACLE_SAMPLE_K, steps_cpu, res["cells"])}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": N, "faces": dm.n_face,
+                       "node_neighbour_entries": dm.n_nbr, "poisson_rtol": RTOL,
+                       "l2": "flushed between timed steps (256 MiB write, untimed)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "outer_its_per_step": sum(i["outer_its"] for i in infos) / len(infos),
+                       "inner_cg_its_per_step": sum(i["inner_its_total"] for i in infos) / len(infos),
+                       "max_rel_res": max(i["rel_res"] for i in infos)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": stats["kernel_launches"],
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    dm.free()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+    else:
+        gpu_arm(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

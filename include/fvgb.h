@@ -231,6 +231,28 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
                                void* ni_dev, double* phi_dev, void* E_dev, int32_t nsteps,
                                fvgb_solve_info* info, void* stream);
 
+/* Counters for measurement (no counterpart in the paper's method).
+ *  kernel_launches  kernels launched by the library since the last reset (all meshes)
+ *  cg_launches      inner CG kernels launched for this mesh
+ *  cg_iterations    CG iterations they ran
+ *  cg_ms            summed device time of those kernels, measured with CUDA events on the
+ *                   launching stream when timing was enabled (0 otherwise)
+ *  solves, outer_its  Poisson solves and their outer refinement steps */
+typedef struct {
+  int64_t kernel_launches;
+  int64_t cg_launches;
+  int64_t cg_iterations;
+  double cg_ms;
+  int64_t solves;
+  int64_t outer_its;
+} fvgb_stats;
+
+/* Turn CUDA-event timing of the inner CG kernels on (1) or off (0). */
+fvgb_status fvgb_stats_enable(fvgb_mesh m, int32_t time_cg);
+
+/* Copy the counters into *out (host); reset = 1 zeroes them afterwards. */
+fvgb_status fvgb_stats_get(fvgb_mesh m, fvgb_stats* out, int32_t reset);
+
 /* Message of the last failing call in this thread ("" if none). */
 const char* fvgb_last_error(void);
 

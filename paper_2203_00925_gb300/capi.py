@@ -32,7 +32,7 @@ EXPORTED = [
     "fvgb_mesh_vert_perm",
     "fvgb_permute", "fvgb_gradient", "fvgb_vertex_values", "fvgb_fv_residual",
     "fvgb_fv_step", "fvgb_poisson_apply", "fvgb_poisson_rhs", "fvgb_poisson_solve",
-    "fvgb_streamer_step", "fvgb_last_error",
+    "fvgb_streamer_step", "fvgb_stats_enable", "fvgb_stats_get", "fvgb_last_error",
 ]
 
 
@@ -69,6 +69,15 @@ class fvgb_streamer_params(C.Structure):
                 ("solve", fvgb_solve_opts)]
 
 
+class fvgb_stats(C.Structure):
+    _fields_ = [("kernel_launches", C.c_int64), ("cg_launches", C.c_int64),
+                ("cg_iterations", C.c_int64), ("cg_ms", C.c_double), ("solves", C.c_int64),
+                ("outer_its", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _vp, _i32, _i64, _d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
 _sig = {
     "fvgb_mesh_upload": (C.c_int, [_i32, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _i32,
@@ -89,6 +98,8 @@ _sig = {
                                      C.POINTER(fvgb_solve_info), _vp]),
     "fvgb_streamer_step": (C.c_int, [_vp, C.POINTER(fvgb_streamer_params), _vp, _vp, _vp, _vp,
                                      _i32, C.POINTER(fvgb_solve_info), _vp]),
+    "fvgb_stats_enable": (C.c_int, [_vp, _i32]),
+    "fvgb_stats_get": (C.c_int, [_vp, C.POINTER(fvgb_stats), _i32]),
     "fvgb_last_error": (C.c_char_p, []),
 }
 for _name, (_res, _args) in _sig.items():
@@ -250,6 +261,16 @@ def fvgb_streamer_step(m, params, ne, ni, phi, E, nsteps, stream=None):
     _check(lib.fvgb_streamer_step(m, C.byref(params), ptr(ne), ptr(ni), ptr(phi), ptr(E),
                                   int(nsteps), infos, stream_handle(stream)), "fvgb_streamer_step")
     return [infos[i].as_dict() for i in range(nsteps)]
+
+
+def fvgb_stats_enable(m, time_cg=True):
+    return _check(lib.fvgb_stats_enable(m, int(bool(time_cg))), "fvgb_stats_enable")
+
+
+def fvgb_stats_get(m, reset=False):
+    st = fvgb_stats()
+    _check(lib.fvgb_stats_get(m, C.byref(st), int(bool(reset))), "fvgb_stats_get")
+    return st.as_dict()
 
 
 def fvgb_last_error():

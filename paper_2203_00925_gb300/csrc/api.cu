@@ -14,6 +14,8 @@
 
 namespace fvgb {
 
+std::atomic<long long> g_kernel_launches{0};
+
 namespace {
 thread_local std::string g_last_error;
 }
@@ -146,6 +148,8 @@ cudaError_t alloc_work(fvgb_mesh_s* m, Work<T>& w) {
 }
 
 void release(fvgb_mesh_s* m) {
+  if (m->ev_cg0) cudaEventDestroy(m->ev_cg0);
+  if (m->ev_cg1) cudaEventDestroy(m->ev_cg1);
   for (void* p : m->allocs) cudaFree(p);
   m->allocs.clear();
   if (m->h_scal) cudaFreeHost(m->h_scal);
@@ -222,6 +226,7 @@ fvgb_status solve_impl(fvgb_mesh m, int bcset, const double* f, double* phi,
                        const fvgb_solve_opts* o, fvgb_solve_info* info, cudaStream_t s) {
   fvgb_solve_info loc{0, 0, 0.0, 0.0};
   const int64_t N = m->topo.N;
+  m->stats.solves++;
   double* b = m->dphi_tmp2;
   double* r = m->dphi_tmp;
   fvgb_status st = poisson_rhs_impl(m, bcset, f, b, s);
@@ -250,13 +255,20 @@ fvgb_status solve_impl(fvgb_mesh m, int bcset, const double* f, double* phi,
       FVGB_TRY(cudaMemcpyAsync(hinfo + 2, &m->barrier->status, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
     }
     FVGB_TRY(cudaStreamSynchronize(s), "synchronize");
+    if (m->cg_pending) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, m->ev_cg0, m->ev_cg1) == cudaSuccess) m->stats.cg_ms += ms;
+      m->cg_pending = false;
+    }
     if (outer > 0) {
       loc.inner_its_total += hinfo[0];
+      m->stats.cg_iterations += hinfo[0];
       if (hinfo[2] != 0) { set_error("grid barrier of the CG kernel timed out"); if (info) *info = loc; return FVGB_ETIMEOUT; }
       if (hinfo[1] != 0) { set_error("CG breakdown or non-finite value"); if (info) *info = loc; return FVGB_ENONFINITE; }
     }
     loc.rel_res = std::sqrt(m->h_scal[0]) / bnorm;
     loc.outer_its = outer;
+    if (outer > 0) m->stats.outer_its++;
     if (!std::isfinite(loc.rel_res)) { set_error("non-finite residual"); if (info) *info = loc; return FVGB_ENONFINITE; }
     if (loc.rel_res <= o->rtol) break;
     if (outer >= o->maxit_outer) {
@@ -264,13 +276,16 @@ fvgb_status solve_impl(fvgb_mesh m, int bcset, const double* f, double* phi,
       if (info) *info = loc;
       return FVGB_ENOCONV;
     }
-    if (fp32) {
-      FVGB_TRY(launch_cg<float>(m, bcset, r, o->inner_rtol, o->maxit_inner, s), "CG launch");
-      FVGB_TRY(launch_add_to_double(m->w32.cg_x, true, phi, N, s), "update");
-    } else {
-      FVGB_TRY(launch_cg<double>(m, bcset, r, o->inner_rtol, o->maxit_inner, s), "CG launch");
-      FVGB_TRY(launch_add_to_double(m->w64.cg_x, false, phi, N, s), "update");
+    if (m->time_cg) FVGB_TRY(cudaEventRecord(m->ev_cg0, s), "event");
+    if (fp32) FVGB_TRY(launch_cg<float>(m, bcset, r, o->inner_rtol, o->maxit_inner, s), "CG launch");
+    else FVGB_TRY(launch_cg<double>(m, bcset, r, o->inner_rtol, o->maxit_inner, s), "CG launch");
+    if (m->time_cg) {
+      FVGB_TRY(cudaEventRecord(m->ev_cg1, s), "event");
+      m->cg_pending = true;
     }
+    m->stats.cg_launches++;
+    if (fp32) FVGB_TRY(launch_add_to_double(m->w32.cg_x, true, phi, N, s), "update");
+    else FVGB_TRY(launch_add_to_double(m->w64.cg_x, false, phi, N, s), "update");
   }
   if (info) *info = loc;
   return FVGB_OK;
@@ -372,6 +387,28 @@ fvgb_status fvgb_mesh_free(fvgb_mesh m) {
   if (!m) return FVGB_OK;
   cudaDeviceSynchronize();
   release(m);
+  return FVGB_OK;
+}
+
+fvgb_status fvgb_stats_enable(fvgb_mesh m, int32_t time_cg) {
+  if (fvgb_status st = check_mesh(m)) return st;
+  if (time_cg && !m->ev_cg0) {
+    FVGB_TRY(cudaEventCreate(&m->ev_cg0), "event create");
+    FVGB_TRY(cudaEventCreate(&m->ev_cg1), "event create");
+  }
+  m->time_cg = time_cg ? 1 : 0;
+  return FVGB_OK;
+}
+
+fvgb_status fvgb_stats_get(fvgb_mesh m, fvgb_stats* out, int32_t reset) {
+  if (fvgb_status st = check_mesh(m)) return st;
+  if (!out) { set_error("out is null"); return FVGB_EINVAL; }
+  *out = m->stats;
+  out->kernel_launches = g_kernel_launches.load();
+  if (reset) {
+    m->stats = fvgb_stats{};
+    g_kernel_launches.store(0);
+  }
   return FVGB_OK;
 }
 

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -103,6 +104,10 @@ struct fvgb_mesh_s {
   fvgb::Barrier* barrier = nullptr;
   int* d_cg_info = nullptr;             // [4] iterations, status
   int cg_grid64 = 0, cg_grid32 = 0;     // cooperative grid sizes
+  fvgb_stats stats{};                   // counters (kernel_launches is library-wide)
+  int time_cg = 0;                      // record CUDA events around CG launches
+  cudaEvent_t ev_cg0 = nullptr, ev_cg1 = nullptr;
+  bool cg_pending = false;              // events recorded, elapsed time not yet read
   std::vector<void*> allocs;
 };
 
@@ -122,6 +127,10 @@ template <>
 inline Work<float>& work_of<float>(fvgb_mesh_s* m) { return m->w32; }
 
 constexpr int kRedBlocks = 1024;   // fixed grid of the deterministic reductions
+constexpr int kCgThreads = 1024;   // threads per block of the persistent CG kernel
+
+extern std::atomic<long long> g_kernel_launches;
+inline void count_launch(int n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void set_error(const std::string& msg);
 fvgb_status cuda_status(cudaError_t e, const char* what);

@@ -300,6 +300,7 @@ cudaError_t launch_gradient(fvgb_mesh_s* m, int bcset, const T* u, T* grad, cuda
   else
     k_gradient<T, 2><<<grid_for(t.N), kThreads, 0, s>>>(t.N, t.F, t.Fi, t.nsell.ptr, t.nsell.idx,
         g.cen, g.cen_lo, g.xf, g.xf_lo, u, b.minv, b.gptr, b.gface, b.bval, grad);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -309,6 +310,7 @@ cudaError_t launch_vertex(fvgb_mesh_s* m, int bcset, const T* u, T* uv, bool hom
   GeoDev<T>& g = geo_of<T>(m);
   k_vertex<T><<<grid_for(t.V), kThreads, 0, s>>>(t.V, t.vsell.ptr, t.vsell.idx, g.valpha, u,
                                                   g.bc[bcset].vdir, homog ? 1 : 0, uv);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -334,6 +336,7 @@ cudaError_t launch_face(fvgb_mesh_s* m, int bcset, const T* u, const T* uv, cons
     else FVGB_FACE(2, true, false);
   }
 #undef FVGB_FACE
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -357,6 +360,7 @@ cudaError_t launch_update(fvgb_mesh_s* m, int mode, const T* flux, const T* src,
   if (t.dim == 3) { FVGB_UPD_MODES(4) } else { FVGB_UPD_MODES(3) }
 #undef FVGB_UPD_MODES
 #undef FVGB_UPD
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -368,6 +372,7 @@ cudaError_t launch_cell_physics(fvgb_mesh_s* m, const T* grad, const T* ne, doub
     k_cell_physics<T, 3><<<grid_for(t.N), kThreads, 0, s>>>(t.N, grad, ne, (T)mu, (T)A, (T)B, E, vel, src);
   else
     k_cell_physics<T, 2><<<grid_for(t.N), kThreads, 0, s>>>(t.N, grad, ne, (T)mu, (T)A, (T)B, E, vel, src);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -378,33 +383,39 @@ cudaError_t launch_poisson_source(fvgb_mesh_s* m, const void* ne, const void* ni
     k_poisson_source<float><<<grid_for(N), kThreads, 0, s>>>(N, (const float*)ne, (const float*)ni, f);
   else
     k_poisson_source<double><<<grid_for(N), kThreads, 0, s>>>(N, (const double*)ne, (const double*)ni, f);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_sumsq(fvgb_mesh_s* m, const double* x, int64_t n, double* out, cudaStream_t s) {
   k_sumsq_partial<<<kRedBlocks, 256, 0, s>>>(x, n, m->d_scal + 8);
   k_sum_final<<<1, 1024, 0, s>>>(m->d_scal + 8, kRedBlocks, out);
+  count_launch(2);
   return cudaGetLastError();
 }
 
 cudaError_t launch_axpy_d(const double* x, double a, double* y, int64_t n, cudaStream_t s) {
   k_axpy_d<<<grid_for(n), kThreads, 0, s>>>(x, a, y, n);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_add_to_double(const void* x, bool fp32, double* y, int64_t n, cudaStream_t s) {
   if (fp32) k_add_to_double<float><<<grid_for(n), kThreads, 0, s>>>((const float*)x, y, n);
   else k_add_to_double<double><<<grid_for(n), kThreads, 0, s>>>((const double*)x, y, n);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_convert(const double* x, float* y, int64_t n, cudaStream_t s) {
   k_convert<<<grid_for(n), kThreads, 0, s>>>(x, y, n);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_convert_back(const float* x, double* y, int64_t n, cudaStream_t s) {
   k_convert_back<<<grid_for(n), kThreads, 0, s>>>(x, y, n);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -416,11 +427,13 @@ cudaError_t launch_permute(const void* src, void* dst, const int32_t* perm, int6
   else
     k_permute<float><<<grid_for(n), kThreads, 0, s>>>((const float*)src, (float*)dst, perm, n,
                                                        ncomp, to_internal ? 1 : 0);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_nonfinite_check(const double* x, int64_t n, int* flag, cudaStream_t s) {
   k_nonfinite<<<grid_for(n), kThreads, 0, s>>>(x, n, flag);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -16,7 +16,6 @@
 namespace fvgb {
 namespace {
 
-constexpr int kCgThreads = 256;
 constexpr unsigned long long kBarrierTimeoutNs = 1000000000ull;
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -71,21 +70,31 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return s;  // valid in thread 0
 }
 
-// Grid-wide FP64 sum in a fixed order; ``part`` alternates between two halves so that a
-// fast block never overwrites partials a slow block is still reading.
-__device__ bool grid_sum(double v, double* part, int parity, Barrier* bar, double* sh,
-                         double* out) {
+// Grid-wide FP64 sums of NV values in a fixed order; ``part`` alternates between two
+// halves so that a fast block never overwrites partials a slow block is still reading.
+template <int K>
+__device__ bool grid_sum(const double (&v)[K], double* part, int parity, Barrier* bar,
+                         double* sh, double (&out)[K]) {
   const unsigned nb = gridDim.x;
-  __shared__ double result;
-  v = block_sum(v, sh);
-  if (threadIdx.x == 0) part[parity * nb + blockIdx.x] = v;
+  __shared__ double result[K];
+  static_assert(K <= 2, "at most two sums per reduction");
+  double* base = part + (size_t)parity * nb * 2;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double t = block_sum(v[k], sh);
+    if (threadIdx.x == 0) base[k * nb + blockIdx.x] = t;
+  }
   if (!grid_barrier(bar, nb)) return false;
-  double s = 0.0;
-  for (unsigned b = threadIdx.x; b < nb; b += blockDim.x) s += __ldcg(part + parity * nb + b);
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) result = s;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = 0.0;
+    for (unsigned b = threadIdx.x; b < nb; b += blockDim.x) s += __ldcg(base + k * nb + b);
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) result[k] = s;
+  }
   __syncthreads();
-  *out = result;
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k] = result[k];
   return true;
 }
 
@@ -100,7 +109,7 @@ struct CgArgs {
   T* r;
   T* p;
   T* q;
-  double* part;         // [2][grid]
+  double* part;         // [2][2][grid]
   Barrier* bar;
   int* info;            // [0] iterations, [1] 0 ok / 2 non-finite or breakdown
   double* res;          // [0] rr0, [1] final rr
@@ -108,6 +117,21 @@ struct CgArgs {
   int maxit;
 };
 
+// y_i = (A_T v)_i for one row; neighbours' v are read through L2 (other blocks wrote them).
+template <typename T, int NV>
+__device__ __forceinline__ T at_row(const CgArgs<T>& a, const T* v, int64_t i, T vi) {
+  T y = a.diag[i] * vi;
+#pragma unroll
+  for (int s = 0; s < NV; ++s) {
+    const int32_t n = a.nbr[s * a.N + i];
+    if (n >= 0) y -= a.coef[s * a.N + i] * __ldcg(v + n);
+  }
+  return y;
+}
+
+// Conjugate gradients with two grid barriers per iteration: after the residual update
+// (and its norm) every block forms p = r + beta p and q = A_T r + beta q = A_T p from the
+// finished r, so no barrier is needed between the p update and the operator.
 template <typename T, int NV>
 __global__ void __launch_bounds__(kCgThreads) k_cg(CgArgs<T> a) {
   __shared__ double sh[32];
@@ -118,55 +142,59 @@ __global__ void __launch_bounds__(kCgThreads) k_cg(CgArgs<T> a) {
   const int64_t hi = lo + chunk < N ? lo + chunk : N;
   int parity = 0;
   int its = 0, bad = 0;
-  double rr = 0.0, rr0 = 0.0, loc = 0.0;
+  double rr = 0.0, rr0 = 0.0;
 
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     const T ri = (T)a.rhs[i];
     a.r[i] = ri;
     a.p[i] = ri;
     a.x[i] = T(0);
-    loc += (double)ri * (double)ri;
   }
-  if (!grid_sum(loc, a.part, parity, a.bar, sh, &rr)) goto done;
-  rr0 = rr;
-  if (!(rr0 > 0.0)) { bad = rr0 == 0.0 ? 0 : 2; goto done; }
-
-  while (its < a.maxit) {
-    // q = A_T p (own rows; neighbours' p read through L2) and p . q
-    loc = 0.0;
+  if (!grid_barrier(a.bar, nb)) goto done;
+  {
+    double loc[2] = {0.0, 0.0}, tot[2];
     for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
       const T pi = a.p[i];
-      T y = a.diag[i] * pi;
-#pragma unroll
-      for (int s = 0; s < NV; ++s) {
-        const int32_t n = a.nbr[s * N + i];
-        if (n >= 0) y -= a.coef[s * N + i] * __ldcg(a.p + n);
-      }
+      const T y = at_row<T, NV>(a, a.p, i, pi);
       a.q[i] = y;
-      loc += (double)pi * (double)y;
+      loc[0] += (double)pi * (double)pi;
+      loc[1] += (double)pi * (double)y;
     }
-    double pq;
-    parity ^= 1;
-    if (!grid_sum(loc, a.part, parity, a.bar, sh, &pq)) goto done;
-    if (!(pq > 0.0) || !isfinite(pq)) { bad = 2; break; }
-    const T alpha = (T)(rr / pq);
-    loc = 0.0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      a.x[i] += alpha * a.p[i];
-      const T ri = a.r[i] - alpha * a.q[i];
-      a.r[i] = ri;
-      loc += (double)ri * (double)ri;
+    if (!grid_sum<2>(loc, a.part, parity, a.bar, sh, tot)) goto done;
+    rr = rr0 = tot[0];
+    double pq = tot[1];
+    if (!(rr0 > 0.0)) { bad = rr0 == 0.0 ? 0 : 2; goto done; }
+    while (its < a.maxit) {
+      if (!(pq > 0.0) || !isfinite(pq)) { bad = 2; break; }
+      const T alpha = (T)(rr / pq);
+      double l1[1] = {0.0}, t1[1];
+      for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        a.x[i] += alpha * a.p[i];
+        const T ri = a.r[i] - alpha * a.q[i];
+        a.r[i] = ri;
+        l1[0] += (double)ri * (double)ri;
+      }
+      parity ^= 1;
+      if (!grid_sum<1>(l1, a.part, parity, a.bar, sh, t1)) goto done;
+      const double rrn = t1[0];
+      ++its;
+      if (!isfinite(rrn)) { bad = 2; break; }
+      if (rrn <= a.tol2 * rr0) { rr = rrn; break; }
+      const T beta = (T)(rrn / rr);
+      rr = rrn;
+      double l2[1] = {0.0}, t2[1];
+      for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const T ri = a.r[i];
+        const T pi = ri + beta * a.p[i];
+        const T qi = at_row<T, NV>(a, a.r, i, ri) + beta * a.q[i];
+        a.p[i] = pi;
+        a.q[i] = qi;
+        l2[0] += (double)pi * (double)qi;
+      }
+      parity ^= 1;
+      if (!grid_sum<1>(l2, a.part, parity, a.bar, sh, t2)) goto done;
+      pq = t2[0];
     }
-    double rrn;
-    parity ^= 1;
-    if (!grid_sum(loc, a.part, parity, a.bar, sh, &rrn)) goto done;
-    ++its;
-    if (!isfinite(rrn)) { bad = 2; break; }
-    if (rrn <= a.tol2 * rr0) { rr = rrn; break; }
-    const T beta = (T)(rrn / rr);
-    rr = rrn;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) a.p[i] = a.r[i] + beta * a.p[i];
-    if (!grid_barrier(a.bar, nb)) goto done;
   }
 done:
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -189,7 +217,7 @@ int cg_grid_size(fvgb_mesh_s* m, bool fp32) {
   const void* k = fp32 ? cg_kernel<float>(m->topo.dim + 1) : cg_kernel<double>(m->topo.dim + 1);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kCgThreads, 0) != cudaSuccess)
     return 0;
-  if (per_sm > 8) per_sm = 8;
+  if (per_sm > 2) per_sm = 2;
   int grid = per_sm * m->num_sms;
   // no more blocks than there are cells to own
   const int64_t need = (m->topo.N + kCgThreads - 1) / kCgThreads;
@@ -223,6 +251,7 @@ cudaError_t launch_cg(fvgb_mesh_s* m, int bcset, const double* rhs, double rtol,
   cudaError_t e = cudaMemsetAsync(m->barrier, 0, sizeof(Barrier), s);
   if (e != cudaSuccess) return e;
   void* args[] = {&a};
+  count_launch();
   return cudaLaunchCooperativeKernel(cg_kernel<T>(m->topo.dim + 1), dim3(grid), dim3(kCgThreads),
                                      args, 0, s);
 }
