@@ -157,6 +157,28 @@ typedef struct {
 fvgb_status fvgb_fv_residual(fvgb_mesh m, const fvgb_tcoef* tc, const void* u_dev,
                              void* res_dev, void* stream);
 
+/* fvgb_fv_residual that allocates nothing. The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they need a residual,
+ * such as a host program whose device memory is handed out by its own pool (a stray
+ * cudaMalloc there can fail or fragment the pool) or a time-critical loop in which
+ * cudaMalloc / cudaFree would add latency and implicit synchronisation. Arguments,
+ * results and errors are those of fvgb_fv_residual.
+ *  - Scratch (the face fluxes and vertex values) lives in one fixed 8 MiB device array
+ *    owned by the library, which every GPU that loads the library holds until the
+ *    process exits. A mesh needs n_face + n_vert reals of it (rounded up to 256 bytes
+ *    after the fluxes): up to about 1,048,000 doubles or 2,097,000 floats, i.e. FP64
+ *    tetrahedral meshes of roughly 480,000 cells. Larger meshes get FVGB_EINVAL with a
+ *    message; use fvgb_fv_residual for them.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current) and caches it; make that first
+ *    call before any stream capture.
+ *  - Every call shares the one array and leaves its contents behind; each call writes
+ *    the scratch it reads, so nothing needs clearing, but calls that overlap on the GPU
+ *    (other streams, other meshes, other host threads) race on it: serialise them.
+ *  - The mesh's device must be the current device. */
+fvgb_status fvgb_fv_residual_noalloc(fvgb_mesh m, const fvgb_tcoef* tc, const void* u_dev,
+                                     void* res_dev, void* stream);
+
 /* nsteps explicit time steps of eq. 6 in place on u_dev: per step
  * u^(k) = u^n + stage_alpha[k] dt Res(u^(k-1)), k = 0..nstage-1, u^{n+1} = u^(last).
  * nstage = 1 with stage_alpha = {1} (or stage_alpha = NULL) is explicit Euler;

@@ -31,6 +31,7 @@ EXPORTED = [
     "fvgb_mesh_upload", "fvgb_mesh_free", "fvgb_mesh_info", "fvgb_mesh_cell_perm",
     "fvgb_mesh_vert_perm",
     "fvgb_permute", "fvgb_gradient", "fvgb_vertex_values", "fvgb_fv_residual",
+    "fvgb_fv_residual_noalloc",
     "fvgb_fv_step", "fvgb_poisson_apply", "fvgb_poisson_rhs", "fvgb_poisson_solve",
     "fvgb_streamer_step", "fvgb_stats_enable", "fvgb_stats_get", "fvgb_last_error",
 ]
@@ -91,6 +92,7 @@ _sig = {
     "fvgb_gradient": (C.c_int, [_vp, _i32, _vp, _vp, _vp]),
     "fvgb_vertex_values": (C.c_int, [_vp, _i32, _vp, _vp, _vp]),
     "fvgb_fv_residual": (C.c_int, [_vp, C.POINTER(fvgb_tcoef), _vp, _vp, _vp]),
+    "fvgb_fv_residual_noalloc": (C.c_int, [_vp, C.POINTER(fvgb_tcoef), _vp, _vp, _vp]),
     "fvgb_fv_step": (C.c_int, [_vp, C.POINTER(fvgb_tcoef), _vp, _d, _i32, _vp, _i32, _vp]),
     "fvgb_poisson_apply": (C.c_int, [_vp, _i32, _vp, _vp, _vp]),
     "fvgb_poisson_rhs": (C.c_int, [_vp, _i32, _vp, _vp, _vp]),
@@ -214,6 +216,12 @@ def tcoef(vel=None, vel_const=(0.0, 0.0, 0.0), diff=0.0, src=None, bcset=0, reco
 def fvgb_fv_residual(m, tc, u, res, stream=None):
     return _check(lib.fvgb_fv_residual(m, C.byref(tc), ptr(u), ptr(res), stream_handle(stream)),
                   "fvgb_fv_residual")
+
+
+def fvgb_fv_residual_noalloc(m, tc, u, res, stream=None):
+    """fvgb_fv_residual with its scratch in the library's fixed device array (no allocation)."""
+    return _check(lib.fvgb_fv_residual_noalloc(m, C.byref(tc), ptr(u), ptr(res),
+                                               stream_handle(stream)), "fvgb_fv_residual_noalloc")
 
 
 def fvgb_fv_step(m, tc, u, dt, nsteps, stage_alpha=None, stream=None):
