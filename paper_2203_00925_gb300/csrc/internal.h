@@ -28,8 +28,8 @@ struct BCDev {
   int32_t* gptr = nullptr;   // [N+1]
   int32_t* gface = nullptr;  // ghost faces
   T* vdir = nullptr;         // [V] NaN = not Dirichlet
-  int32_t* at_nbr = nullptr; // [nv][N]
-  T* at_coef = nullptr;      // [nv][N]
+  int32_t* at_nbr = nullptr; // [N][4] (unused slot: the cell itself)
+  T* at_coef = nullptr;      // [N][4] (unused slot: 0)
   T* at_diag = nullptr;      // [N]
 };
 
@@ -127,7 +127,7 @@ template <>
 inline Work<float>& work_of<float>(fvgb_mesh_s* m) { return m->w32; }
 
 constexpr int kRedBlocks = 1024;   // fixed grid of the deterministic reductions
-constexpr int kCgThreads = 1024;   // threads per block of the persistent CG kernel
+constexpr int kCgThreads = 512;    // threads per block of the persistent CG kernel
 
 extern std::atomic<long long> g_kernel_launches;
 inline void count_launch(int n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }

@@ -550,20 +550,22 @@ int build_host_mesh(int dim, int64_t n_vert, const double* xyz_in, int64_t n_cel
       for (int k = 0; k < nsym; ++k) B.minv[k * N + i] = inv[k];
     }
     if (singular) { err = "singular least-squares gradient stencil"; return kEMESH; }
-    // two-point operator A_T
-    B.at_nbr.assign((size_t)nv * N, -1);
-    B.at_coef.assign((size_t)nv * N, 0.0);
+    // two-point operator A_T: four slots per cell (cell-major); an unused slot points
+    // at the cell itself with coefficient 0 so that the kernel needs no branch
+    B.at_nbr.assign((size_t)4 * N, 0);
+    B.at_coef.assign((size_t)4 * N, 0.0);
     B.at_diag.assign(N, 0.0);
 #pragma omp parallel for
     for (int64_t i = 0; i < N; ++i) {
       double diag = 0.0;
+      for (int k = 0; k < 4; ++k) B.at_nbr[i * 4 + k] = (int32_t)i;
       for (int k = 0; k < nv; ++k) {
         int32_t e = m.cell_face[k * N + i];
         int32_t f = e >= 0 ? e : ~e;
         double c1 = m.coef[f];
         if (f < Fi) {
-          B.at_nbr[k * N + i] = e >= 0 ? m.fR[f] : m.fL[f];
-          B.at_coef[k * N + i] = c1;
+          B.at_nbr[i * 4 + k] = e >= 0 ? m.fR[f] : m.fL[f];
+          B.at_coef[i * 4 + k] = c1;
           diag += c1;
         } else if (B.bkind[f - Fi] == 1) {
           diag += c1;

@@ -16,8 +16,8 @@ struct BCSetHost {
   std::vector<int32_t> gptr;      // [N+1] Dirichlet ghost points of each cell (CSR)
   std::vector<int32_t> gface;     //        boundary face index (global face id)
   std::vector<double> vdir;       // [V] Dirichlet vertex value, NaN when not Dirichlet
-  std::vector<int32_t> at_nbr;    // SoA [dim+1][N] two-point operator: neighbour or -1
-  std::vector<double> at_coef;    // SoA [dim+1][N] off-diagonal coefficient c1 (0 if none)
+  std::vector<int32_t> at_nbr;    // [N][4] two-point operator: neighbour (the cell itself if none)
+  std::vector<double> at_coef;    // [N][4] off-diagonal coefficient c1 (0 if none)
   std::vector<double> at_diag;    // [N]
   int n_dirichlet_faces = 0;
 };

@@ -56,53 +56,58 @@ __device__ bool grid_barrier(Barrier* bar, unsigned nblocks) {
   return ok != 0;
 }
 
+// Block-wide FP64 sum in a fixed order: a shared-memory tree over the block's threads,
+// finished by warp 0. Few FP64 instructions per thread (GB300's FP64 rate is low).
 __device__ __forceinline__ double block_sum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  sh[threadIdx.x] = v;
   __syncthreads();
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x < 32) {
-    s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  for (unsigned s = blockDim.x >> 1; s >= 32; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
   }
-  return s;  // valid in thread 0
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = sh[threadIdx.x];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  return t;  // valid in thread 0
 }
 
-// Grid-wide FP64 sums of NV values in a fixed order; ``part`` alternates between two
+// Grid-wide FP64 sums of K values in a fixed order (block tree, then warp 0 of every
+// block sums the block partials in the same order); ``part`` alternates between two
 // halves so that a fast block never overwrites partials a slow block is still reading.
+// Returns false when the grid barrier gave up. The sums land in out (shared memory).
 template <int K>
 __device__ bool grid_sum(const double (&v)[K], double* part, int parity, Barrier* bar,
-                         double* sh, double (&out)[K]) {
-  const unsigned nb = gridDim.x;
-  __shared__ double result[K];
+                         double* sh, double* out) {
   static_assert(K <= 2, "at most two sums per reduction");
+  const unsigned nb = gridDim.x;
   double* base = part + (size_t)parity * nb * 2;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const double t = block_sum(v[k], sh);
     if (threadIdx.x == 0) base[k * nb + blockIdx.x] = t;
+    __syncthreads();
   }
   if (!grid_barrier(bar, nb)) return false;
+  if (threadIdx.x < 32) {
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double s = 0.0;
-    for (unsigned b = threadIdx.x; b < nb; b += blockDim.x) s += __ldcg(base + k * nb + b);
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) result[k] = s;
+    for (int k = 0; k < K; ++k) {
+      double t = 0.0;
+      for (unsigned b = threadIdx.x; b < nb; b += 32) t += __ldcg(base + k * nb + b);
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (threadIdx.x == 0) out[k] = t;
+    }
   }
   __syncthreads();
-#pragma unroll
-  for (int k = 0; k < K; ++k) out[k] = result[k];
   return true;
 }
 
 template <typename T>
 struct CgArgs {
   int64_t N;
-  const int32_t* nbr;   // [NV][N]
-  const T* coef;        // [NV][N]
+  const int32_t* nbr;   // [N][4]
+  const T* coef;        // [N][4]
   const T* diag;        // [N]
   const double* rhs;    // [N]
   T* x;
@@ -117,97 +122,205 @@ struct CgArgs {
   int maxit;
 };
 
-// y_i = (A_T v)_i for one row; neighbours' v are read through L2 (other blocks wrote them).
-template <typename T, int NV>
-__device__ __forceinline__ T at_row(const CgArgs<T>& a, const T* v, int64_t i, T vi) {
-  T y = a.diag[i] * vi;
-#pragma unroll
-  for (int s = 0; s < NV; ++s) {
-    const int32_t n = a.nbr[s * a.N + i];
-    if (n >= 0) y -= a.coef[s * a.N + i] * __ldcg(v + n);
+// Four operator coefficients of one row, loaded with vector loads.
+template <typename T>
+struct Coef4;
+template <>
+struct Coef4<float> {
+  float c[4];
+  __device__ __forceinline__ void load(const float* p, int64_t i) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p) + i);
+    c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
   }
-  return y;
+};
+template <>
+struct Coef4<double> {
+  double c[4];
+  __device__ __forceinline__ void load(const double* p, int64_t i) {
+    const double2 v0 = __ldg(reinterpret_cast<const double2*>(p) + 2 * i);
+    const double2 v1 = __ldg(reinterpret_cast<const double2*>(p) + 2 * i + 1);
+    c[0] = v0.x; c[1] = v0.y; c[2] = v1.x; c[3] = v1.y;
+  }
+};
+
+// Rows per thread per trip through a phase: all loads of the trip are issued before any
+// store so that the gathers of several rows are in flight together.
+template <typename T>
+__host__ __device__ constexpr int unroll_rows() { return sizeof(T) == 4 ? 4 : 2; }
+
+// Phase 1: x += alpha p, r -= alpha q (own rows); returns this thread's sum of r^2.
+template <typename T>
+__device__ __forceinline__ T cg_phase_xr(const CgArgs<T>& a, int64_t lo, int64_t hi, T alpha) {
+  T* __restrict__ X = a.x;
+  T* __restrict__ R = a.r;
+  const T* __restrict__ P = a.p;
+  const T* __restrict__ Q = a.q;
+  constexpr int kUnroll = unroll_rows<T>();
+  T acc = T(0);
+  const int64_t bd = blockDim.x;
+  for (int64_t b = lo + threadIdx.x; b < hi; b += kUnroll * bd) {
+    T x[kUnroll], p[kUnroll], r[kUnroll], q[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t i = b + u * bd;
+      if (i < hi) { x[u] = X[i]; p[u] = P[i]; r[u] = R[i]; q[u] = Q[i]; }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t i = b + u * bd;
+      if (i < hi) {
+        const T rn = r[u] - alpha * q[u];
+        X[i] = x[u] + alpha * p[u];
+        R[i] = rn;
+        acc += rn * rn;
+      }
+    }
+  }
+  return acc;
+}
+
+// Phase 2: p = r + beta p, q = A_T r + beta q (= A_T p); returns this thread's sum of
+// p.q. Neighbours' r are read through L2 (other blocks wrote them this iteration).
+template <typename T>
+__device__ __forceinline__ T cg_phase_pq(const CgArgs<T>& a, int64_t lo, int64_t hi, T beta,
+                                         const T* v_src) {
+  T* __restrict__ P = a.p;
+  T* __restrict__ Q = a.q;
+  const T* __restrict__ R = v_src;
+  const int4* __restrict__ NB = reinterpret_cast<const int4*>(a.nbr);
+  constexpr int kUnroll = unroll_rows<T>();
+  T acc = T(0);
+  const int64_t bd = blockDim.x;
+  for (int64_t b = lo + threadIdx.x; b < hi; b += kUnroll * bd) {
+    T r[kUnroll], p[kUnroll], q[kUnroll], d[kUnroll], g[kUnroll][4];
+    int4 nb[kUnroll];
+    Coef4<T> c[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t i = b + u * bd;
+      if (i < hi) {
+        nb[u] = __ldg(NB + i);
+        r[u] = R[i]; p[u] = P[i]; q[u] = Q[i];
+        d[u] = __ldg(a.diag + i);
+        c[u].load(a.coef, i);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t i = b + u * bd;
+      if (i < hi) {
+        g[u][0] = __ldcg(R + nb[u].x);
+        g[u][1] = __ldcg(R + nb[u].y);
+        g[u][2] = __ldcg(R + nb[u].z);
+        g[u][3] = __ldcg(R + nb[u].w);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t i = b + u * bd;
+      if (i < hi) {
+        T y = d[u] * r[u];
+        y -= c[u].c[0] * g[u][0];
+        y -= c[u].c[1] * g[u][1];
+        y -= c[u].c[2] * g[u][2];
+        y -= c[u].c[3] * g[u][3];
+        const T pn = r[u] + beta * p[u];
+        const T qn = y + beta * q[u];
+        P[i] = pn;
+        Q[i] = qn;
+        acc += pn * qn;
+      }
+    }
+  }
+  return acc;
 }
 
 // Conjugate gradients with two grid barriers per iteration: after the residual update
 // (and its norm) every block forms p = r + beta p and q = A_T r + beta q = A_T p from the
 // finished r, so no barrier is needed between the p update and the operator.
-template <typename T, int NV>
+// Dot products: each thread accumulates its own rows in T, the sums across threads and
+// blocks are FP64 in a fixed order. The scalars alpha, beta and the stopping test are
+// computed once per block (thread 0) and broadcast through shared memory.
+template <typename T>
 __global__ void __launch_bounds__(kCgThreads) k_cg(CgArgs<T> a) {
-  __shared__ double sh[32];
+  __shared__ double sh[kCgThreads];
+  __shared__ double tot[2];
+  __shared__ T s_alpha, s_beta;
+  __shared__ int s_state;   // 0 continue, 1 converged, 2 breakdown / non-finite, 3 zero rhs
   const int64_t N = a.N;
   const unsigned nb = gridDim.x;
   const int64_t chunk = (N + nb - 1) / nb;
   const int64_t lo = blockIdx.x * chunk;
   const int64_t hi = lo + chunk < N ? lo + chunk : N;
   int parity = 0;
-  int its = 0, bad = 0;
-  double rr = 0.0, rr0 = 0.0;
+  int its = 0;
+  double rr = 0.0, rr0 = 0.0;   // meaningful in thread 0
+  if (threadIdx.x == 0) s_state = 0;
 
+  // r = rhs, p = 0, q = 0, x = 0: the first p/q phase (beta = 0) then gives p = r, q = A_T r
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     const T ri = (T)a.rhs[i];
     a.r[i] = ri;
-    a.p[i] = ri;
+    a.p[i] = T(0);
+    a.q[i] = T(0);
     a.x[i] = T(0);
   }
   if (!grid_barrier(a.bar, nb)) goto done;
   {
-    double loc[2] = {0.0, 0.0}, tot[2];
+    T l0 = T(0);
     for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      const T pi = a.p[i];
-      const T y = at_row<T, NV>(a, a.p, i, pi);
-      a.q[i] = y;
-      loc[0] += (double)pi * (double)pi;
-      loc[1] += (double)pi * (double)y;
+      const T ri = a.r[i];
+      l0 += ri * ri;
     }
+    const T l1 = cg_phase_pq<T>(a, lo, hi, T(0), a.r);
+    const double loc[2] = {(double)l0, (double)l1};
     if (!grid_sum<2>(loc, a.part, parity, a.bar, sh, tot)) goto done;
-    rr = rr0 = tot[0];
-    double pq = tot[1];
-    if (!(rr0 > 0.0)) { bad = rr0 == 0.0 ? 0 : 2; goto done; }
-    while (its < a.maxit) {
-      if (!(pq > 0.0) || !isfinite(pq)) { bad = 2; break; }
-      const T alpha = (T)(rr / pq);
-      double l1[1] = {0.0}, t1[1];
-      for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        a.x[i] += alpha * a.p[i];
-        const T ri = a.r[i] - alpha * a.q[i];
-        a.r[i] = ri;
-        l1[0] += (double)ri * (double)ri;
-      }
+    if (threadIdx.x == 0) {
+      rr = rr0 = tot[0];
+      const double pq = tot[1];
+      s_state = !(rr0 > 0.0) ? (rr0 == 0.0 ? 3 : 2) : (!(pq > 0.0) || !isfinite(pq) ? 2 : 0);
+      s_alpha = (T)(rr / pq);
+    }
+    __syncthreads();
+    while (s_state == 0 && its < a.maxit) {
+      const T lr = cg_phase_xr<T>(a, lo, hi, s_alpha);
       parity ^= 1;
-      if (!grid_sum<1>(l1, a.part, parity, a.bar, sh, t1)) goto done;
-      const double rrn = t1[0];
+      const double l1v[1] = {(double)lr};
+      if (!grid_sum<1>(l1v, a.part, parity, a.bar, sh, tot)) goto done;
       ++its;
-      if (!isfinite(rrn)) { bad = 2; break; }
-      if (rrn <= a.tol2 * rr0) { rr = rrn; break; }
-      const T beta = (T)(rrn / rr);
-      rr = rrn;
-      double l2[1] = {0.0}, t2[1];
-      for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const T ri = a.r[i];
-        const T pi = ri + beta * a.p[i];
-        const T qi = at_row<T, NV>(a, a.r, i, ri) + beta * a.q[i];
-        a.p[i] = pi;
-        a.q[i] = qi;
-        l2[0] += (double)pi * (double)qi;
+      if (threadIdx.x == 0) {
+        const double rrn = tot[0];
+        if (!isfinite(rrn)) s_state = 2;
+        else if (rrn <= a.tol2 * rr0) s_state = 1;
+        s_beta = (T)(rrn / rr);
+        rr = rrn;
       }
+      __syncthreads();
+      if (s_state != 0) break;
+      const T lpq = cg_phase_pq<T>(a, lo, hi, s_beta, a.r);
       parity ^= 1;
-      if (!grid_sum<1>(l2, a.part, parity, a.bar, sh, t2)) goto done;
-      pq = t2[0];
+      const double l2v[1] = {(double)lpq};
+      if (!grid_sum<1>(l2v, a.part, parity, a.bar, sh, tot)) goto done;
+      if (threadIdx.x == 0) {
+        const double pq = tot[0];
+        if (!(pq > 0.0) || !isfinite(pq)) s_state = 2;
+        s_alpha = (T)(rr / pq);
+      }
+      __syncthreads();
     }
   }
 done:
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.info[0] = its;
-    a.info[1] = bad;
+    a.info[1] = s_state == 2 ? 2 : 0;
     a.res[0] = rr0;
     a.res[1] = rr;
   }
 }
 
 template <typename T>
-const void* cg_kernel(int nv) {
-  return nv == 4 ? (const void*)k_cg<T, 4> : (const void*)k_cg<T, 3>;
+const void* cg_kernel(int) {
+  return (const void*)k_cg<T>;
 }
 
 }  // namespace
