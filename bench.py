@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     return ap.parse_args()
 
 
@@ -240,6 +241,74 @@ def gpu_arm(args, world, rank, local):
         total_ms = float(t.item())
     value = world * N * args.steps / (total_ms / 1e3)
 
+    # ---- roofline of the dominant kernel: the persistent FP64 CG kernel ------------------
+    # GB300 runs FP64 at ~1/69 of the FP32 rate; ncu shows this kernel bound by the FP64
+    # pipe with its working set in L2, so it is reported against the FP64 ALU peak
+    # (nominal 1.25 TFLOP/s = SMs x 2 FP64 FMA/clk x 2 flop x max clock).
+    w = 8
+    its, launches = stats["cg_iterations"], max(stats["cg_launches"], 1)
+    per_launch_its = its / launches
+    flops_per_launch = N * (per_launch_its * 21 + 13)
+    bytes_per_launch = N * (per_launch_its * (16 * w + 16) + 10 * w + 24)
+    avg_launch_s = stats["cg_ms"] / 1e3 / launches
+    props = torch.cuda.get_device_properties(local)
+    peak_tflops = props.multi_processor_count * 2 * 2 * 2.070e9 / 1e12
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    hbm = float(peaks["hbm_gbs"])
+    achieved = flops_per_launch / avg_launch_s / 1e12 if avg_launch_s > 0 else None
+    kname = "k_cg<double,4>"
+    prof = profile_traffic(kname, source_hash("solver.cu"))
+    traffic = prof["dram_bytes_per_launch"] if prof else None
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / peak_tflops if achieved else None,
+                "traffic": traffic,
+                "peak_source": "derived FP64 peak: SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
+                "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
+                "iterations_per_launch": per_launch_its,
+                "cg_share_of_step": stats["cg_ms"] / total_ms if world == 1 else None,
+                "hbm_view": {"algorithmic_bytes_per_launch": bytes_per_launch,
+                             "achieved_GBps": bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else None,
+                             "peak_GBps": hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}}
+
+    # ---- mixed precision on the same workload: FP32 transport + FP32 inner CG, FP64 outer
+    # refinement; same steps from the same state, error against this FP64 run --------------
+    variants = None
+    if world == 1 and not args.no_variants:
+        ref_ne = dm.to_host(ne)
+        ref_phi = dm.to_host(phi)
+        ref_q = capi.fvgb_integral(dm.handle, ni) - capi.fvgb_integral(dm.handle, ne)
+        dmx = device.DeviceMesh(mesh, [case.bc_ne(), case.bc_phi()], prec="mixed")
+        spx = capi.streamer_params(mu=case.mu, A=case.A, B=case.B, De=case.De, dt=dt,
+                                   solve=capi.solve_opts(rtol=RTOL, inner_rtol=0.1, prec=capi.FVGB_FP32))
+        nex, nix = dmx.to_device(ne0), dmx.to_device(ni0)
+        phix = torch.zeros(N, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            capi.fvgb_streamer_step(dmx.handle, spx, nex, nix, phix, None, 1)
+        barrier()
+        evx = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        infx = []
+        for s in range(args.steps):
+            flush.zero_()
+            evx[s][0].record(stream)
+            infx += capi.fvgb_streamer_step(dmx.handle, spx, nex, nix, phix, None, 1)
+            evx[s][1].record(stream)
+        barrier()
+        mixed_ms = sum(a.elapsed_time(b) for a, b in evx)
+        qx = capi.fvgb_integral(dmx.handle, nix) - capi.fvgb_integral(dmx.handle, nex)
+        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        variants = {"mixed": {
+            "desc": "FP32 transport + FP32 inner CG (FP64 dot products), FP64 outer residual",
+            "ms_per_step": mixed_ms / args.steps, "value": N * args.steps / (mixed_ms / 1e3),
+            "speedup_vs_fp64": total_ms / mixed_ms,
+            "max_rel_res": max(i["rel_res"] for i in infx),
+            "inner_cg_its_per_step": sum(i["inner_its_total"] for i in infx) / len(infx),
+            "rel_err_vs_fp64_after_steps": {"n_e": rel(dmx.to_host(nex), ref_ne),
+                                            "phi": rel(dmx.to_host(phix), ref_phi),
+                                            "total_charge": abs(qx - ref_q) / abs(ref_q) if ref_q else None},
+            "steps_compared": args.warmup + args.steps}}
+        dmx.free()
+
     # ---- end to end through the public API with host buffers ------------------------------
     e2e = None
     if not args.no_e2e:
@@ -277,35 +346,6 @@ def gpu_arm(args, world, rank, local):
         e2e = {"value": world * N * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": 3 * N * 8, "d2h_bytes_per_step": 3 * N * 8}
 
-    # ---- roofline of the dominant kernel: the persistent FP64 CG kernel ------------------
-    # GB300 runs FP64 at ~1/69 of the FP32 rate; ncu shows this kernel bound by the FP64
-    # pipe with its working set in L2, so it is reported against the FP64 ALU peak
-    # (nominal 1.25 TFLOP/s = SMs x 2 FP64 FMA/clk x 2 flop x max clock).
-    w = 8
-    its, launches = stats["cg_iterations"], max(stats["cg_launches"], 1)
-    per_launch_its = its / launches
-    flops_per_launch = N * (per_launch_its * 21 + 13)
-    bytes_per_launch = N * (per_launch_its * (16 * w + 16) + 10 * w + 24)
-    avg_launch_s = stats["cg_ms"] / 1e3 / launches
-    props = torch.cuda.get_device_properties(local)
-    peak_tflops = props.multi_processor_count * 2 * 2 * 2.070e9 / 1e12
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    hbm = float(peaks["hbm_gbs"])
-    achieved = flops_per_launch / avg_launch_s / 1e12 if avg_launch_s > 0 else None
-    kname = "k_cg<double,4>"
-    prof = profile_traffic(kname, source_hash("solver.cu"))
-    traffic = prof["dram_bytes_per_launch"] if prof else None
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / peak_tflops if achieved else None,
-                "traffic": traffic,
-                "peak_source": "derived FP64 peak: SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
-                "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
-                "iterations_per_launch": per_launch_its,
-                "cg_share_of_step": stats["cg_ms"] / total_ms if world == 1 else None,
-                "hbm_view": {"algorithmic_bytes_per_launch": bytes_per_launch,
-                             "achieved_GBps": bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else None,
-                             "peak_GBps": hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}}
-
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         steps_cpu = 5
@@ -329,6 +369,7 @@ def gpu_arm(args, world, rank, local):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "variants": variants,
             "gpu_launches": stats["kernel_launches"],
             "clocks": clk,
         }

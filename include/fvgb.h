@@ -101,6 +101,39 @@ fvgb_status fvgb_mesh_upload(int32_t dim, int64_t n_vert, const double* xyz,
                              const fvgb_bcset* bcsets, int32_t reorder, int32_t prec,
                              void* stream, fvgb_mesh* out);
 
+/* One mesh of an ensemble (BASELINE's batched workload: many independent meshes
+ * advanced together). Arrays as in fvgb_mesh_upload; bcsets points at n_bcset sets for
+ * this mesh (the same number for every mesh; tags are the mesh's own). */
+typedef struct {
+  int64_t n_vert;
+  const double* xyz;
+  int64_t n_cell;
+  const int32_t* cell_vert;
+  int64_t n_bface;
+  const int32_t* bface_vert;
+  const int32_t* bface_tag;
+  const fvgb_bcset* bcsets;
+} fvgb_mesh_part;
+
+/* Upload n_part independent meshes as one mesh whose cells, faces and vertices are the
+ * meshes' packed one after the other (part p's cells form one contiguous internal range,
+ * Morton-ordered within the part). Every operator then runs over all parts in one launch;
+ * fvgb_poisson_solve solves every part to its own tolerance (per-part norms, CG scalars and
+ * stopping tests); fvgb_streamer_step advances all parts with one time step.
+ * Boundary tags must be < 65536 and n_part <= 128. Errors as fvgb_mesh_upload. */
+fvgb_status fvgb_mesh_upload_ensemble(int32_t dim, int32_t n_part, const fvgb_mesh_part* parts,
+                                      int32_t n_bcset, int32_t reorder, int32_t prec,
+                                      void* stream, fvgb_mesh* out);
+
+/* Number of parts (1 for fvgb_mesh_upload) and, when cell_begin is not NULL, the internal
+ * cell range of each part: cell_begin[0..n_part] (host, n_part + 1 entries). */
+fvgb_status fvgb_mesh_parts(fvgb_mesh m, int32_t* n_part, int64_t* cell_begin);
+
+/* Per-part results of the last fvgb_poisson_solve on this mesh (host arrays of n_part
+ * entries, any may be NULL): final relative residual, outer steps, inner CG iterations. */
+fvgb_status fvgb_solve_parts(fvgb_mesh m, double* rel_res, int32_t* outer_its,
+                             int32_t* inner_its);
+
 /* Release every device and host allocation of the mesh (synchronises the device). */
 fvgb_status fvgb_mesh_free(fvgb_mesh m);
 
@@ -252,6 +285,11 @@ typedef struct {
 fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void* ne_dev,
                                void* ni_dev, double* phi_dev, void* E_dev, int32_t nsteps,
                                fvgb_solve_info* info, void* stream);
+
+/* Integral of a cell field over the domain, sum_i mu_i u_i (the mass of eq. 2 summed
+ * over the cells), accumulated in FP64 in a fixed order (bitwise reproducible).
+ *  u_dev [n_cell] real; *out_host receives the sum. Synchronises the stream. */
+fvgb_status fvgb_integral(fvgb_mesh m, const void* u_dev, double* out_host, void* stream);
 
 /* Counters for measurement (no counterpart in the paper's method).
  *  kernel_launches  kernels launched by the library since the last reset (all meshes)

@@ -28,12 +28,13 @@ STATUS_NAMES = {0: "FVGB_OK", 1: "FVGB_EINVAL", 2: "FVGB_EMESH", 3: "FVGB_ENOMEM
                 7: "FVGB_ETIMEOUT", 8: "FVGB_EUNSUPPORTED"}
 
 EXPORTED = [
-    "fvgb_mesh_upload", "fvgb_mesh_free", "fvgb_mesh_info", "fvgb_mesh_cell_perm",
+    "fvgb_mesh_upload", "fvgb_mesh_upload_ensemble", "fvgb_mesh_parts", "fvgb_solve_parts",
+    "fvgb_mesh_free", "fvgb_mesh_info", "fvgb_mesh_cell_perm",
     "fvgb_mesh_vert_perm",
     "fvgb_permute", "fvgb_gradient", "fvgb_vertex_values", "fvgb_fv_residual",
     "fvgb_fv_residual_noalloc",
     "fvgb_fv_step", "fvgb_poisson_apply", "fvgb_poisson_rhs", "fvgb_poisson_solve",
-    "fvgb_streamer_step", "fvgb_stats_enable", "fvgb_stats_get", "fvgb_last_error",
+    "fvgb_streamer_step", "fvgb_integral", "fvgb_stats_enable", "fvgb_stats_get", "fvgb_last_error",
 ]
 
 
@@ -43,6 +44,12 @@ class fvgb_bc(C.Structure):
 
 class fvgb_bcset(C.Structure):
     _fields_ = [("n_bc", C.c_int32), ("bc", C.POINTER(fvgb_bc))]
+
+
+class fvgb_mesh_part(C.Structure):
+    _fields_ = [("n_vert", C.c_int64), ("xyz", C.c_void_p), ("n_cell", C.c_int64),
+                ("cell_vert", C.c_void_p), ("n_bface", C.c_int64), ("bface_vert", C.c_void_p),
+                ("bface_tag", C.c_void_p), ("bcsets", C.POINTER(fvgb_bcset))]
 
 
 class fvgb_tcoef(C.Structure):
@@ -83,6 +90,10 @@ _vp, _i32, _i64, _d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
 _sig = {
     "fvgb_mesh_upload": (C.c_int, [_i32, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _i32,
                                    C.POINTER(fvgb_bcset), _i32, _i32, _vp, C.POINTER(_vp)]),
+    "fvgb_mesh_upload_ensemble": (C.c_int, [_i32, _i32, C.POINTER(fvgb_mesh_part), _i32, _i32, _i32,
+                                            _vp, C.POINTER(_vp)]),
+    "fvgb_mesh_parts": (C.c_int, [_vp, C.POINTER(_i32), _vp]),
+    "fvgb_solve_parts": (C.c_int, [_vp, _vp, _vp, _vp]),
     "fvgb_mesh_free": (C.c_int, [_vp]),
     "fvgb_mesh_info": (C.c_int, [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64),
                                  C.POINTER(_i64)]),
@@ -100,6 +111,7 @@ _sig = {
                                      C.POINTER(fvgb_solve_info), _vp]),
     "fvgb_streamer_step": (C.c_int, [_vp, C.POINTER(fvgb_streamer_params), _vp, _vp, _vp, _vp,
                                      _i32, C.POINTER(fvgb_solve_info), _vp]),
+    "fvgb_integral": (C.c_int, [_vp, _vp, C.POINTER(_d), _vp]),
     "fvgb_stats_enable": (C.c_int, [_vp, _i32]),
     "fvgb_stats_get": (C.c_int, [_vp, C.POINTER(fvgb_stats), _i32]),
     "fvgb_last_error": (C.c_char_p, []),
@@ -168,6 +180,59 @@ def fvgb_mesh_upload(dim, xyz, cell_vert, bface_vert, bface_tag, bcsets, reorder
                                 sets, reorder, prec, stream_handle(stream), C.byref(out)),
            "fvgb_mesh_upload")
     return out.value
+
+
+def _bcset_array(bcsets, keep):
+    sets = (fvgb_bcset * len(bcsets))()
+    for k, bc in enumerate(bcsets):
+        arr = (fvgb_bc * len(bc))()
+        for j, (tag, (kind, value)) in enumerate(sorted(bc.items())):
+            arr[j] = fvgb_bc(int(tag), int(kind), float(value))
+        keep.append(arr)
+        sets[k] = fvgb_bcset(len(bc), C.cast(arr, C.POINTER(fvgb_bc)))
+    keep.append(sets)
+    return sets
+
+
+def fvgb_mesh_upload_ensemble(dim, meshes, bcsets_per_mesh, reorder=2, prec=FVGB_FP64, stream=None):
+    """Upload several independent meshes as one; meshes are objects with xyz, cells,
+    bface_vert, bface_tag (numpy), bcsets_per_mesh a list (per mesh) of lists of
+    {tag: (kind, value)}. Returns the handle."""
+    import numpy as np
+    keep = []
+    parts = (fvgb_mesh_part * len(meshes))()
+    for p, (msh, bcs) in enumerate(zip(meshes, bcsets_per_mesh)):
+        xyz = np.ascontiguousarray(msh.xyz, dtype=np.float64)
+        cv = np.ascontiguousarray(msh.cells, dtype=np.int32)
+        bv = np.ascontiguousarray(msh.bface_vert, dtype=np.int32)
+        bt = np.ascontiguousarray(msh.bface_tag, dtype=np.int32)
+        keep += [xyz, cv, bv, bt]
+        sets = _bcset_array(bcs, keep)
+        parts[p] = fvgb_mesh_part(xyz.shape[0], ptr(xyz), cv.shape[0], ptr(cv), bv.shape[0], ptr(bv),
+                                  ptr(bt), C.cast(sets, C.POINTER(fvgb_bcset)))
+    out = _vp()
+    _check(lib.fvgb_mesh_upload_ensemble(dim, len(meshes), parts, len(bcsets_per_mesh[0]), reorder,
+                                         prec, stream_handle(stream), C.byref(out)),
+           "fvgb_mesh_upload_ensemble")
+    return out.value
+
+
+def fvgb_mesh_parts(m):
+    import numpy as np
+    n = _i32()
+    _check(lib.fvgb_mesh_parts(m, C.byref(n), None), "fvgb_mesh_parts")
+    begin = np.empty(n.value + 1, dtype=np.int64)
+    _check(lib.fvgb_mesh_parts(m, C.byref(n), ptr(begin)), "fvgb_mesh_parts")
+    return n.value, begin
+
+
+def fvgb_solve_parts(m, n_part):
+    import numpy as np
+    rel = np.empty(n_part, dtype=np.float64)
+    outer = np.empty(n_part, dtype=np.int32)
+    inner = np.empty(n_part, dtype=np.int32)
+    _check(lib.fvgb_solve_parts(m, ptr(rel), ptr(outer), ptr(inner)), "fvgb_solve_parts")
+    return rel, outer, inner
 
 
 def fvgb_mesh_free(m):
@@ -269,6 +334,12 @@ def fvgb_streamer_step(m, params, ne, ni, phi, E, nsteps, stream=None):
     _check(lib.fvgb_streamer_step(m, C.byref(params), ptr(ne), ptr(ni), ptr(phi), ptr(E),
                                   int(nsteps), infos, stream_handle(stream)), "fvgb_streamer_step")
     return [infos[i].as_dict() for i in range(nsteps)]
+
+
+def fvgb_integral(m, u, stream=None):
+    out = _d()
+    _check(lib.fvgb_integral(m, ptr(u), C.byref(out), stream_handle(stream)), "fvgb_integral")
+    return out.value
 
 
 def fvgb_stats_enable(m, time_cg=True):

@@ -147,6 +147,49 @@ cudaError_t alloc_work(fvgb_mesh_s* m, Work<T>& w) {
   return cudaSuccess;
 }
 
+// Sub-chunks of the persistent solve: block b owns rows [b N / G, (b+1) N / G), cut at
+// part boundaries; parts are contiguous ranges of internal cells.
+cudaError_t setup_parts(fvgb_mesh_s* m, const std::vector<int64_t>& part_begin, cudaStream_t s) {
+  const int64_t N = m->topo.N;
+  const int G = m->solve_grid;
+  const int P = (int)part_begin.size() - 1;
+  m->part_cell_begin = part_begin;
+  std::vector<int32_t> blk_sc(G + 1, 0), sc_part, part_sc(P + 1, 0);
+  std::vector<int64_t> sc_begin;
+  int p = 0;
+  for (int b = 0; b < G; ++b) {
+    blk_sc[b] = (int32_t)sc_part.size();
+    const int64_t lo = (int64_t)b * N / G, hi = (int64_t)(b + 1) * N / G;
+    int64_t i = lo;
+    while (i < hi) {
+      while (part_begin[p + 1] <= i) ++p;
+      sc_begin.push_back(i);
+      sc_part.push_back(p);
+      i = std::min(hi, part_begin[p + 1]);
+    }
+  }
+  blk_sc[G] = (int32_t)sc_part.size();
+  sc_begin.push_back(N);
+  const int n_sc = (int)sc_part.size();
+  for (int q = 0, sc = 0; q <= P; ++q) {
+    while (sc < n_sc && sc_part[sc] < q) ++sc;
+    part_sc[q] = sc;
+  }
+  PartsDev& pd = m->parts;
+  pd.n_part = P;
+  pd.n_sc = n_sc;
+  cudaError_t e;
+  if ((e = dupload(m, &pd.blk_sc, blk_sc, s))) return e;
+  if ((e = dupload(m, &pd.sc_begin, sc_begin, s))) return e;
+  if ((e = dupload(m, &pd.sc_part, sc_part, s))) return e;
+  if ((e = dupload(m, &pd.part_sc, part_sc, s))) return e;
+  if ((e = dalloc(m, &pd.buf, 4 * (size_t)n_sc))) return e;
+  if ((e = dalloc(m, &pd.active, P))) return e;
+  if ((e = dalloc(m, &pd.out_inner, P))) return e;
+  if ((e = dalloc(m, &pd.norms, P))) return e;
+  return cudaSuccess;
+}
+
 void release(fvgb_mesh_s* m) {
   if (m->ev_cg0) cudaEventDestroy(m->ev_cg0);
   if (m->ev_cg1) cudaEventDestroy(m->ev_cg1);
@@ -222,37 +265,56 @@ fvgb_status poisson_rhs_impl(fvgb_mesh m, int bcset, const double* f, double* b,
   return FVGB_OK;
 }
 
+// Outer FP64 refinement loop, per part: r = b - A phi, stop a part when
+// ||r_p|| <= rtol ||b_p||, otherwise one inner CG solve of A_T delta = r on the parts
+// still active and phi += delta. One host synchronisation per outer step.
 fvgb_status solve_impl(fvgb_mesh m, int bcset, const double* f, double* phi,
                        const fvgb_solve_opts* o, fvgb_solve_info* info, cudaStream_t s) {
   fvgb_solve_info loc{0, 0, 0.0, 0.0};
-  const int64_t N = m->topo.N;
   m->stats.solves++;
+  const int64_t N = m->topo.N;
+  const int P = m->parts.n_part;
+  const bool fp32 = o->prec == FVGB_FP32 || o->prec == FVGB_MIXED;
+  if (fp32 && !is_fp32(m)) { set_error("FP32 inner solve needs a mesh uploaded with FVGB_FP32 or FVGB_MIXED"); return FVGB_EINVAL; }
   double* b = m->dphi_tmp2;
   double* r = m->dphi_tmp;
   fvgb_status st = poisson_rhs_impl(m, bcset, f, b, s);
   if (st) return st;
-  FVGB_TRY(launch_sumsq(m, b, N, m->d_scal + 0, s), "reduction");
-  FVGB_TRY(cudaMemcpyAsync(m->h_scal, m->d_scal, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+  // host staging in pinned memory: [0, P) norms, [P, 2P) ints (active flags, inner its)
+  double* hn = m->h_scal + 8;
+  int* hact = (int*)(m->h_scal + 8 + P);
+  int* hinner = hact + P;
+  int* hst = hinner + P;                    // [0] CG status, [1] CG its, [2] barrier status
+  FVGB_TRY(launch_part_sumsq(m, b, m->parts.norms, s), "norm kernel");
+  FVGB_TRY(cudaMemcpyAsync(hn, m->parts.norms, P * sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
   FVGB_TRY(cudaStreamSynchronize(s), "synchronize");
-  const double bnorm = std::sqrt(m->h_scal[0]);
-  loc.bnorm = bnorm;
-  if (!std::isfinite(bnorm)) { set_error("non-finite right-hand side"); if (info) *info = loc; return FVGB_ENONFINITE; }
-  if (bnorm == 0.0) {
-    FVGB_TRY(cudaMemsetAsync(phi, 0, N * sizeof(double), s), "memset");
-    if (info) *info = loc;
-    return FVGB_OK;
+  std::vector<double> bn2(hn, hn + P);
+  double bsum = 0.0;
+  bool any_zero = false;
+  for (int p = 0; p < P; ++p) {
+    bsum += bn2[p];
+    if (!std::isfinite(bn2[p])) { set_error("non-finite right-hand side"); if (info) *info = loc; return FVGB_ENONFINITE; }
+    if (bn2[p] == 0.0) any_zero = true;
   }
-  const bool fp32 = o->prec == FVGB_FP32 || o->prec == FVGB_MIXED;
-  if (fp32 && !is_fp32(m)) { set_error("FP32 inner solve needs a mesh uploaded with FVGB_FP32 or FVGB_MIXED"); return FVGB_EINVAL; }
-  int* hinfo = (int*)(m->h_scal + 4);
+  loc.bnorm = std::sqrt(bsum);
+  if (any_zero) {   // a part with b = 0 has the solution 0
+    for (int p = 0; p < P; ++p)
+      if (bn2[p] == 0.0)
+        FVGB_TRY(cudaMemsetAsync(phi + m->part_cell_begin[p], 0,
+                                 (m->part_cell_begin[p + 1] - m->part_cell_begin[p]) * sizeof(double), s), "memset");
+  }
+  m->last_outer.assign(P, 0);
+  m->last_inner.assign(P, 0);
+  m->last_rel.assign(P, 0.0);
   for (int outer = 0;; ++outer) {
     st = poisson_residual(m, bcset, phi, b, r, s);
     if (st) return st;
-    FVGB_TRY(launch_sumsq(m, r, N, m->d_scal + 0, s), "reduction");
-    FVGB_TRY(cudaMemcpyAsync(m->h_scal, m->d_scal, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+    FVGB_TRY(launch_part_sumsq(m, r, m->parts.norms, s), "norm kernel");
+    FVGB_TRY(cudaMemcpyAsync(hn, m->parts.norms, P * sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
     if (outer > 0) {
-      FVGB_TRY(cudaMemcpyAsync(hinfo, m->d_cg_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
-      FVGB_TRY(cudaMemcpyAsync(hinfo + 2, &m->barrier->status, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+      FVGB_TRY(cudaMemcpyAsync(hinner, m->parts.out_inner, P * sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+      FVGB_TRY(cudaMemcpyAsync(hst, m->d_cg_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+      FVGB_TRY(cudaMemcpyAsync(hst + 2, &m->barrier->status, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
     }
     FVGB_TRY(cudaStreamSynchronize(s), "synchronize");
     if (m->cg_pending) {
@@ -261,21 +323,36 @@ fvgb_status solve_impl(fvgb_mesh m, int bcset, const double* f, double* phi,
       m->cg_pending = false;
     }
     if (outer > 0) {
-      loc.inner_its_total += hinfo[0];
-      m->stats.cg_iterations += hinfo[0];
-      if (hinfo[2] != 0) { set_error("grid barrier of the CG kernel timed out"); if (info) *info = loc; return FVGB_ETIMEOUT; }
-      if (hinfo[1] != 0) { set_error("CG breakdown or non-finite value"); if (info) *info = loc; return FVGB_ENONFINITE; }
+      m->stats.cg_iterations += hst[1];
+      int mx = 0;
+      for (int p = 0; p < P; ++p) {
+        m->last_inner[p] += hinner[p];
+        mx = std::max(mx, m->last_inner[p]);
+      }
+      loc.inner_its_total = mx;
+      if (hst[2] != 0) { set_error("a grid barrier of the CG kernel timed out"); if (info) *info = loc; return FVGB_ETIMEOUT; }
+      if (hst[0] != 0) { set_error("CG breakdown or non-finite value"); if (info) *info = loc; return FVGB_ENONFINITE; }
     }
-    loc.rel_res = std::sqrt(m->h_scal[0]) / bnorm;
+    int n_active = 0;
+    loc.rel_res = 0.0;
+    for (int p = 0; p < P; ++p) {
+      const double rel = bn2[p] > 0.0 ? std::sqrt(hn[p] / bn2[p]) : 0.0;
+      if (!std::isfinite(rel)) { set_error("non-finite residual"); if (info) *info = loc; return FVGB_ENONFINITE; }
+      m->last_rel[p] = rel;
+      loc.rel_res = std::max(loc.rel_res, rel);
+      hact[p] = rel > o->rtol ? 1 : 0;
+      n_active += hact[p];
+    }
     loc.outer_its = outer;
-    if (outer > 0) m->stats.outer_its++;
-    if (!std::isfinite(loc.rel_res)) { set_error("non-finite residual"); if (info) *info = loc; return FVGB_ENONFINITE; }
-    if (loc.rel_res <= o->rtol) break;
+    if (n_active == 0) break;
     if (outer >= o->maxit_outer) {
       set_error("Poisson refinement did not reach rtol within maxit_outer");
       if (info) *info = loc;
       return FVGB_ENOCONV;
     }
+    for (int p = 0; p < P; ++p) m->last_outer[p] += hact[p];
+    m->stats.outer_its++;
+    FVGB_TRY(cudaMemcpyAsync(m->parts.active, hact, P * sizeof(int), cudaMemcpyHostToDevice, s), "copy");
     if (m->time_cg) FVGB_TRY(cudaEventRecord(m->ev_cg0, s), "event");
     if (fp32) FVGB_TRY(launch_cg<float>(m, bcset, r, o->inner_rtol, o->maxit_inner, s), "CG launch");
     else FVGB_TRY(launch_cg<double>(m, bcset, r, o->inner_rtol, o->maxit_inner, s), "CG launch");
@@ -305,6 +382,12 @@ extern "C" {
 
 const char* fvgb_last_error(void) { return g_last_error.c_str(); }
 
+static fvgb_status upload_impl(int32_t dim, int64_t n_vert, const double* xyz, int64_t n_cell,
+                               const int32_t* cell_vert, int64_t n_bface, const int32_t* bface_vert,
+                               const int32_t* bface_tag, const std::vector<std::vector<BCInput>>& sets,
+                               int32_t reorder, int32_t prec, void* stream, fvgb_mesh* out,
+                               const int32_t* cell_part, int n_part);
+
 fvgb_status fvgb_mesh_upload(int32_t dim, int64_t n_vert, const double* xyz, int64_t n_cell,
                              const int32_t* cell_vert, int64_t n_bface, const int32_t* bface_vert,
                              const int32_t* bface_tag, int32_t n_bcset, const fvgb_bcset* bcsets,
@@ -320,10 +403,78 @@ fvgb_status fvgb_mesh_upload(int32_t dim, int64_t n_vert, const double* xyz, int
     for (int j = 0; j < bcsets[k].n_bc; ++j)
       sets[k].push_back(BCInput{bcsets[k].bc[j].tag, bcsets[k].bc[j].kind, bcsets[k].bc[j].value});
   }
+  return upload_impl(dim, n_vert, xyz, n_cell, cell_vert, n_bface, bface_vert, bface_tag, sets,
+                     reorder, prec, stream, out, nullptr, 1);
+}
+
+fvgb_status fvgb_mesh_upload_ensemble(int32_t dim, int32_t n_part, const fvgb_mesh_part* parts,
+                                      int32_t n_bcset, int32_t reorder, int32_t prec,
+                                      void* stream, fvgb_mesh* out) {
+  set_error("");
+  if (!out) { set_error("out is null"); return FVGB_EINVAL; }
+  *out = nullptr;
+  if (n_part < 1 || n_part > kMaxParts || !parts) { set_error("n_part must be in [1, 128]"); return FVGB_EINVAL; }
+  if (n_bcset < 1) { set_error("at least one boundary-condition set is required"); return FVGB_EINVAL; }
+  if (dim != 2 && dim != 3) { set_error("dim must be 2 or 3"); return FVGB_EINVAL; }
+  constexpr int32_t kTagStride = 65536;
+  int64_t nv = 0, nc = 0, nb = 0;
+  for (int p = 0; p < n_part; ++p) {
+    const fvgb_mesh_part& q = parts[p];
+    if (q.n_vert <= 0 || q.n_cell <= 0 || q.n_bface <= 0 || !q.xyz || !q.cell_vert || !q.bface_vert ||
+        !q.bface_tag || !q.bcsets) {
+      set_error("part " + std::to_string(p) + ": empty mesh or null array");
+      return FVGB_EINVAL;
+    }
+    nv += q.n_vert; nc += q.n_cell; nb += q.n_bface;
+  }
+  if (nv > (int64_t)INT32_MAX || nc > (int64_t)INT32_MAX / 4) { set_error("ensemble too large for int32 indices"); return FVGB_EINVAL; }
+  std::vector<double> xyz((size_t)nv * dim);
+  std::vector<int32_t> cv((size_t)nc * (dim + 1)), bfv((size_t)nb * dim), bft(nb), cpart(nc);
+  std::vector<std::vector<BCInput>> sets(n_bcset);
+  int64_t ov = 0, oc = 0, ob = 0;
+  for (int p = 0; p < n_part; ++p) {
+    const fvgb_mesh_part& q = parts[p];
+    std::copy(q.xyz, q.xyz + q.n_vert * dim, xyz.begin() + ov * dim);
+    for (int64_t i = 0; i < q.n_cell * (dim + 1); ++i) {
+      const int32_t v = q.cell_vert[i];
+      if (v < 0 || v >= q.n_vert) { set_error("part " + std::to_string(p) + ": cell vertex index out of range"); return FVGB_EMESH; }
+      cv[oc * (dim + 1) + i] = (int32_t)(v + ov);
+    }
+    for (int64_t i = 0; i < q.n_cell; ++i) cpart[oc + i] = p;
+    for (int64_t i = 0; i < q.n_bface * dim; ++i) {
+      const int32_t v = q.bface_vert[i];
+      if (v < 0 || v >= q.n_vert) { set_error("part " + std::to_string(p) + ": boundary vertex index out of range"); return FVGB_EMESH; }
+      bfv[ob * dim + i] = (int32_t)(v + ov);
+    }
+    for (int64_t i = 0; i < q.n_bface; ++i) {
+      const int32_t t = q.bface_tag[i];
+      if (t <= 0 || t >= kTagStride) { set_error("part " + std::to_string(p) + ": boundary tags must be in [1, 65535]"); return FVGB_EMESH; }
+      bft[ob + i] = p * kTagStride + t;
+    }
+    for (int k = 0; k < n_bcset; ++k) {
+      const fvgb_bcset& bs = q.bcsets[k];
+      if (bs.n_bc < 0 || (bs.n_bc > 0 && !bs.bc)) { set_error("bad bcset"); return FVGB_EINVAL; }
+      for (int j = 0; j < bs.n_bc; ++j) {
+        if (bs.bc[j].tag <= 0 || bs.bc[j].tag >= kTagStride) { set_error("bc tags must be in [1, 65535]"); return FVGB_EINVAL; }
+        sets[k].push_back(BCInput{p * kTagStride + bs.bc[j].tag, bs.bc[j].kind, bs.bc[j].value});
+      }
+    }
+    ov += q.n_vert; oc += q.n_cell; ob += q.n_bface;
+  }
+  return upload_impl(dim, nv, xyz.data(), nc, cv.data(), nb, bfv.data(), bft.data(), sets, reorder,
+                     prec, stream, out, cpart.data(), n_part);
+}
+
+static fvgb_status upload_impl(int32_t dim, int64_t n_vert, const double* xyz, int64_t n_cell,
+                               const int32_t* cell_vert, int64_t n_bface, const int32_t* bface_vert,
+                               const int32_t* bface_tag, const std::vector<std::vector<BCInput>>& sets,
+                               int32_t reorder, int32_t prec, void* stream, fvgb_mesh* out,
+                               const int32_t* cell_part, int n_part) {
+  if (prec != FVGB_FP64 && prec != FVGB_FP32 && prec != FVGB_MIXED) { set_error("bad precision"); return FVGB_EINVAL; }
   HostMesh h;
   std::string err;
   int rc = build_host_mesh(dim, n_vert, xyz, n_cell, cell_vert, n_bface, bface_vert, bface_tag,
-                           sets, reorder, h, err);
+                           sets, reorder, h, err, cell_part, n_part);
   if (rc) { set_error(err); return (fvgb_status)rc; }
 
   cudaStream_t s = (cudaStream_t)stream;
@@ -369,15 +520,14 @@ fvgb_status fvgb_mesh_upload(int32_t dim, int64_t n_vert, const double* xyz, int
   if ((e = cudaMemsetAsync(m->dzero, 0, h.N * sizeof(double), s))) return fail(e, "memset");
   if ((e = dalloc(m, &m->barrier, 1))) return fail(e, "allocation");
   if ((e = dalloc(m, &m->d_cg_info, 4))) return fail(e, "allocation");
-  if ((e = cudaMallocHost((void**)&m->h_scal, 64 * sizeof(double)))) return fail(e, "pinned allocation");
-  m->cg_grid64 = cg_grid_size(m, false);
-  m->cg_grid32 = prec != FVGB_FP64 ? cg_grid_size(m, true) : 0;
-  if (m->cg_grid64 <= 0 || (prec != FVGB_FP64 && m->cg_grid32 <= 0)) {
+  if ((e = cudaMallocHost((void**)&m->h_scal, (16 + 4 * kMaxParts) * sizeof(double)))) return fail(e, "pinned allocation");
+  m->solve_grid = solve_grid_size(m);
+  if (m->solve_grid <= 0) {
     set_error("this device cannot run the library's kernels (built for sm_103a)");
     release(m);
     return FVGB_EUNSUPPORTED;
   }
-  if (m->cg_grid64 > 8 * 1024 || m->cg_grid32 > 8 * 1024) { set_error("too many SMs"); release(m); return FVGB_EUNSUPPORTED; }
+  if ((e = setup_parts(m, h.part_cell_begin, s))) return fail(e, "parts setup");
   if ((e = cudaStreamSynchronize(s))) return fail(e, "synchronize");
   *out = m;
   return FVGB_OK;
@@ -387,6 +537,17 @@ fvgb_status fvgb_mesh_free(fvgb_mesh m) {
   if (!m) return FVGB_OK;
   cudaDeviceSynchronize();
   release(m);
+  return FVGB_OK;
+}
+
+fvgb_status fvgb_integral(fvgb_mesh m, const void* u, double* out, void* stream) {
+  if (fvgb_status st = check_mesh(m)) return st;
+  if (!u || !out) { set_error("null argument"); return FVGB_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  FVGB_TRY(launch_integral(m, u, is_fp32(m), m->d_scal + 1, s), "integral kernel");
+  FVGB_TRY(cudaMemcpyAsync(m->h_scal + 1, m->d_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+  FVGB_TRY(cudaStreamSynchronize(s), "synchronize");
+  *out = m->h_scal[1];
   return FVGB_OK;
 }
 
@@ -419,6 +580,23 @@ fvgb_status fvgb_mesh_info(fvgb_mesh m, int64_t* n_cell, int64_t* n_face, int64_
   if (n_face) *n_face = m->topo.F;
   if (n_vert) *n_vert = m->topo.V;
   if (n_nbr) *n_nbr = m->topo.n_nbr;
+  return FVGB_OK;
+}
+
+fvgb_status fvgb_mesh_parts(fvgb_mesh m, int32_t* n_part, int64_t* cell_begin) {
+  if (fvgb_status st = check_mesh(m)) return st;
+  if (n_part) *n_part = m->parts.n_part;
+  if (cell_begin) std::copy(m->part_cell_begin.begin(), m->part_cell_begin.end(), cell_begin);
+  return FVGB_OK;
+}
+
+fvgb_status fvgb_solve_parts(fvgb_mesh m, double* rel_res, int32_t* outer_its, int32_t* inner_its) {
+  if (fvgb_status st = check_mesh(m)) return st;
+  const size_t P = (size_t)m->parts.n_part;
+  if (m->last_rel.size() != P) { set_error("no solve has run on this mesh"); return FVGB_EINVAL; }
+  if (rel_res) std::copy(m->last_rel.begin(), m->last_rel.end(), rel_res);
+  if (outer_its) std::copy(m->last_outer.begin(), m->last_outer.end(), outer_its);
+  if (inner_its) std::copy(m->last_inner.begin(), m->last_inner.end(), inner_its);
   return FVGB_OK;
 }
 

@@ -76,6 +76,22 @@ struct Work {
   T* cg_x = nullptr;
 };
 
+// Parts of a mesh (an ensemble of independent meshes packed into one index space) and
+// the sub-chunks of the persistent solve: block b owns rows [b N / G, (b+1) N / G) cut at
+// part boundaries.
+struct PartsDev {
+  int n_part = 1;
+  int n_sc = 0;
+  int32_t* blk_sc = nullptr;    // [G+1] first sub-chunk of each block
+  int64_t* sc_begin = nullptr;  // [n_sc+1] first row of each sub-chunk
+  int32_t* sc_part = nullptr;   // [n_sc] part of each sub-chunk
+  int32_t* part_sc = nullptr;   // [P+1] first sub-chunk of each part
+  double* buf = nullptr;        // [2][2][n_sc] partial sums
+  int* active = nullptr;        // [P] parts the inner solve works on
+  int* out_inner = nullptr;     // [P] inner iterations of the last CG launch
+  double* norms = nullptr;      // [P] per-part sums of squares
+};
+
 struct Barrier {
   unsigned int count;
   unsigned int gen;
@@ -103,7 +119,11 @@ struct fvgb_mesh_s {
   double* dzero = nullptr;              // [N] zeros
   fvgb::Barrier* barrier = nullptr;
   int* d_cg_info = nullptr;             // [4] iterations, status
-  int cg_grid64 = 0, cg_grid32 = 0;     // cooperative grid sizes
+  int solve_grid = 0;                   // cooperative grid of the Poisson kernel
+  fvgb::PartsDev parts;
+  std::vector<int64_t> part_cell_begin; // [P+1] internal cell range of each part
+  std::vector<int32_t> last_outer, last_inner;  // per-part results of the last solve
+  std::vector<double> last_rel;
   fvgb_stats stats{};                   // counters (kernel_launches is library-wide)
   int time_cg = 0;                      // record CUDA events around CG launches
   cudaEvent_t ev_cg0 = nullptr, ev_cg1 = nullptr;
@@ -127,7 +147,8 @@ template <>
 inline Work<float>& work_of<float>(fvgb_mesh_s* m) { return m->w32; }
 
 constexpr int kRedBlocks = 1024;   // fixed grid of the deterministic reductions
-constexpr int kCgThreads = 512;    // threads per block of the persistent CG kernel
+constexpr int kCgThreads = 512;    // threads per block of the persistent Poisson kernel
+constexpr int kMaxParts = 128;     // parts of an ensemble mesh handled by one solve
 
 extern std::atomic<long long> g_kernel_launches;
 inline void count_launch(int n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -155,6 +176,7 @@ cudaError_t launch_cell_physics(fvgb_mesh_s* m, const T* grad, const T* ne, doub
 cudaError_t launch_poisson_source(fvgb_mesh_s* m, const void* ne, const void* ni, bool fp32,
                                   double* f, cudaStream_t s);
 cudaError_t launch_sumsq(fvgb_mesh_s* m, const double* x, int64_t n, double* out, cudaStream_t s);
+cudaError_t launch_integral(fvgb_mesh_s* m, const void* u, bool fp32, double* out, cudaStream_t s);
 cudaError_t launch_axpy_d(const double* x, double a, double* y, int64_t n, cudaStream_t s);
 cudaError_t launch_add_to_double(const void* x, bool fp32, double* y, int64_t n, cudaStream_t s);
 cudaError_t launch_convert(const double* x, float* y, int64_t n, cudaStream_t s);
@@ -164,9 +186,10 @@ cudaError_t launch_permute(const void* src, void* dst, const int32_t* perm, int6
 cudaError_t launch_nonfinite_check(const double* x, int64_t n, int* flag, cudaStream_t s);
 
 // solver.cu ----------------------------------------------------------------------------
-int cg_grid_size(fvgb_mesh_s* m, bool fp32);
+int solve_grid_size(fvgb_mesh_s* m);
 template <typename T>
-cudaError_t launch_cg(fvgb_mesh_s* m, int bcset, const double* rhs, double rtol, int maxit,
+cudaError_t launch_cg(fvgb_mesh_s* m, int bcset, const double* r, double inner_rtol, int maxit,
                       cudaStream_t s);
+cudaError_t launch_part_sumsq(fvgb_mesh_s* m, const double* v, double* out, cudaStream_t s);
 
 }  // namespace fvgb

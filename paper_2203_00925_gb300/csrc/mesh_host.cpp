@@ -114,7 +114,7 @@ int build_host_mesh(int dim, int64_t n_vert, const double* xyz_in, int64_t n_cel
                     const int32_t* cell_vert, int64_t n_bface, const int32_t* bface_vert,
                     const int32_t* bface_tag,
                     const std::vector<std::vector<BCInput>>& bcsets, int reorder,
-                    HostMesh& m, std::string& err) {
+                    HostMesh& m, std::string& err, const int32_t* cell_part, int n_part) {
   if (dim != 2 && dim != 3) { err = "dim must be 2 or 3"; return kEINVAL; }
   if (n_vert <= 0 || n_cell <= 0 || n_bface <= 0 || !xyz_in || !cell_vert || !bface_vert ||
       !bface_tag) {
@@ -157,15 +157,30 @@ int build_host_mesh(int dim, int64_t n_vert, const double* xyz_in, int64_t n_cel
   }
   if (bad >= 0) { err = "cell " + std::to_string(bad) + " has non-positive orientation"; return kEMESH; }
 
+  // ---- parts (independent meshes packed together) -------------------------------------
+  if (n_part < 1) { err = "n_part must be >= 1"; return kEINVAL; }
+  std::vector<int32_t> part(N, 0);
+  if (cell_part) {
+    for (int64_t c = 0; c < N; ++c) {
+      if (cell_part[c] < 0 || cell_part[c] >= n_part) { err = "cell part id out of range"; return kEINVAL; }
+      part[c] = cell_part[c];
+      if (reorder == 0 && c > 0 && part[c] < part[c - 1]) {
+        err = "without reordering the parts must be contiguous and in order";
+        return kEINVAL;
+      }
+    }
+  }
+
   // ---- cell order ---------------------------------------------------------------------
   m.cell_perm.resize(N);
   std::iota(m.cell_perm.begin(), m.cell_perm.end(), 0);
   if (reorder == 2) {
-    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    // Morton key of the centre inside the bounding box of its part's centres
+    std::vector<double> lo((size_t)n_part * 3, 1e300), hi((size_t)n_part * 3, -1e300);
     for (int64_t c = 0; c < N; ++c)
       for (int a = 0; a < d; ++a) {
-        lo[a] = std::min(lo[a], ucen[c * d + a]);
-        hi[a] = std::max(hi[a], ucen[c * d + a]);
+        lo[part[c] * 3 + a] = std::min(lo[part[c] * 3 + a], ucen[c * d + a]);
+        hi[part[c] * 3 + a] = std::max(hi[part[c] * 3 + a], ucen[c * d + a]);
       }
     std::vector<uint64_t> key(N);
     const double levels = d == 3 ? 2097151.0 : 4294967295.0;
@@ -173,14 +188,23 @@ int build_host_mesh(int dim, int64_t n_vert, const double* xyz_in, int64_t n_cel
     for (int64_t c = 0; c < N; ++c) {
       uint64_t k = 0;
       for (int a = 0; a < d; ++a) {
-        double span = hi[a] > lo[a] ? hi[a] - lo[a] : 1.0;
-        uint64_t q = (uint64_t)std::llround((ucen[c * d + a] - lo[a]) / span * levels);
+        const double l = lo[part[c] * 3 + a], h = hi[part[c] * 3 + a];
+        double span = h > l ? h - l : 1.0;
+        uint64_t q = (uint64_t)std::llround((ucen[c * d + a] - l) / span * levels);
         k |= (d == 3 ? spread3(q) : spread2(q)) << a;
       }
       key[c] = k;
     }
-    std::stable_sort(m.cell_perm.begin(), m.cell_perm.end(),
-                     [&](int32_t x, int32_t y) { return key[x] < key[y]; });
+    std::stable_sort(m.cell_perm.begin(), m.cell_perm.end(), [&](int32_t x, int32_t y) {
+      if (part[x] != part[y]) return part[x] < part[y];
+      return key[x] < key[y];
+    });
+  }
+  m.part_cell_begin.assign(n_part + 1, 0);
+  for (int64_t c = 0; c < N; ++c) m.part_cell_begin[part[c] + 1]++;
+  for (int q = 0; q < n_part; ++q) {
+    if (m.part_cell_begin[q + 1] == 0) { err = "part " + std::to_string(q) + " has no cells"; return kEINVAL; }
+    m.part_cell_begin[q + 1] += m.part_cell_begin[q];
   }
 
   // ---- vertex order: first touch in the new cell order --------------------------------

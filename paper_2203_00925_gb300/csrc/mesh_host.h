@@ -42,6 +42,7 @@ struct HostMesh {
   std::vector<int32_t> vptr, vcell;     // cells around each vertex (CSR, sorted)
   std::vector<double> valpha;           // LS interpolation weight of each (vertex, cell)
   std::vector<BCSetHost> bcs;
+  std::vector<int64_t> part_cell_begin; // [P+1] internal cell range of each part
 };
 
 struct BCInput {
@@ -55,6 +56,7 @@ int build_host_mesh(int dim, int64_t n_vert, const double* xyz, int64_t n_cell,
                     const int32_t* cell_vert, int64_t n_bface, const int32_t* bface_vert,
                     const int32_t* bface_tag,
                     const std::vector<std::vector<BCInput>>& bcsets, int reorder,
-                    HostMesh& out, std::string& err);
+                    HostMesh& out, std::string& err, const int32_t* cell_part = nullptr,
+                    int n_part = 1);
 
 }  // namespace fvgb

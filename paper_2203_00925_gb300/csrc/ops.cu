@@ -240,6 +240,19 @@ __global__ void __launch_bounds__(256) k_sumsq_partial(const double* __restrict_
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_wsum_partial(const T* __restrict__ u,
+                                                      const double* __restrict__ vol, int64_t n,
+                                                      double* __restrict__ part) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += vol[i] * (double)u[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
 __global__ void __launch_bounds__(1024) k_sum_final(const double* __restrict__ part, int n,
                                                     double* __restrict__ out) {
   __shared__ double sh[32];
@@ -389,6 +402,15 @@ cudaError_t launch_poisson_source(fvgb_mesh_s* m, const void* ne, const void* ni
 
 cudaError_t launch_sumsq(fvgb_mesh_s* m, const double* x, int64_t n, double* out, cudaStream_t s) {
   k_sumsq_partial<<<kRedBlocks, 256, 0, s>>>(x, n, m->d_scal + 8);
+  k_sum_final<<<1, 1024, 0, s>>>(m->d_scal + 8, kRedBlocks, out);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_integral(fvgb_mesh_s* m, const void* u, bool fp32, double* out, cudaStream_t s) {
+  const int64_t n = m->topo.N;
+  if (fp32) k_wsum_partial<float><<<kRedBlocks, 256, 0, s>>>((const float*)u, m->g64.vol, n, m->d_scal + 8);
+  else k_wsum_partial<double><<<kRedBlocks, 256, 0, s>>>((const double*)u, m->g64.vol, n, m->d_scal + 8);
   k_sum_final<<<1, 1024, 0, s>>>(m->d_scal + 8, kRedBlocks, out);
   count_launch(2);
   return cudaGetLastError();

@@ -1,14 +1,20 @@
-// Inner conjugate-gradient solve of the Poisson refinement loop: A_T delta = r on the
-// symmetric positive definite two-point part A_T of the diamond operator (eq.
-// "laplace" keeps, per face, the term |S_f|^2 / ((x_R - x_L) . S_f) (P_R - P_L)).
+// Inner solve of the Poisson refinement loop (eq. 1.1 discretised by eq. 7 /
+// eq. "laplace"): conjugate gradients on the SPD two-point part A_T of the diamond
+// operator (per face the term |S_f|^2 / ((x_R - x_L) . S_f) (P_R - P_L)), A_T delta = r,
+// in T = float or double with FP64 dot products, as ONE persistent cooperative kernel.
 //
-// One persistent cooperative launch runs the whole CG loop: each block owns a
-// contiguous range of cells, vectors are in T (float or double), every dot product is
-// accumulated in FP64 and reduced in a fixed order (block partials -> every block sums
-// all partials in the same order), so all blocks take the same decisions and the
-// result is bitwise reproducible for a given grid size. Grid-wide barriers are
-// bounded: a barrier that waits longer than one second sets a status word and every
-// block leaves the loop; the host reports FVGB_ETIMEOUT.
+// A mesh may hold several independent parts (an ensemble of meshes packed into one
+// index space); every part has its own CG scalars and stopping test, and only the parts
+// flagged active by the outer loop are solved (delta = 0 elsewhere).
+//
+// Work split: block b owns the contiguous cell range [b N / G, (b+1) N / G), cut at part
+// boundaries into "sub-chunks" (one part each). Every sum is formed per sub-chunk (block
+// tree), then per part over its sub-chunks in a fixed order by every block, so all
+// blocks take the same decisions and results are bitwise reproducible for a given grid.
+// The same decomposition gives the per-part norms of the outer loop (k_part_sumsq).
+//
+// Grid-wide barriers are bounded: a wait longer than one second sets a status word and
+// every block leaves; the host reports FVGB_ETIMEOUT.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -24,8 +30,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Sense-by-generation grid barrier with a bounded wait. Returns false when any block
-// gave up (status set), in which case the caller leaves its loop.
+// Grid barrier by generation count with a bounded wait. Returns false when any block
+// gave up (status set), in which case the caller leaves.
 __device__ bool grid_barrier(Barrier* bar, unsigned nblocks) {
   __shared__ int ok;
   __syncthreads();
@@ -56,8 +62,7 @@ __device__ bool grid_barrier(Barrier* bar, unsigned nblocks) {
   return ok != 0;
 }
 
-// Block-wide FP64 sum in a fixed order: a shared-memory tree over the block's threads,
-// finished by warp 0. Few FP64 instructions per thread (GB300's FP64 rate is low).
+// Block-wide FP64 sum in a fixed order (shared-memory tree, finished by warp 0).
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   sh[threadIdx.x] = v;
   __syncthreads();
@@ -70,57 +75,55 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     t = sh[threadIdx.x];
     for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
   }
+  __syncthreads();
   return t;  // valid in thread 0
 }
 
-// Grid-wide FP64 sums of K values in a fixed order (block tree, then warp 0 of every
-// block sums the block partials in the same order); ``part`` alternates between two
-// halves so that a fast block never overwrites partials a slow block is still reading.
-// Returns false when the grid barrier gave up. The sums land in out (shared memory).
-template <int K>
-__device__ bool grid_sum(const double (&v)[K], double* part, int parity, Barrier* bar,
-                         double* sh, double* out) {
-  static_assert(K <= 2, "at most two sums per reduction");
-  const unsigned nb = gridDim.x;
-  double* base = part + (size_t)parity * nb * 2;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const double t = block_sum(v[k], sh);
-    if (threadIdx.x == 0) base[k * nb + blockIdx.x] = t;
-    __syncthreads();
-  }
-  if (!grid_barrier(bar, nb)) return false;
-  if (threadIdx.x < 32) {
+template <typename T>
+struct SolveArgs {
+  int64_t N;
+  // two-point operator in T, cell-major [N][4]
+  const int32_t* at_nbr;
+  const T* at_coef;
+  const T* at_diag;
+  const double* r_in;       // [N] right-hand side (FP64 outer residual)
+  T* cx;
+  T* cr;
+  T* cp;
+  T* cq;
+  // parts
+  int n_part;
+  int n_sc;
+  const int32_t* blk_sc;    // [G+1]
+  const int64_t* sc_begin;  // [n_sc+1]
+  const int32_t* sc_part;   // [n_sc]
+  const int32_t* part_sc;   // [P+1]
+  const int* active;        // [P] parts to solve
+  double* buf;              // [2][2][n_sc] partial sums
+  Barrier* bar;
+  double inner_tol2;
+  int maxit_inner;
+  int* out_inner;           // [P] iterations per part
+  int* out_status;          // [0]: 0 ok, 6 non-finite / breakdown; [1]: iterations run
+};
+
+// Sum the per-sub-chunk partials of K quantities into per-part totals (shared memory
+// tot[k * P + p]), every part in sub-chunk order. Call after a grid barrier.
+template <typename T, int K>
+__device__ void part_totals(const SolveArgs<T>& a, const double* buf, double* tot) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int p = warp; p < a.n_part; p += nw) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       double t = 0.0;
-      for (unsigned b = threadIdx.x; b < nb; b += 32) t += __ldcg(base + k * nb + b);
+      for (int sc = a.part_sc[p] + lane; sc < a.part_sc[p + 1]; sc += 32)
+        t += __ldcg(buf + (size_t)k * a.n_sc + sc);
       for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-      if (threadIdx.x == 0) out[k] = t;
+      if (lane == 0) tot[k * a.n_part + p] = t;
     }
   }
   __syncthreads();
-  return true;
 }
-
-template <typename T>
-struct CgArgs {
-  int64_t N;
-  const int32_t* nbr;   // [N][4]
-  const T* coef;        // [N][4]
-  const T* diag;        // [N]
-  const double* rhs;    // [N]
-  T* x;
-  T* r;
-  T* p;
-  T* q;
-  double* part;         // [2][2][grid]
-  Barrier* bar;
-  int* info;            // [0] iterations, [1] 0 ok / 2 non-finite or breakdown
-  double* res;          // [0] rr0, [1] final rr
-  double tol2;
-  int maxit;
-};
 
 // Four operator coefficients of one row, loaded with vector loads.
 template <typename T>
@@ -143,30 +146,30 @@ struct Coef4<double> {
   }
 };
 
-// Rows per thread per trip through a phase: all loads of the trip are issued before any
-// store so that the gathers of several rows are in flight together.
+// Rows per thread per trip: all loads of a trip are issued before any store so that the
+// gathers of several rows are in flight together.
 template <typename T>
 __host__ __device__ constexpr int unroll_rows() { return sizeof(T) == 4 ? 4 : 2; }
 
-// Phase 1: x += alpha p, r -= alpha q (own rows); returns this thread's sum of r^2.
+// CG phase 1 on rows [lo, hi): x += alpha p, r -= alpha q; returns the thread's sum of r^2.
 template <typename T>
-__device__ __forceinline__ T cg_phase_xr(const CgArgs<T>& a, int64_t lo, int64_t hi, T alpha) {
-  T* __restrict__ X = a.x;
-  T* __restrict__ R = a.r;
-  const T* __restrict__ P = a.p;
-  const T* __restrict__ Q = a.q;
-  constexpr int kUnroll = unroll_rows<T>();
+__device__ __forceinline__ T cg_phase_xr(const SolveArgs<T>& a, int64_t lo, int64_t hi, T alpha) {
+  constexpr int U = unroll_rows<T>();
+  T* __restrict__ X = a.cx;
+  T* __restrict__ R = a.cr;
+  const T* __restrict__ P = a.cp;
+  const T* __restrict__ Q = a.cq;
   T acc = T(0);
   const int64_t bd = blockDim.x;
-  for (int64_t b = lo + threadIdx.x; b < hi; b += kUnroll * bd) {
-    T x[kUnroll], p[kUnroll], r[kUnroll], q[kUnroll];
+  for (int64_t b = lo + threadIdx.x; b < hi; b += U * bd) {
+    T x[U], p[U], r[U], q[U];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int64_t i = b + u * bd;
       if (i < hi) { x[u] = X[i]; p[u] = P[i]; r[u] = R[i]; q[u] = Q[i]; }
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int64_t i = b + u * bd;
       if (i < hi) {
         const T rn = r[u] - alpha * q[u];
@@ -179,34 +182,33 @@ __device__ __forceinline__ T cg_phase_xr(const CgArgs<T>& a, int64_t lo, int64_t
   return acc;
 }
 
-// Phase 2: p = r + beta p, q = A_T r + beta q (= A_T p); returns this thread's sum of
-// p.q. Neighbours' r are read through L2 (other blocks wrote them this iteration).
+// CG phase 2 on rows [lo, hi): p = r + beta p, q = A_T r + beta q (= A_T p); returns the
+// thread's sum of p.q. Neighbours' r are read through L2 (other blocks wrote them).
 template <typename T>
-__device__ __forceinline__ T cg_phase_pq(const CgArgs<T>& a, int64_t lo, int64_t hi, T beta,
-                                         const T* v_src) {
-  T* __restrict__ P = a.p;
-  T* __restrict__ Q = a.q;
-  const T* __restrict__ R = v_src;
-  const int4* __restrict__ NB = reinterpret_cast<const int4*>(a.nbr);
-  constexpr int kUnroll = unroll_rows<T>();
+__device__ __forceinline__ T cg_phase_pq(const SolveArgs<T>& a, int64_t lo, int64_t hi, T beta) {
+  constexpr int U = unroll_rows<T>();
+  T* __restrict__ P = a.cp;
+  T* __restrict__ Q = a.cq;
+  const T* __restrict__ R = a.cr;
+  const int4* __restrict__ NB = reinterpret_cast<const int4*>(a.at_nbr);
   T acc = T(0);
   const int64_t bd = blockDim.x;
-  for (int64_t b = lo + threadIdx.x; b < hi; b += kUnroll * bd) {
-    T r[kUnroll], p[kUnroll], q[kUnroll], d[kUnroll], g[kUnroll][4];
-    int4 nb[kUnroll];
-    Coef4<T> c[kUnroll];
+  for (int64_t b = lo + threadIdx.x; b < hi; b += U * bd) {
+    T r[U], p[U], q[U], d[U], g[U][4];
+    int4 nb[U];
+    Coef4<T> c[U];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int64_t i = b + u * bd;
       if (i < hi) {
         nb[u] = __ldg(NB + i);
         r[u] = R[i]; p[u] = P[i]; q[u] = Q[i];
-        d[u] = __ldg(a.diag + i);
-        c[u].load(a.coef, i);
+        d[u] = __ldg(a.at_diag + i);
+        c[u].load(a.at_coef, i);
       }
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int64_t i = b + u * bd;
       if (i < hi) {
         g[u][0] = __ldcg(R + nb[u].x);
@@ -216,7 +218,7 @@ __device__ __forceinline__ T cg_phase_pq(const CgArgs<T>& a, int64_t lo, int64_t
       }
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int64_t i = b + u * bd;
       if (i < hi) {
         T y = d[u] * r[u];
@@ -235,137 +237,194 @@ __device__ __forceinline__ T cg_phase_pq(const CgArgs<T>& a, int64_t lo, int64_t
   return acc;
 }
 
-// Conjugate gradients with two grid barriers per iteration: after the residual update
-// (and its norm) every block forms p = r + beta p and q = A_T r + beta q = A_T p from the
-// finished r, so no barrier is needed between the p update and the operator.
-// Dot products: each thread accumulates its own rows in T, the sums across threads and
-// blocks are FP64 in a fixed order. The scalars alpha, beta and the stopping test are
-// computed once per block (thread 0) and broadcast through shared memory.
 template <typename T>
-__global__ void __launch_bounds__(kCgThreads) k_cg(CgArgs<T> a) {
+__global__ void __launch_bounds__(kCgThreads) k_cg(SolveArgs<T> a) {
   __shared__ double sh[kCgThreads];
-  __shared__ double tot[2];
-  __shared__ T s_alpha, s_beta;
-  __shared__ int s_state;   // 0 continue, 1 converged, 2 breakdown / non-finite, 3 zero rhs
-  const int64_t N = a.N;
-  const unsigned nb = gridDim.x;
-  const int64_t chunk = (N + nb - 1) / nb;
-  const int64_t lo = blockIdx.x * chunk;
-  const int64_t hi = lo + chunk < N ? lo + chunk : N;
+  __shared__ double tot[2 * kMaxParts];
+  __shared__ double s_rr[kMaxParts], s_rr0[kMaxParts];
+  __shared__ T s_alpha[kMaxParts], s_beta[kMaxParts];
+  __shared__ int s_cg[kMaxParts];      // 0 running, 1 converged, 2 breakdown, 3 idle
+  __shared__ int s_inner[kMaxParts];
+  __shared__ int s_flag, s_status;
+  const unsigned G = gridDim.x;
+  const int P = a.n_part;
+  const int sc0 = a.blk_sc[blockIdx.x], sc1 = a.blk_sc[blockIdx.x + 1];
   int parity = 0;
-  int its = 0;
-  double rr = 0.0, rr0 = 0.0;   // meaningful in thread 0
-  if (threadIdx.x == 0) s_state = 0;
+  int total_its = 0;
+  if (threadIdx.x == 0) s_status = 0;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) s_inner[p] = 0;
 
-  // r = rhs, p = 0, q = 0, x = 0: the first p/q phase (beta = 0) then gives p = r, q = A_T r
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    const T ri = (T)a.rhs[i];
-    a.r[i] = ri;
-    a.p[i] = T(0);
-    a.q[i] = T(0);
-    a.x[i] = T(0);
-  }
-  if (!grid_barrier(a.bar, nb)) goto done;
-  {
-    T l0 = T(0);
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      const T ri = a.r[i];
-      l0 += ri * ri;
+  // r = rhs on active parts (0 elsewhere), p = q = x = 0; the first p/q phase (beta = 0)
+  // then gives p = r, q = A_T r
+  for (int sc = sc0; sc < sc1; ++sc) {
+    const bool act = a.active[a.sc_part[sc]] != 0;
+    for (int64_t i = a.sc_begin[sc] + threadIdx.x; i < a.sc_begin[sc + 1]; i += blockDim.x) {
+      a.cr[i] = act ? (T)a.r_in[i] : T(0);
+      a.cp[i] = T(0);
+      a.cq[i] = T(0);
+      a.cx[i] = T(0);
     }
-    const T l1 = cg_phase_pq<T>(a, lo, hi, T(0), a.r);
-    const double loc[2] = {(double)l0, (double)l1};
-    if (!grid_sum<2>(loc, a.part, parity, a.bar, sh, tot)) goto done;
-    if (threadIdx.x == 0) {
-      rr = rr0 = tot[0];
-      const double pq = tot[1];
-      s_state = !(rr0 > 0.0) ? (rr0 == 0.0 ? 3 : 2) : (!(pq > 0.0) || !isfinite(pq) ? 2 : 0);
-      s_alpha = (T)(rr / pq);
+  }
+  if (!grid_barrier(a.bar, G)) goto done;
+  for (int sc = sc0; sc < sc1; ++sc) {
+    const int p = a.sc_part[sc];
+    T l0 = T(0), l1 = T(0);
+    if (a.active[p]) {
+      for (int64_t i = a.sc_begin[sc] + threadIdx.x; i < a.sc_begin[sc + 1]; i += blockDim.x) {
+        const T ri = a.cr[i];
+        l0 += ri * ri;
+      }
+      l1 = cg_phase_pq<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], T(0));
+    }
+    const double t0 = block_sum((double)l0, sh);
+    const double t1 = block_sum((double)l1, sh);
+    if (threadIdx.x == 0) { a.buf[sc] = t0; a.buf[a.n_sc + sc] = t1; }
+  }
+  if (!grid_barrier(a.bar, G)) goto done;
+  part_totals<T, 2>(a, a.buf, tot);
+  if (threadIdx.x == 0) s_flag = 0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    const double rr0 = tot[p], pq = tot[P + p];
+    s_rr[p] = s_rr0[p] = rr0;
+    int st = 3;
+    if (a.active[p]) {
+      if (!(rr0 > 0.0)) st = rr0 == 0.0 ? 3 : 2;
+      else st = (!(pq > 0.0) || !isfinite(pq)) ? 2 : 0;
+    }
+    s_cg[p] = st;
+    s_alpha[p] = st == 0 ? (T)(rr0 / pq) : T(0);
+    if (st == 0) atomicOr(&s_flag, 1);
+  }
+  __syncthreads();
+  for (int its = 0; s_flag != 0 && its < a.maxit_inner; ++its) {
+    parity ^= 1;
+    double* buf = a.buf + (size_t)parity * 2 * a.n_sc;
+    for (int sc = sc0; sc < sc1; ++sc) {
+      const int p = a.sc_part[sc];
+      T l = T(0);
+      if (s_cg[p] == 0) l = cg_phase_xr<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], s_alpha[p]);
+      const double t = block_sum((double)l, sh);
+      if (threadIdx.x == 0) buf[sc] = t;
+    }
+    if (!grid_barrier(a.bar, G)) goto done;
+    part_totals<T, 1>(a, buf, tot);
+    ++total_its;
+    if (threadIdx.x == 0) s_flag = 0;
+    __syncthreads();
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+      if (s_cg[p] != 0) continue;
+      s_inner[p] += 1;
+      const double rrn = tot[p];
+      if (!isfinite(rrn)) { s_cg[p] = 2; continue; }
+      if (rrn <= a.inner_tol2 * s_rr0[p]) { s_cg[p] = 1; continue; }
+      s_beta[p] = (T)(rrn / s_rr[p]);
+      s_rr[p] = rrn;
+      atomicOr(&s_flag, 1);
     }
     __syncthreads();
-    while (s_state == 0 && its < a.maxit) {
-      const T lr = cg_phase_xr<T>(a, lo, hi, s_alpha);
-      parity ^= 1;
-      const double l1v[1] = {(double)lr};
-      if (!grid_sum<1>(l1v, a.part, parity, a.bar, sh, tot)) goto done;
-      ++its;
-      if (threadIdx.x == 0) {
-        const double rrn = tot[0];
-        if (!isfinite(rrn)) s_state = 2;
-        else if (rrn <= a.tol2 * rr0) s_state = 1;
-        s_beta = (T)(rrn / rr);
-        rr = rrn;
-      }
-      __syncthreads();
-      if (s_state != 0) break;
-      const T lpq = cg_phase_pq<T>(a, lo, hi, s_beta, a.r);
-      parity ^= 1;
-      const double l2v[1] = {(double)lpq};
-      if (!grid_sum<1>(l2v, a.part, parity, a.bar, sh, tot)) goto done;
-      if (threadIdx.x == 0) {
-        const double pq = tot[0];
-        if (!(pq > 0.0) || !isfinite(pq)) s_state = 2;
-        s_alpha = (T)(rr / pq);
-      }
-      __syncthreads();
+    if (s_flag == 0) break;
+    parity ^= 1;
+    buf = a.buf + (size_t)parity * 2 * a.n_sc;
+    for (int sc = sc0; sc < sc1; ++sc) {
+      const int p = a.sc_part[sc];
+      T l = T(0);
+      if (s_cg[p] == 0) l = cg_phase_pq<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], s_beta[p]);
+      const double t = block_sum((double)l, sh);
+      if (threadIdx.x == 0) buf[sc] = t;
     }
+    if (!grid_barrier(a.bar, G)) goto done;
+    part_totals<T, 1>(a, buf, tot);
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+      if (s_cg[p] != 0) continue;
+      const double pq = tot[p];
+      if (!(pq > 0.0) || !isfinite(pq)) { s_cg[p] = 2; continue; }
+      s_alpha[p] = (T)(s_rr[p] / pq);
+    }
+    __syncthreads();
   }
+  for (int p = threadIdx.x; p < P; p += blockDim.x)
+    if (s_cg[p] == 2) s_status = 6;
 done:
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.info[0] = its;
-    a.info[1] = s_state == 2 ? 2 : 0;
-    a.res[0] = rr0;
-    a.res[1] = rr;
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    for (int p = threadIdx.x; p < P; p += blockDim.x) a.out_inner[p] = s_inner[p];
+    if (threadIdx.x == 0) {
+      a.out_status[0] = s_status;
+      a.out_status[1] = total_its;
+    }
   }
 }
 
-template <typename T>
-const void* cg_kernel(int) {
-  return (const void*)k_cg<T>;
+// Per-part sum of squares of an FP64 vector over the same sub-chunks (one block per
+// range of the persistent grid): partials per sub-chunk, then one block sums each part's
+// sub-chunks in order.
+__global__ void __launch_bounds__(kCgThreads) k_part_sumsq_partial(const double* __restrict__ v,
+    const int32_t* __restrict__ blk_sc, const int64_t* __restrict__ sc_begin, double* __restrict__ buf) {
+  __shared__ double sh[kCgThreads];
+  for (int sc = blk_sc[blockIdx.x]; sc < blk_sc[blockIdx.x + 1]; ++sc) {
+    double l = 0.0;
+    for (int64_t i = sc_begin[sc] + threadIdx.x; i < sc_begin[sc + 1]; i += blockDim.x) l += v[i] * v[i];
+    l = block_sum(l, sh);
+    if (threadIdx.x == 0) buf[sc] = l;
+  }
+}
+
+__global__ void __launch_bounds__(kCgThreads) k_part_sumsq_final(const double* __restrict__ buf,
+    const int32_t* __restrict__ part_sc, int n_part, double* __restrict__ out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int p = warp; p < n_part; p += nw) {
+    double t = 0.0;
+    for (int sc = part_sc[p] + lane; sc < part_sc[p + 1]; sc += 32) t += buf[sc];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) out[p] = t;
+  }
 }
 
 }  // namespace
 
-int cg_grid_size(fvgb_mesh_s* m, bool fp32) {
-  int per_sm = 0;
-  const void* k = fp32 ? cg_kernel<float>(m->topo.dim + 1) : cg_kernel<double>(m->topo.dim + 1);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kCgThreads, 0) != cudaSuccess)
+int solve_grid_size(fvgb_mesh_s* m) {
+  int a = 0, b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, (const void*)k_cg<float>, kCgThreads, 0) != cudaSuccess)
     return 0;
-  if (per_sm > 2) per_sm = 2;
-  int grid = per_sm * m->num_sms;
-  // no more blocks than there are cells to own
-  const int64_t need = (m->topo.N + kCgThreads - 1) / kCgThreads;
-  if (need < grid) grid = need > 0 ? (int)need : 1;
-  return grid;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, (const void*)k_cg<double>, kCgThreads, 0) != cudaSuccess)
+    return 0;
+  const int per_sm = a < b ? a : b;
+  return per_sm >= 1 ? m->num_sms : 0;   // one block per SM
+}
+
+cudaError_t launch_part_sumsq(fvgb_mesh_s* m, const double* v, double* out, cudaStream_t s) {
+  const PartsDev& pd = m->parts;
+  k_part_sumsq_partial<<<m->solve_grid, kCgThreads, 0, s>>>(v, pd.blk_sc, pd.sc_begin, pd.buf);
+  k_part_sumsq_final<<<1, kCgThreads, 0, s>>>(pd.buf, pd.part_sc, pd.n_part, out);
+  count_launch(2);
+  return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_cg(fvgb_mesh_s* m, int bcset, const double* rhs, double rtol, int maxit,
+cudaError_t launch_cg(fvgb_mesh_s* m, int bcset, const double* r, double inner_rtol, int maxit,
                       cudaStream_t s) {
   GeoDev<T>& g = geo_of<T>(m);
   Work<T>& w = work_of<T>(m);
-  const BCDev<T>& b = g.bc[bcset];
-  CgArgs<T> a;
+  SolveArgs<T> a;
   a.N = m->topo.N;
-  a.nbr = b.at_nbr;
-  a.coef = b.at_coef;
-  a.diag = b.at_diag;
-  a.rhs = rhs;
-  a.x = w.cg_x;
-  a.r = w.cg_r;
-  a.p = w.cg_p;
-  a.q = w.cg_q;
-  a.part = m->d_scal + 8 + kRedBlocks;
+  a.at_nbr = g.bc[bcset].at_nbr; a.at_coef = g.bc[bcset].at_coef; a.at_diag = g.bc[bcset].at_diag;
+  a.r_in = r;
+  a.cx = w.cg_x; a.cr = w.cg_r; a.cp = w.cg_p; a.cq = w.cg_q;
+  const PartsDev& pd = m->parts;
+  a.n_part = pd.n_part; a.n_sc = pd.n_sc;
+  a.blk_sc = pd.blk_sc; a.sc_begin = pd.sc_begin; a.sc_part = pd.sc_part;
+  a.part_sc = pd.part_sc; a.active = pd.active; a.buf = pd.buf;
   a.bar = m->barrier;
-  a.info = m->d_cg_info;
-  a.res = m->d_scal + 2;
-  a.tol2 = rtol * rtol;
-  a.maxit = maxit;
-  const int grid = sizeof(T) == 4 ? m->cg_grid32 : m->cg_grid64;
+  a.inner_tol2 = inner_rtol * inner_rtol;
+  a.maxit_inner = maxit;
+  a.out_inner = pd.out_inner;
+  a.out_status = m->d_cg_info;
   cudaError_t e = cudaMemsetAsync(m->barrier, 0, sizeof(Barrier), s);
   if (e != cudaSuccess) return e;
   void* args[] = {&a};
   count_launch();
-  return cudaLaunchCooperativeKernel(cg_kernel<T>(m->topo.dim + 1), dim3(grid), dim3(kCgThreads),
+  return cudaLaunchCooperativeKernel((const void*)k_cg<T>, dim3(m->solve_grid), dim3(kCgThreads),
                                      args, 0, s);
 }
 

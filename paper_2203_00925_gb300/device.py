@@ -22,19 +22,30 @@ def bcset(spec):
 
 
 class DeviceMesh:
-    def __init__(self, mesh, bcsets, prec="fp64", reorder=2, device="cuda", stream=None):
+    """One mesh, or with ``ensemble=True`` a list of meshes (``bcsets`` then a list per
+    mesh) packed into one index space; the caller's order of an ensemble is the meshes'
+    cells one after the other."""
+
+    def __init__(self, mesh, bcsets, prec="fp64", reorder=2, device="cuda", stream=None,
+                 ensemble=False):
         if not torch.cuda.is_available():
             raise RuntimeError("DeviceMesh needs a CUDA device (no CPU fallback)")
         self.device = torch.device(device)
         if self.device.index is None:
             self.device = torch.device("cuda", torch.cuda.current_device())
         torch.cuda.set_device(self.device)
-        self.dim = mesh.dim
         self.prec = PREC[prec] if isinstance(prec, str) else int(prec)
         self.real = torch.float64 if self.prec == capi.FVGB_FP64 else torch.float32
-        self.handle = capi.fvgb_mesh_upload(mesh.dim, mesh.xyz, mesh.cells, mesh.bface_vert,
-                                            mesh.bface_tag, [bcset(b) for b in bcsets],
-                                            reorder, self.prec, stream)
+        if ensemble:
+            self.dim = mesh[0].dim
+            self.handle = capi.fvgb_mesh_upload_ensemble(
+                self.dim, mesh, [[bcset(b) for b in bl] for bl in bcsets], reorder, self.prec, stream)
+        else:
+            self.dim = mesh.dim
+            self.handle = capi.fvgb_mesh_upload(mesh.dim, mesh.xyz, mesh.cells, mesh.bface_vert,
+                                                mesh.bface_tag, [bcset(b) for b in bcsets],
+                                                reorder, self.prec, stream)
+        self.n_part, self.part_begin = capi.fvgb_mesh_parts(self.handle)
         info = capi.fvgb_mesh_info(self.handle)
         self.n_cell, self.n_face, self.n_vert, self.n_nbr = (
             info["n_cell"], info["n_face"], info["n_vert"], info["n_nbr"])

@@ -137,6 +137,10 @@ def test_config1_200_euler_steps(dev, prec):
         assert abs(fv.mass(g, got) - m0) <= 1e-13 * abs(m0)
     else:
         assert abs(fv.mass(g, got) - m0) <= 1e-5 * abs(m0)
+    # the device-side FP64 integral agrees with the oracle's and shows conservation too
+    gm = capi.fvgb_integral(dm.handle, ud)
+    assert gm == pytest.approx(fv.mass(g, got), rel=1e-13 if prec == "fp64" else 1e-7)
+    assert abs(gm - m0) <= (1e-13 if prec == "fp64" else 1e-5) * abs(m0)
     dm.free()
 
 
