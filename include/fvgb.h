@@ -286,6 +286,15 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
                                void* ni_dev, double* phi_dev, void* E_dev, int32_t nsteps,
                                fvgb_solve_info* info, void* stream);
 
+/* Graph mode for fvgb_streamer_step (off by default). When on, a whole step - source,
+ * right-hand side, the FP64 refinement loop of the Poisson solve as a CUDA-graph
+ * conditional WHILE node around the cooperative inner CG, then field and transport - is
+ * captured once as a CUDA graph (for the given arrays and parameters; a change of either
+ * recaptures) and replayed per step. The loop decisions run on the device, so a call with
+ * nsteps steps synchronises the stream once, at its end; a failing solve is then
+ * reported for the first step that failed (later steps of the call have run). */
+fvgb_status fvgb_set_graph_mode(fvgb_mesh m, int32_t on);
+
 /* Integral of a cell field over the domain, sum_i mu_i u_i (the mass of eq. 2 summed
  * over the cells), accumulated in FP64 in a fixed order (bitwise reproducible).
  *  u_dev [n_cell] real; *out_host receives the sum. Synchronises the stream. */

@@ -34,7 +34,7 @@ EXPORTED = [
     "fvgb_permute", "fvgb_gradient", "fvgb_vertex_values", "fvgb_fv_residual",
     "fvgb_fv_residual_noalloc",
     "fvgb_fv_step", "fvgb_poisson_apply", "fvgb_poisson_rhs", "fvgb_poisson_solve",
-    "fvgb_streamer_step", "fvgb_integral", "fvgb_stats_enable", "fvgb_stats_get", "fvgb_last_error",
+    "fvgb_streamer_step", "fvgb_set_graph_mode", "fvgb_integral", "fvgb_stats_enable", "fvgb_stats_get", "fvgb_last_error",
 ]
 
 
@@ -112,6 +112,7 @@ _sig = {
     "fvgb_streamer_step": (C.c_int, [_vp, C.POINTER(fvgb_streamer_params), _vp, _vp, _vp, _vp,
                                      _i32, C.POINTER(fvgb_solve_info), _vp]),
     "fvgb_integral": (C.c_int, [_vp, _vp, C.POINTER(_d), _vp]),
+    "fvgb_set_graph_mode": (C.c_int, [_vp, _i32]),
     "fvgb_stats_enable": (C.c_int, [_vp, _i32]),
     "fvgb_stats_get": (C.c_int, [_vp, C.POINTER(fvgb_stats), _i32]),
     "fvgb_last_error": (C.c_char_p, []),
@@ -334,6 +335,10 @@ def fvgb_streamer_step(m, params, ne, ni, phi, E, nsteps, stream=None):
     _check(lib.fvgb_streamer_step(m, C.byref(params), ptr(ne), ptr(ni), ptr(phi), ptr(E),
                                   int(nsteps), infos, stream_handle(stream)), "fvgb_streamer_step")
     return [infos[i].as_dict() for i in range(nsteps)]
+
+
+def fvgb_set_graph_mode(m, on=True):
+    return _check(lib.fvgb_set_graph_mode(m, int(bool(on))), "fvgb_set_graph_mode")
 
 
 def fvgb_integral(m, u, stream=None):

@@ -30,12 +30,6 @@ fvgb_status cuda_status(cudaError_t e, const char* what) {
 
 namespace {
 
-#define FVGB_TRY(expr, what)                                   \
-  do {                                                         \
-    fvgb_status st_ = cuda_status((expr), (what));             \
-    if (st_ != FVGB_OK) return st_;                            \
-  } while (0)
-
 template <typename T>
 cudaError_t dalloc(fvgb_mesh_s* m, T** p, size_t count) {
   void* q = nullptr;
@@ -191,6 +185,7 @@ cudaError_t setup_parts(fvgb_mesh_s* m, const std::vector<int64_t>& part_begin, 
 }
 
 void release(fvgb_mesh_s* m) {
+  graph_release(m);
   if (m->ev_cg0) cudaEventDestroy(m->ev_cg0);
   if (m->ev_cg1) cudaEventDestroy(m->ev_cg1);
   for (void* p : m->allocs) cudaFree(p);
@@ -210,7 +205,9 @@ fvgb_status check_bcset(fvgb_mesh m, int32_t k) {
   return FVGB_OK;
 }
 
+}  // namespace
 bool is_fp32(fvgb_mesh m) { return m->prec != FVGB_FP64; }
+namespace {
 
 // ---- transport residual / step in precision T --------------------------------------------
 template <typename T>
@@ -225,6 +222,7 @@ fvgb_status residual_T(fvgb_mesh m, const fvgb_tcoef* tc, const T* u, T* res, cu
   return FVGB_OK;
 }
 
+}  // namespace
 template <typename T>
 fvgb_status step_T(fvgb_mesh m, const fvgb_tcoef* tc, T* u, double dt, int nsteps,
                    const double* alpha, int nstage, T* ni_out, cudaStream_t s) {
@@ -245,6 +243,8 @@ fvgb_status step_T(fvgb_mesh m, const fvgb_tcoef* tc, T* u, double dt, int nstep
   }
   return FVGB_OK;
 }
+template fvgb_status step_T<float>(fvgb_mesh, const fvgb_tcoef*, float*, double, int, const double*, int, float*, cudaStream_t);
+template fvgb_status step_T<double>(fvgb_mesh, const fvgb_tcoef*, double*, double, int, const double*, int, double*, cudaStream_t);
 
 // FP64 full diamond operator pieces
 fvgb_status poisson_residual(fvgb_mesh m, int bcset, const double* x, const double* b, double* r,
@@ -265,6 +265,7 @@ fvgb_status poisson_rhs_impl(fvgb_mesh m, int bcset, const double* f, double* b,
   return FVGB_OK;
 }
 
+namespace {
 // Outer FP64 refinement loop, per part: r = b - A phi, stop a part when
 // ||r_p|| <= rtol ||b_p||, otherwise one inner CG solve of A_T delta = r on the parts
 // still active and phi += delta. One host synchronisation per outer step.
@@ -367,6 +368,38 @@ fvgb_status solve_impl(fvgb_mesh m, int bcset, const double* f, double* phi,
   if (info) *info = loc;
   return FVGB_OK;
 }
+
+}  // namespace
+
+// Field, cell physics and the transport update of one streamer step (after the solve).
+fvgb_status streamer_transport(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, void* ni,
+                               const double* phi, void* E, cudaStream_t s) {
+  const int64_t N = m->topo.N;
+  fvgb_tcoef tc;
+  std::memset(&tc, 0, sizeof(tc));
+  tc.diff = p->De;
+  tc.bcset = p->bcset_ne;
+  static const double euler[1] = {1.0};
+  if (is_fp32(m)) {
+    Work<float>& w = m->w32;
+    FVGB_TRY(launch_convert(phi, w.tmp, N, s), "convert");
+    FVGB_TRY(launch_gradient<float>(m, p->bcset_phi, w.tmp, w.grad, s), "gradient kernel");
+    FVGB_TRY(launch_cell_physics<float>(m, w.grad, (const float*)ne, p->mu, p->A, p->B, (float*)E,
+                                        w.vel, w.src, s), "cell kernel");
+    tc.vel_dev = w.vel;
+    tc.src_dev = w.src;
+    return step_T<float>(m, &tc, (float*)ne, p->dt, 1, euler, 1, (float*)ni, s);
+  }
+  Work<double>& w = m->w64;
+  FVGB_TRY(launch_gradient<double>(m, p->bcset_phi, phi, w.grad, s), "gradient kernel");
+  FVGB_TRY(launch_cell_physics<double>(m, w.grad, (const double*)ne, p->mu, p->A, p->B,
+                                       (double*)E, w.vel, w.src, s), "cell kernel");
+  tc.vel_dev = w.vel;
+  tc.src_dev = w.src;
+  return step_T<double>(m, &tc, (double*)ne, p->dt, 1, euler, 1, (double*)ni, s);
+}
+
+namespace {
 
 bool opts_ok(const fvgb_solve_opts* o) {
   return o && o->rtol > 0.0 && o->inner_rtol > 0.0 && o->inner_rtol < 1.0 && o->maxit_inner > 0 &&
@@ -700,8 +733,10 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
   if (!p || !ne || !ni || !phi || nsteps < 0 || !opts_ok(&p->solve)) { set_error("bad streamer arguments"); return FVGB_EINVAL; }
   if (fvgb_status st = check_bcset(m, p->bcset_ne)) return st;
   if (fvgb_status st = check_bcset(m, p->bcset_phi)) return st;
+  const bool fp32_solve = p->solve.prec == FVGB_FP32 || p->solve.prec == FVGB_MIXED;
+  if (fp32_solve && !is_fp32(m)) { set_error("FP32 inner solve needs a mesh uploaded with FVGB_FP32 or FVGB_MIXED"); return FVGB_EINVAL; }
   cudaStream_t s = (cudaStream_t)stream;
-  const int64_t N = m->topo.N;
+  if (m->use_graph) return streamer_graph_steps(m, p, ne, ni, phi, E, nsteps, info, s);
   const bool fp32 = is_fp32(m);
   double* f = m->w64.tmp;   // FP64 scratch of the mesh (unused by the FP64 transport path)
   for (int n = 0; n < nsteps; ++n) {
@@ -709,31 +744,15 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
     if (st) return st;
     st = solve_impl(m, p->bcset_phi, f, phi, &p->solve, info ? info + n : nullptr, s);
     if (st) return st;
-    fvgb_tcoef tc;
-    std::memset(&tc, 0, sizeof(tc));
-    tc.diff = p->De;
-    tc.bcset = p->bcset_ne;
-    static const double euler[1] = {1.0};
-    if (fp32) {
-      Work<float>& w = m->w32;
-      FVGB_TRY(launch_convert(phi, w.tmp, N, s), "convert");
-      FVGB_TRY(launch_gradient<float>(m, p->bcset_phi, w.tmp, w.grad, s), "gradient kernel");
-      FVGB_TRY(launch_cell_physics<float>(m, w.grad, (const float*)ne, p->mu, p->A, p->B, (float*)E,
-                                          w.vel, w.src, s), "cell kernel");
-      tc.vel_dev = w.vel;
-      tc.src_dev = w.src;
-      st = step_T<float>(m, &tc, (float*)ne, p->dt, 1, euler, 1, (float*)ni, s);
-    } else {
-      Work<double>& w = m->w64;
-      FVGB_TRY(launch_gradient<double>(m, p->bcset_phi, phi, w.grad, s), "gradient kernel");
-      FVGB_TRY(launch_cell_physics<double>(m, w.grad, (const double*)ne, p->mu, p->A, p->B,
-                                           (double*)E, w.vel, w.src, s), "cell kernel");
-      tc.vel_dev = w.vel;
-      tc.src_dev = w.src;
-      st = step_T<double>(m, &tc, (double*)ne, p->dt, 1, euler, 1, (double*)ni, s);
-    }
+    st = streamer_transport(m, p, ne, ni, phi, E, s);
     if (st) return st;
   }
+  return FVGB_OK;
+}
+
+fvgb_status fvgb_set_graph_mode(fvgb_mesh m, int32_t on) {
+  if (fvgb_status st = check_mesh(m)) return st;
+  m->use_graph = on ? 1 : 0;
   return FVGB_OK;
 }
 

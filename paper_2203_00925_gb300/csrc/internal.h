@@ -99,6 +99,8 @@ struct Barrier {
   int pad;
 };
 
+struct GraphState;
+
 }  // namespace fvgb
 
 struct fvgb_mesh_s {
@@ -128,6 +130,8 @@ struct fvgb_mesh_s {
   int time_cg = 0;                      // record CUDA events around CG launches
   cudaEvent_t ev_cg0 = nullptr, ev_cg1 = nullptr;
   bool cg_pending = false;              // events recorded, elapsed time not yet read
+  int use_graph = 0;                    // run streamer steps as one CUDA graph each
+  fvgb::GraphState* graph = nullptr;    // captured step graph (graph.cu)
   std::vector<void*> allocs;
 };
 
@@ -184,6 +188,28 @@ cudaError_t launch_convert_back(const float* x, double* y, int64_t n, cudaStream
 cudaError_t launch_permute(const void* src, void* dst, const int32_t* perm, int64_t n, int ncomp,
                            int elem_bytes, bool to_internal, cudaStream_t s);
 cudaError_t launch_nonfinite_check(const double* x, int64_t n, int* flag, cudaStream_t s);
+
+// api.cu -------------------------------------------------------------------------------
+bool is_fp32(fvgb_mesh m);
+#define FVGB_TRY(expr, what)                                   \
+  do {                                                         \
+    fvgb_status st_ = cuda_status((expr), (what));             \
+    if (st_ != FVGB_OK) return st_;                            \
+  } while (0)
+fvgb_status poisson_residual(fvgb_mesh m, int bcset, const double* x, const double* b, double* r,
+                             cudaStream_t s);
+fvgb_status poisson_rhs_impl(fvgb_mesh m, int bcset, const double* f, double* b, cudaStream_t s);
+template <typename T>
+fvgb_status step_T(fvgb_mesh m, const fvgb_tcoef* tc, T* u, double dt, int nsteps,
+                   const double* alpha, int nstage, T* ni_out, cudaStream_t s);
+fvgb_status streamer_transport(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, void* ni,
+                               const double* phi, void* E, cudaStream_t s);
+
+// graph.cu -----------------------------------------------------------------------------
+fvgb_status streamer_graph_steps(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, void* ni,
+                                 double* phi, void* E, int nsteps, fvgb_solve_info* info,
+                                 cudaStream_t s);
+void graph_release(fvgb_mesh m);
 
 // solver.cu ----------------------------------------------------------------------------
 int solve_grid_size(fvgb_mesh_s* m);
