@@ -295,6 +295,20 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
  * reported for the first step that failed (later steps of the call have run). */
 fvgb_status fvgb_set_graph_mode(fvgb_mesh m, int32_t on);
 
+/* Autotuner (no counterpart in the paper): pick the launch shape - threads per block
+ * and elements per thread - of the four gather kernels (0 least-squares gradient,
+ * 1 vertex values, 2 face fluxes, 3 face-to-cell update) by timing every candidate
+ * (threads 128..1024 x 1, 2, 4 elements) with CUDA events on this mesh. Shapes are cached
+ * per device and mesh class (dimension, precision, size bucket floor(log2 n_cell)); a
+ * later mesh of the same class reuses them unless force = 1. Results never depend on the
+ * shape. shapes_out (host, 8 ints or NULL) receives (threads, elements) per kernel.
+ * Synchronises the stream; drops a captured step graph. */
+fvgb_status fvgb_autotune(fvgb_mesh m, int32_t force, int32_t* shapes_out, void* stream);
+
+/* Set one kernel's launch shape by hand (kernel 0..3 as above; threads a multiple of 32
+ * in [32, 1024], elements per thread in [1, 64]). */
+fvgb_status fvgb_set_launch_shape(fvgb_mesh m, int32_t kernel, int32_t threads, int32_t ipt);
+
 /* Integral of a cell field over the domain, sum_i mu_i u_i (the mass of eq. 2 summed
  * over the cells), accumulated in FP64 in a fixed order (bitwise reproducible).
  *  u_dev [n_cell] real; *out_host receives the sum. Synchronises the stream. */

@@ -34,7 +34,8 @@ EXPORTED = [
     "fvgb_permute", "fvgb_gradient", "fvgb_vertex_values", "fvgb_fv_residual",
     "fvgb_fv_residual_noalloc",
     "fvgb_fv_step", "fvgb_poisson_apply", "fvgb_poisson_rhs", "fvgb_poisson_solve",
-    "fvgb_streamer_step", "fvgb_set_graph_mode", "fvgb_integral", "fvgb_stats_enable", "fvgb_stats_get", "fvgb_last_error",
+    "fvgb_streamer_step", "fvgb_set_graph_mode", "fvgb_autotune", "fvgb_set_launch_shape",
+    "fvgb_integral", "fvgb_stats_enable", "fvgb_stats_get", "fvgb_last_error",
 ]
 
 
@@ -113,6 +114,8 @@ _sig = {
                                      _i32, C.POINTER(fvgb_solve_info), _vp]),
     "fvgb_integral": (C.c_int, [_vp, _vp, C.POINTER(_d), _vp]),
     "fvgb_set_graph_mode": (C.c_int, [_vp, _i32]),
+    "fvgb_autotune": (C.c_int, [_vp, _i32, _vp, _vp]),
+    "fvgb_set_launch_shape": (C.c_int, [_vp, _i32, _i32, _i32]),
     "fvgb_stats_enable": (C.c_int, [_vp, _i32]),
     "fvgb_stats_get": (C.c_int, [_vp, C.POINTER(fvgb_stats), _i32]),
     "fvgb_last_error": (C.c_char_p, []),
@@ -339,6 +342,17 @@ def fvgb_streamer_step(m, params, ne, ni, phi, E, nsteps, stream=None):
 
 def fvgb_set_graph_mode(m, on=True):
     return _check(lib.fvgb_set_graph_mode(m, int(bool(on))), "fvgb_set_graph_mode")
+
+
+def fvgb_autotune(m, force=False, stream=None):
+    import numpy as np
+    shapes = np.zeros(8, dtype=np.int32)
+    _check(lib.fvgb_autotune(m, int(bool(force)), ptr(shapes), stream_handle(stream)), "fvgb_autotune")
+    return shapes.reshape(4, 2)
+
+
+def fvgb_set_launch_shape(m, kernel, threads, ipt=1):
+    return _check(lib.fvgb_set_launch_shape(m, kernel, threads, ipt), "fvgb_set_launch_shape")
 
 
 def fvgb_integral(m, u, stream=None):

@@ -230,6 +230,13 @@ fvgb_status build_graph(fvgb_mesh m, GraphState& g, const fvgb_streamer_params* 
 
 }  // namespace
 
+void graph_invalidate(fvgb_mesh m) {
+  if (m->graph && m->graph->exec) {
+    cudaGraphExecDestroy(m->graph->exec);
+    m->graph->exec = nullptr;
+  }
+}
+
 void graph_release(fvgb_mesh m) {
   GraphState* g = m->graph;
   if (!g) return;

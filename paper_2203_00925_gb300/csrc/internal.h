@@ -101,6 +101,13 @@ struct Barrier {
 
 struct GraphState;
 
+// Launch shape of a tunable kernel: threads per block and elements per thread.
+struct LaunchShape {
+  int threads = 256;
+  int ipt = 1;
+};
+enum TuneKernel { kTuneGrad = 0, kTuneVertex = 1, kTuneFace = 2, kTuneUpdate = 3, kTuneCount = 4 };
+
 }  // namespace fvgb
 
 struct fvgb_mesh_s {
@@ -131,6 +138,7 @@ struct fvgb_mesh_s {
   cudaEvent_t ev_cg0 = nullptr, ev_cg1 = nullptr;
   bool cg_pending = false;              // events recorded, elapsed time not yet read
   int use_graph = 0;                    // run streamer steps as one CUDA graph each
+  fvgb::LaunchShape tune[fvgb::kTuneCount];  // launch shapes (autotuned or default)
   fvgb::GraphState* graph = nullptr;    // captured step graph (graph.cu)
   std::vector<void*> allocs;
 };
@@ -210,6 +218,7 @@ fvgb_status streamer_graph_steps(fvgb_mesh m, const fvgb_streamer_params* p, voi
                                  double* phi, void* E, int nsteps, fvgb_solve_info* info,
                                  cudaStream_t s);
 void graph_release(fvgb_mesh m);
+void graph_invalidate(fvgb_mesh m);
 
 // solver.cu ----------------------------------------------------------------------------
 int solve_grid_size(fvgb_mesh_s* m);

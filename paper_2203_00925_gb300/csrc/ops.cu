@@ -22,6 +22,13 @@ inline unsigned grid_for(int64_t n, int threads = kThreads) {
   return (unsigned)((n + threads - 1) / threads);
 }
 
+// Grid of a tunable kernel: threads x items per thread cover n elements (grid-stride).
+inline unsigned shape_grid(const fvgb_mesh_s* m, int k, int64_t n) {
+  const int64_t per_block = (int64_t)m->tune[k].threads * m->tune[k].ipt;
+  const int64_t g = (n + per_block - 1) / per_block;
+  return (unsigned)(g > 0 ? g : 1);
+}
+
 // Difference of two centre coordinates. FP32 keeps each coordinate as a (high, low)
 // pair of floats so that the difference of nearby centres keeps FP32 relative accuracy.
 __device__ __forceinline__ double cdiff(const double* a, const double*, int64_t ia,
@@ -35,154 +42,158 @@ __device__ __forceinline__ float cdiff(const float* a, const float* alo, int64_t
 
 // ---- Algorithm "grad": grad u_i = M_i^{-1} sum_j d_ij (u_j - u_i) ------------------------
 template <typename T, int D>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(1024)
 k_gradient(int64_t N, int64_t F, int64_t Fi, const int64_t* __restrict__ sptr,
            const int32_t* __restrict__ sidx, const T* __restrict__ cen,
            const T* __restrict__ cen_lo, const T* __restrict__ xf, const T* __restrict__ xf_lo,
            const T* __restrict__ u, const T* __restrict__ minv, const int32_t* __restrict__ gptr,
            const int32_t* __restrict__ gface, const T* __restrict__ bval, T* __restrict__ grad) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int64_t sl = i >> 5;
-  const int lane = (int)(i & 31);
-  const int64_t b0 = sptr[sl], b1 = sptr[sl + 1];
-  const T ui = u[i];
-  T J[D];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = i >> 5;
+    const int lane = (int)(i & 31);
+    const int64_t b0 = sptr[sl], b1 = sptr[sl + 1];
+    const T ui = u[i];
+    T J[D];
 #pragma unroll
-  for (int a = 0; a < D; ++a) J[a] = T(0);
-  for (int64_t p = b0 + lane; p < b1; p += 32) {
-    const int32_t j = __ldg(sidx + p);
-    const T du = u[j] - ui;
+    for (int a = 0; a < D; ++a) J[a] = T(0);
+    for (int64_t p = b0 + lane; p < b1; p += 32) {
+      const int32_t j = __ldg(sidx + p);
+      const T du = u[j] - ui;
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const T dx = cdiff(cen + a * N, cen_lo ? cen_lo + a * N : nullptr, j, cen + a * N,
-                         cen_lo ? cen_lo + a * N : nullptr, i);
-      J[a] += dx * du;
+      for (int a = 0; a < D; ++a) {
+        const T dx = cdiff(cen + a * N, cen_lo ? cen_lo + a * N : nullptr, j, cen + a * N,
+                           cen_lo ? cen_lo + a * N : nullptr, i);
+        J[a] += dx * du;
+      }
     }
-  }
-  for (int32_t t = gptr[i]; t < gptr[i + 1]; ++t) {
-    const int32_t f = gface[t];
-    const T du = bval[f - Fi] - ui;
+    for (int32_t t = gptr[i]; t < gptr[i + 1]; ++t) {
+      const int32_t f = gface[t];
+      const T du = bval[f - Fi] - ui;
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const T dx = cdiff(xf + a * F, xf_lo ? xf_lo + a * F : nullptr, f, cen + a * N,
-                         cen_lo ? cen_lo + a * N : nullptr, i);
-      J[a] += dx * du;
+      for (int a = 0; a < D; ++a) {
+        const T dx = cdiff(xf + a * F, xf_lo ? xf_lo + a * F : nullptr, f, cen + a * N,
+                           cen_lo ? cen_lo + a * N : nullptr, i);
+        J[a] += dx * du;
+      }
     }
-  }
-  if constexpr (D == 3) {
-    const T m0 = minv[i], m1 = minv[N + i], m2 = minv[2 * N + i], m3 = minv[3 * N + i],
-            m4 = minv[4 * N + i], m5 = minv[5 * N + i];
-    grad[i] = m0 * J[0] + m1 * J[1] + m2 * J[2];
-    grad[N + i] = m1 * J[0] + m3 * J[1] + m4 * J[2];
-    grad[2 * N + i] = m2 * J[0] + m4 * J[1] + m5 * J[2];
-  } else {
-    const T m0 = minv[i], m1 = minv[N + i], m2 = minv[2 * N + i];
-    grad[i] = m0 * J[0] + m1 * J[1];
-    grad[N + i] = m1 * J[0] + m2 * J[1];
+    if constexpr (D == 3) {
+      const T m0 = minv[i], m1 = minv[N + i], m2 = minv[2 * N + i], m3 = minv[3 * N + i],
+              m4 = minv[4 * N + i], m5 = minv[5 * N + i];
+      grad[i] = m0 * J[0] + m1 * J[1] + m2 * J[2];
+      grad[N + i] = m1 * J[0] + m3 * J[1] + m4 * J[2];
+      grad[2 * N + i] = m2 * J[0] + m4 * J[1] + m5 * J[2];
+    } else {
+      const T m0 = minv[i], m1 = minv[N + i], m2 = minv[2 * N + i];
+      grad[i] = m0 * J[0] + m1 * J[1];
+      grad[N + i] = m1 * J[0] + m2 * J[1];
+    }
   }
 }
 
 // ---- Algorithm "ls": u_A = sum_c alpha_{A,c} u_c; Dirichlet vertices take g --------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(1024)
 k_vertex(int64_t V, const int64_t* __restrict__ sptr, const int32_t* __restrict__ sidx,
          const T* __restrict__ alpha, const T* __restrict__ u, const T* __restrict__ vdir,
          int homog, T* __restrict__ uv) {
-  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (v >= V) return;
-  const int64_t sl = v >> 5;
-  const int lane = (int)(v & 31);
-  const int64_t b0 = sptr[sl], b1 = sptr[sl + 1];
-  T s = T(0);
-  for (int64_t p = b0 + lane; p < b1; p += 32) s += alpha[p] * u[__ldg(sidx + p)];
-  const T g = vdir[v];
-  if (g == g) s = homog ? T(0) : g;  // Dirichlet vertex (vdir is NaN elsewhere)
-  uv[v] = s;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = v >> 5;
+    const int lane = (int)(v & 31);
+    const int64_t b0 = sptr[sl], b1 = sptr[sl + 1];
+    T s = T(0);
+    for (int64_t p = b0 + lane; p < b1; p += 32) s += alpha[p] * u[__ldg(sidx + p)];
+    const T g = vdir[v];
+    if (g == g) s = homog ? T(0) : g;  // Dirichlet vertex (vdir is NaN elsewhere)
+    uv[v] = s;
+  }
 }
 
 // ---- face flux: F = (V_f . S_f) u_up - D grad u_f . S_f (eq. 4, eq. 15, eq. "diamond") ----
 template <typename T, int D, bool CONV, bool VFIELD>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(1024)
 k_face(int64_t F, int64_t Fi, int64_t N, const int32_t* __restrict__ fL,
        const int32_t* __restrict__ fR, const int32_t* __restrict__ fvert,
        const T* __restrict__ S, const T* __restrict__ coef, const T* __restrict__ u,
        const T* __restrict__ uv, const T* __restrict__ vel, T vc0, T vc1, T vc2, T Dcoef,
        const int8_t* __restrict__ bkind, const T* __restrict__ bval, int homog,
        T* __restrict__ flux) {
-  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (f >= F) return;
-  const int32_t L = fL[f];
-  const T uL = u[L];
-  int kind = 3;  // interior
-  int32_t R = -1;
-  T uR;
-  if (f < Fi) {
-    R = fR[f];
-    uR = u[R];
-  } else {
-    kind = bkind[f - Fi];
-    if (kind == FVGB_BC_WALL) { flux[f] = T(0); return; }
-    uR = kind == FVGB_BC_DIRICHLET ? (homog ? T(0) : bval[f - Fi]) : uL;
-  }
-  T Ff = T(0);
-  if (CONV) {
-    T vf[3];
-    if (VFIELD) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < F;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t L = fL[f];
+    const T uL = u[L];
+    int kind = 3;  // interior
+    int32_t R = -1;
+    T uR;
+    if (f < Fi) {
+      R = fR[f];
+      uR = u[R];
+    } else {
+      kind = bkind[f - Fi];
+      if (kind == FVGB_BC_WALL) { flux[f] = T(0); continue; }
+      uR = kind == FVGB_BC_DIRICHLET ? (homog ? T(0) : bval[f - Fi]) : uL;
+    }
+    T Ff = T(0);
+    if (CONV) {
+      T vf[3];
+      if (VFIELD) {
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const T vl = vel[a * N + L];
-        const T vr = R >= 0 ? vel[a * N + R] : vl;
-        vf[a] = T(0.5) * (vl + vr);
+        for (int a = 0; a < D; ++a) {
+          const T vl = vel[a * N + L];
+          const T vr = R >= 0 ? vel[a * N + R] : vl;
+          vf[a] = T(0.5) * (vl + vr);
+        }
+      } else {
+        vf[0] = vc0; vf[1] = vc1; vf[2] = vc2;
       }
-    } else {
-      vf[0] = vc0; vf[1] = vc1; vf[2] = vc2;
+      T vn = vf[0] * S[f] + vf[1] * S[F + f];
+      if (D == 3) vn += vf[2] * S[2 * F + f];
+      Ff = vn * (vn >= T(0) ? uL : uR);
     }
-    T vn = vf[0] * S[f] + vf[1] * S[F + f];
-    if (D == 3) vn += vf[2] * S[2 * F + f];
-    Ff = vn * (vn >= T(0) ? uL : uR);
-  }
-  if (Dcoef != T(0) && (kind == 3 || kind == FVGB_BC_DIRICHLET)) {
-    T q;
-    if constexpr (D == 3) {
-      const T ua = uv[fvert[f]], ub = uv[fvert[F + f]], uc = uv[fvert[2 * F + f]];
-      q = coef[f] * (uR - uL) + coef[F + f] * (ua - uc) + coef[2 * F + f] * (ub - uc);
-    } else {
-      const T ua = uv[fvert[f]], ub = uv[fvert[F + f]];
-      q = coef[f] * (uR - uL) + coef[F + f] * (ub - ua);
+    if (Dcoef != T(0) && (kind == 3 || kind == FVGB_BC_DIRICHLET)) {
+      T q;
+      if constexpr (D == 3) {
+        const T ua = uv[fvert[f]], ub = uv[fvert[F + f]], uc = uv[fvert[2 * F + f]];
+        q = coef[f] * (uR - uL) + coef[F + f] * (ua - uc) + coef[2 * F + f] * (ub - uc);
+      } else {
+        const T ua = uv[fvert[f]], ub = uv[fvert[F + f]];
+        q = coef[f] * (uR - uL) + coef[F + f] * (ub - ua);
+      }
+      Ff -= Dcoef * q;
     }
-    Ff -= Dcoef * q;
+    flux[f] = Ff;
   }
-  flux[f] = Ff;
 }
 
 // ---- gather of the face fluxes of every cell (eq. 4) and what follows from it ---------------
 template <typename T, int NV, int MODE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(1024)
 k_update(int64_t N, const int32_t* __restrict__ cell_face, const T* __restrict__ flux,
          const T* __restrict__ inv_vol, const T* __restrict__ vol, const T* __restrict__ src,
          const T* base, T adt, const T* __restrict__ aux, T* out, T* out2) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  T acc = T(0);  // sum over faces entering i minus faces leaving i
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T acc = T(0);  // sum over faces entering i minus faces leaving i
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    const int32_t e = cell_face[k * N + i];
-    acc += e >= 0 ? -flux[e] : flux[~e];
-  }
-  if constexpr (MODE == kResidual) {
-    out[i] = acc * inv_vol[i] + (src ? src[i] : T(0));
-  } else if constexpr (MODE == kStep) {
-    const T s = src ? src[i] : T(0);
-    const T r = acc * inv_vol[i] + s;
-    out[i] = base[i] + adt * r;
-    if (out2) out2[i] += adt * s;
-  } else if constexpr (MODE == kPoissonApply) {
-    out[i] = acc;                       // A x = -mu Lap_h x
-  } else if constexpr (MODE == kPoissonResidual) {
-    out[i] = aux[i] - acc;              // r = b - A x
-  } else {
-    out[i] = -vol[i] * (aux ? aux[i] : T(0)) - acc;   // b = -mu f + mu Lap_h(0; g)
+    for (int k = 0; k < NV; ++k) {
+      const int32_t e = cell_face[k * N + i];
+      acc += e >= 0 ? -flux[e] : flux[~e];
+    }
+    if constexpr (MODE == kResidual) {
+      out[i] = acc * inv_vol[i] + (src ? src[i] : T(0));
+    } else if constexpr (MODE == kStep) {
+      const T s = src ? src[i] : T(0);
+      const T r = acc * inv_vol[i] + s;
+      out[i] = base[i] + adt * r;
+      if (out2) out2[i] += adt * s;
+    } else if constexpr (MODE == kPoissonApply) {
+      out[i] = acc;                       // A x = -mu Lap_h x
+    } else if constexpr (MODE == kPoissonResidual) {
+      out[i] = aux[i] - acc;              // r = b - A x
+    } else {
+      out[i] = -vol[i] * (aux ? aux[i] : T(0)) - acc;   // b = -mu f + mu Lap_h(0; g)
+    }
   }
 }
 
@@ -308,10 +319,10 @@ cudaError_t launch_gradient(fvgb_mesh_s* m, int bcset, const T* u, T* grad, cuda
   GeoDev<T>& g = geo_of<T>(m);
   const BCDev<T>& b = g.bc[bcset];
   if (t.dim == 3)
-    k_gradient<T, 3><<<grid_for(t.N), kThreads, 0, s>>>(t.N, t.F, t.Fi, t.nsell.ptr, t.nsell.idx,
+    k_gradient<T, 3><<<shape_grid(m, kTuneGrad, t.N), m->tune[kTuneGrad].threads, 0, s>>>(t.N, t.F, t.Fi, t.nsell.ptr, t.nsell.idx,
         g.cen, g.cen_lo, g.xf, g.xf_lo, u, b.minv, b.gptr, b.gface, b.bval, grad);
   else
-    k_gradient<T, 2><<<grid_for(t.N), kThreads, 0, s>>>(t.N, t.F, t.Fi, t.nsell.ptr, t.nsell.idx,
+    k_gradient<T, 2><<<shape_grid(m, kTuneGrad, t.N), m->tune[kTuneGrad].threads, 0, s>>>(t.N, t.F, t.Fi, t.nsell.ptr, t.nsell.idx,
         g.cen, g.cen_lo, g.xf, g.xf_lo, u, b.minv, b.gptr, b.gface, b.bval, grad);
   count_launch();
   return cudaGetLastError();
@@ -321,7 +332,7 @@ template <typename T>
 cudaError_t launch_vertex(fvgb_mesh_s* m, int bcset, const T* u, T* uv, bool homog, cudaStream_t s) {
   const TopoDev& t = m->topo;
   GeoDev<T>& g = geo_of<T>(m);
-  k_vertex<T><<<grid_for(t.V), kThreads, 0, s>>>(t.V, t.vsell.ptr, t.vsell.idx, g.valpha, u,
+  k_vertex<T><<<shape_grid(m, kTuneVertex, t.V), m->tune[kTuneVertex].threads, 0, s>>>(t.V, t.vsell.ptr, t.vsell.idx, g.valpha, u,
                                                   g.bc[bcset].vdir, homog ? 1 : 0, uv);
   count_launch();
   return cudaGetLastError();
@@ -334,9 +345,10 @@ cudaError_t launch_face(fvgb_mesh_s* m, int bcset, const T* u, const T* uv, cons
   GeoDev<T>& g = geo_of<T>(m);
   const BCDev<T>& b = g.bc[bcset];
   const T v0 = vc ? (T)vc[0] : T(0), v1 = vc ? (T)vc[1] : T(0), v2 = vc ? (T)vc[2] : T(0);
-  const unsigned gr = grid_for(t.F);
+  const unsigned gr = shape_grid(m, kTuneFace, t.F);
+  const int tb = m->tune[kTuneFace].threads;
 #define FVGB_FACE(DD, CV, VF)                                                                   \
-  k_face<T, DD, CV, VF><<<gr, kThreads, 0, s>>>(t.F, t.Fi, t.N, t.fL, t.fR, t.fvert, g.S, g.coef, \
+  k_face<T, DD, CV, VF><<<gr, tb, 0, s>>>(t.F, t.Fi, t.N, t.fL, t.fR, t.fvert, g.S, g.coef, \
                                                 u, uv, vel, v0, v1, v2, (T)D, b.bkind, b.bval,  \
                                                 homog ? 1 : 0, flux)
   if (t.dim == 3) {
@@ -358,9 +370,10 @@ cudaError_t launch_update(fvgb_mesh_s* m, int mode, const T* flux, const T* src,
                           double adt, const T* aux, T* out, T* out2, cudaStream_t s) {
   const TopoDev& t = m->topo;
   GeoDev<T>& g = geo_of<T>(m);
-  const unsigned gr = grid_for(t.N);
+  const unsigned gr = shape_grid(m, kTuneUpdate, t.N);
+  const int tb = m->tune[kTuneUpdate].threads;
 #define FVGB_UPD(NV, MD)                                                                 \
-  k_update<T, NV, MD><<<gr, kThreads, 0, s>>>(t.N, t.cell_face, flux, g.inv_vol, g.vol, src, \
+  k_update<T, NV, MD><<<gr, tb, 0, s>>>(t.N, t.cell_face, flux, g.inv_vol, g.vol, src, \
                                               base, (T)adt, aux, out, out2)
 #define FVGB_UPD_MODES(NV)                                       \
   switch (mode) {                                                \

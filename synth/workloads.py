@@ -53,3 +53,20 @@ class StreamerCase:
 def streamer_mesh(k, seed=201):
     """Unit cube, k^3 jittered hexes x 6 Kuhn tetrahedra (6 k^3 cells)."""
     return jittered_cube(k, seed=seed)
+
+
+def ensemble_cases(n_mesh=64, seed=5000, lo=20_000, hi=1_000_000):
+    """The batched workload: n_mesh jittered Kuhn cubes with cell-count targets
+    log-uniform in [lo, hi] (k_i = round((n_i / 6)^(1/3))), mesh seeds seed + i, and per
+    case a seed position uniform in [0.3, 0.7]^2 x [0.8, 0.95] and a voltage uniform in
+    [15, 25] kV drawn from the stream seeded by ``seed``."""
+    import numpy as np
+    from .meshgen import ensemble_sizes
+    _, ks = ensemble_sizes(n_mesh, lo, hi, seed)
+    rng = np.random.default_rng(seed + 1)
+    cases = []
+    for i, k in enumerate(ks):
+        centre = (rng.uniform(0.3, 0.7), rng.uniform(0.3, 0.7), rng.uniform(0.8, 0.95))
+        V = rng.uniform(15e3, 25e3)
+        cases.append((int(k), seed + i, StreamerCase(V=V, centre=centre)))
+    return cases
