@@ -40,6 +40,7 @@ extern "C" {
 #endif
 
 typedef struct fvgb_mesh_s* fvgb_mesh;
+typedef struct fvgb_mpnn_s* fvgb_mpnn;
 
 typedef enum {
   FVGB_OK = 0,
@@ -277,6 +278,13 @@ typedef struct {
   int32_t bcset_ne;
   int32_t bcset_phi;
   fvgb_solve_opts solve;
+  fvgb_mpnn warm;        /* learned warm start (see fvgb_mpnn_*) or NULL: when set, each
+                            step after the first on this mesh predicts the increment of
+                            phi from the change of n_i - n_e since the previous step and
+                            phi, and starts the Poisson solve of every part from
+                            phi + prediction where that start has the smaller FP64
+                            residual ||b - A phi||, from phi elsewhere (the solve still
+                            converges to rtol either way) */
 } fvgb_streamer_params;
 
 /* ne_dev, ni_dev: [n_cell] real; phi_dev: [n_cell] double (in: guess, out: last
@@ -335,6 +343,47 @@ fvgb_status fvgb_stats_enable(fvgb_mesh m, int32_t time_cg);
 
 /* Copy the counters into *out (host); reset = 1 zeroes them afterwards. */
 fvgb_status fvgb_stats_get(fvgb_mesh m, fvgb_stats* out, int32_t reset);
+
+/* Forget the space charge of the previous streamer step on this mesh (the next step
+ * with a learned warm start then starts from phi alone and records the charge). */
+fvgb_status fvgb_streamer_reset(fvgb_mesh m);
+
+/* ---- Learned warm start (no counterpart in the paper) --------------------------------
+ * A message-passing network predicts the potential increment of a streamer step:
+ *   f_i = [ (e/eps0) dq_i mu_i^(2/3) / (V s0),  phi_prev_i / (V s1) ]
+ *   h = relu(W_enc f + b_enc) (width 64); 3 layers: m_i = sum_j w_ij (h_j - h_i) over the
+ *   interior faces (w = c1 / max c1 of set bcset), h = h + relu(W_l [h ; m] + b_l);
+ *   out = N(f) = w_dec . h + b_dec; increment = V s2 (N(f) - N(f with f0 = 0)), i.e. the
+ *   response to the charge change (what the network gives for an unchanged charge is
+ *   removed, so no change predicts no increment).
+ * Layer products run on the tensor cores (BF16 weights and activations, FP32
+ * accumulation); master weights, gradients and Adam state are FP32.
+ * Parameters: one FP32 vector of fvgb_mpnn_param_count() entries, blocks in order
+ * W_enc [64][2], b_enc [64], then per layer W_l [64][128] (inputs [h ; m]), b_l [64],
+ * then w_dec [64], b_dec [1]. A network belongs to one mesh; move weights between
+ * meshes with get/set. */
+fvgb_status fvgb_mpnn_create(fvgb_mesh m, int32_t bcset, fvgb_mpnn* out);
+fvgb_status fvgb_mpnn_free(fvgb_mpnn net);
+int64_t fvgb_mpnn_param_count(void);
+/* Set the FP32 parameters (host array) and reset the optimiser state. */
+fvgb_status fvgb_mpnn_set_params(fvgb_mpnn net, const float* theta_host);
+fvgb_status fvgb_mpnn_get_params(fvgb_mpnn net, float* theta_host);
+/* Input / output scales V, s0, s1, s2 (all > 0) of the formulas above. */
+fvgb_status fvgb_mpnn_set_scales(fvgb_mpnn net, double V, double s0, double s1, double s2);
+/* dphi_dev = predicted increment from dq_dev (change of n_i - n_e) and phi_prev_dev
+ * (all [n_cell] double, device). Stream-ordered, no synchronisation. */
+fvgb_status fvgb_mpnn_predict(fvgb_mpnn net, const double* dq_dev, const double* phi_prev_dev,
+                              double* dphi_dev, void* stream);
+/* Loss mean_i (pred_i - dphi_i / (V s2))^2, pred = N(f) - N(f0 = 0), and its gradient (host, param_count floats,
+ * or NULL) for one sample; synchronises the stream. */
+fvgb_status fvgb_mpnn_loss_grad(fvgb_mpnn net, const double* dq_dev, const double* phi_prev_dev,
+                                const double* dphi_dev, double* loss_host, float* grad_host,
+                                void* stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on one sample; loss_host may be NULL (then
+ * the call does not synchronise). */
+fvgb_status fvgb_mpnn_train_step(fvgb_mpnn net, const double* dq_dev, const double* phi_prev_dev,
+                                 const double* dphi_dev, float lr, double* loss_host,
+                                 void* stream);
 
 /* Message of the last failing call in this thread ("" if none). */
 const char* fvgb_last_error(void);

@@ -11,9 +11,10 @@ Architecture (per cell i; messages over interior faces, weight w_ij = c1_f / max
         m_i   = sum_j w_ij (h_j - h_i)
         z     = W_l [h ; m] + b_l                                 (64 x 128)
         h     = h + relu(z)
-    out_i = w_dec . h + b_dec
-    prediction delta phi_i = V s2 out_i;  loss = mean_i (out_i - t_i)^2,
-    t_i = delta phi_i / (V s2).
+    out_i = w_dec . h + b_dec = N(f)_i
+    prediction delta phi_i = V s2 (N(f) - N(f with f0 = 0))_i  (the response to the charge
+    change; the part the network would give for an unchanged charge is removed),
+    loss = mean_i (pred_i - t_i)^2,  pred = N(f) - N(f0 = 0),  t_i = delta phi_i / (V s2).
 
 Parameters are one flat vector (see ``layout``). ``forward`` keeps the activations,
 ``backward`` is the hand-derived gradient (message passing is symmetric, so its adjoint
@@ -96,18 +97,20 @@ def forward(graph, theta, f):
     return out, cache
 
 
+def predict(graph, theta, f):
+    """N(f) - N(f with the charge feature zeroed)."""
+    f_zero = f.copy()
+    f_zero[:, 0] = 0.0
+    return forward(graph, theta, f)[0] - forward(graph, theta, f_zero)[0]
+
+
 def loss(graph, theta, f, t):
-    out, _ = forward(graph, theta, f)
-    return float(np.mean((out - t) ** 2))
+    return float(np.mean((predict(graph, theta, f) - t) ** 2))
 
 
-def backward(graph, theta, f, t):
-    """(loss, gradient of the loss with respect to the flat parameter vector)."""
-    p = unpack(theta)
-    out, c = forward(graph, theta, f)
-    N = out.shape[0]
+def _backward_one(graph, p, c, dout):
+    """Gradient of sum_i dout_i N(f)_i for one forward cache."""
     g = {}
-    dout = 2.0 * (out - t) / N
     g["w_dec"] = c["h"][-1].T @ dout
     g["b_dec"] = np.array([dout.sum()])
     dh = np.outer(dout, p["w_dec"])
@@ -121,7 +124,20 @@ def backward(graph, theta, f, t):
     dz0 = dh * (c["z0"] > 0.0)
     g["W_enc"] = dz0.T @ c["f"]
     g["b_enc"] = dz0.sum(axis=0)
-    return float(np.mean((out - t) ** 2)), pack(g)
+    return pack(g)
+
+
+def backward(graph, theta, f, t):
+    """(loss, gradient of the loss with respect to the flat parameter vector)."""
+    p = unpack(theta)
+    f_zero = f.copy()
+    f_zero[:, 0] = 0.0
+    out_a, ca = forward(graph, theta, f)
+    out_b, cb = forward(graph, theta, f_zero)
+    pred = out_a - out_b
+    dout = 2.0 * (pred - t) / pred.shape[0]
+    grad = _backward_one(graph, p, ca, dout) - _backward_one(graph, p, cb, dout)
+    return float(np.mean((pred - t) ** 2)), grad
 
 
 def init_params(seed):

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfvgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["ops.cu", "solver.cu", "api.cu", "graph.cu", "tune.cu", "noalloc.cu"]
+CU_SOURCES = ["ops.cu", "solver.cu", "api.cu", "graph.cu", "tune.cu", "mpnn.cu", "noalloc.cu"]
 CPP_SOURCES = ["mesh_host.cpp"]
 
 

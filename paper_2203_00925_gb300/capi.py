@@ -34,7 +34,10 @@ EXPORTED = [
     "fvgb_permute", "fvgb_gradient", "fvgb_vertex_values", "fvgb_fv_residual",
     "fvgb_fv_residual_noalloc",
     "fvgb_fv_step", "fvgb_poisson_apply", "fvgb_poisson_rhs", "fvgb_poisson_solve",
-    "fvgb_streamer_step", "fvgb_set_graph_mode", "fvgb_autotune", "fvgb_set_launch_shape",
+    "fvgb_streamer_step", "fvgb_streamer_reset", "fvgb_set_graph_mode",
+    "fvgb_mpnn_create", "fvgb_mpnn_free", "fvgb_mpnn_param_count", "fvgb_mpnn_set_params",
+    "fvgb_mpnn_get_params", "fvgb_mpnn_set_scales", "fvgb_mpnn_predict", "fvgb_mpnn_loss_grad",
+    "fvgb_mpnn_train_step", "fvgb_autotune", "fvgb_set_launch_shape",
     "fvgb_integral", "fvgb_stats_enable", "fvgb_stats_get", "fvgb_last_error",
 ]
 
@@ -75,7 +78,7 @@ class fvgb_solve_info(C.Structure):
 class fvgb_streamer_params(C.Structure):
     _fields_ = [("mu", C.c_double), ("A", C.c_double), ("B", C.c_double), ("De", C.c_double),
                 ("dt", C.c_double), ("bcset_ne", C.c_int32), ("bcset_phi", C.c_int32),
-                ("solve", fvgb_solve_opts)]
+                ("solve", fvgb_solve_opts), ("warm", C.c_void_p)]
 
 
 class fvgb_stats(C.Structure):
@@ -114,6 +117,16 @@ _sig = {
                                      _i32, C.POINTER(fvgb_solve_info), _vp]),
     "fvgb_integral": (C.c_int, [_vp, _vp, C.POINTER(_d), _vp]),
     "fvgb_set_graph_mode": (C.c_int, [_vp, _i32]),
+    "fvgb_streamer_reset": (C.c_int, [_vp]),
+    "fvgb_mpnn_create": (C.c_int, [_vp, _i32, C.POINTER(_vp)]),
+    "fvgb_mpnn_free": (C.c_int, [_vp]),
+    "fvgb_mpnn_param_count": (C.c_int64, []),
+    "fvgb_mpnn_set_params": (C.c_int, [_vp, _vp]),
+    "fvgb_mpnn_get_params": (C.c_int, [_vp, _vp]),
+    "fvgb_mpnn_set_scales": (C.c_int, [_vp, _d, _d, _d, _d]),
+    "fvgb_mpnn_predict": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "fvgb_mpnn_loss_grad": (C.c_int, [_vp, _vp, _vp, _vp, C.POINTER(_d), _vp, _vp]),
+    "fvgb_mpnn_train_step": (C.c_int, [_vp, _vp, _vp, _vp, C.c_float, C.POINTER(_d), _vp]),
     "fvgb_autotune": (C.c_int, [_vp, _i32, _vp, _vp]),
     "fvgb_set_launch_shape": (C.c_int, [_vp, _i32, _i32, _i32]),
     "fvgb_stats_enable": (C.c_int, [_vp, _i32]),
@@ -328,9 +341,67 @@ def fvgb_poisson_solve(m, bcset, f, phi, opts, stream=None, check=True):
 
 
 def streamer_params(mu=0.0382, A=4332.0, B=2.0e5, De=0.1, dt=1e-9, bcset_ne=0, bcset_phi=1,
-                    solve=None):
+                    solve=None, warm=None):
     return fvgb_streamer_params(mu, A, B, De, dt, bcset_ne, bcset_phi,
-                                solve if solve is not None else solve_opts())
+                                solve if solve is not None else solve_opts(), warm)
+
+
+def fvgb_streamer_reset(m):
+    return _check(lib.fvgb_streamer_reset(m), "fvgb_streamer_reset")
+
+
+def fvgb_mpnn_create(m, bcset):
+    out = _vp()
+    _check(lib.fvgb_mpnn_create(m, bcset, C.byref(out)), "fvgb_mpnn_create")
+    return out.value
+
+
+def fvgb_mpnn_free(net):
+    return _check(lib.fvgb_mpnn_free(net), "fvgb_mpnn_free")
+
+
+def fvgb_mpnn_param_count():
+    return int(lib.fvgb_mpnn_param_count())
+
+
+def fvgb_mpnn_set_params(net, theta):
+    import numpy as np
+    t = np.ascontiguousarray(theta, dtype=np.float32)
+    return _check(lib.fvgb_mpnn_set_params(net, ptr(t)), "fvgb_mpnn_set_params")
+
+
+def fvgb_mpnn_get_params(net):
+    import numpy as np
+    t = np.empty(fvgb_mpnn_param_count(), dtype=np.float32)
+    _check(lib.fvgb_mpnn_get_params(net, ptr(t)), "fvgb_mpnn_get_params")
+    return t
+
+
+def fvgb_mpnn_set_scales(net, V, s0, s1, s2):
+    return _check(lib.fvgb_mpnn_set_scales(net, V, s0, s1, s2), "fvgb_mpnn_set_scales")
+
+
+def fvgb_mpnn_predict(net, dq, phi_prev, dphi, stream=None):
+    return _check(lib.fvgb_mpnn_predict(net, ptr(dq), ptr(phi_prev), ptr(dphi), stream_handle(stream)),
+                  "fvgb_mpnn_predict")
+
+
+def fvgb_mpnn_loss_grad(net, dq, phi_prev, dphi, want_grad=True, stream=None):
+    import numpy as np
+    loss = _d()
+    g = np.empty(fvgb_mpnn_param_count(), dtype=np.float32) if want_grad else None
+    _check(lib.fvgb_mpnn_loss_grad(net, ptr(dq), ptr(phi_prev), ptr(dphi), C.byref(loss),
+                                   ptr(g) if g is not None else None, stream_handle(stream)),
+           "fvgb_mpnn_loss_grad")
+    return loss.value, g
+
+
+def fvgb_mpnn_train_step(net, dq, phi_prev, dphi, lr, want_loss=False, stream=None):
+    loss = _d()
+    _check(lib.fvgb_mpnn_train_step(net, ptr(dq), ptr(phi_prev), ptr(dphi), float(lr),
+                                    C.byref(loss) if want_loss else None, stream_handle(stream)),
+           "fvgb_mpnn_train_step")
+    return loss.value if want_loss else None
 
 
 def fvgb_streamer_step(m, params, ne, ni, phi, E, nsteps, stream=None):

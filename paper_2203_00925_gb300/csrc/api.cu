@@ -371,6 +371,40 @@ fvgb_status solve_impl(fvgb_mesh m, int bcset, const double* f, double* phi,
 
 }  // namespace
 
+// Learned warm start: dq = (n_i - n_e) - previous; when predict, phi += prediction on
+// the parts where that start has the smaller FP64 residual ||b - A phi|| (the plain
+// start phi_prev elsewhere), so the solve from it is never started from a worse guess.
+fvgb_status warm_start(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, void* ni, double* phi,
+                       bool predict, cudaStream_t s) {
+  const int64_t N = m->topo.N;
+  const int P = m->parts.n_part;
+  if (!m->q_prev) {
+    FVGB_TRY(dalloc(m, &m->q_prev, N), "allocation");
+    FVGB_TRY(dalloc(m, &m->dq, N), "allocation");
+    FVGB_TRY(dalloc(m, &m->dphi_pred, N), "allocation");
+    FVGB_TRY(dalloc(m, &m->phi_save, N), "allocation");
+    FVGB_TRY(dalloc(m, &m->warm_norms, 2 * P), "allocation");
+    FVGB_TRY(dalloc(m, &m->warm_used, P), "allocation");
+    FVGB_TRY(cudaMemsetAsync(m->q_prev, 0, N * sizeof(double), s), "memset");
+  }
+  FVGB_TRY(launch_charge_delta(m, ne, ni, is_fp32(m), m->q_prev, m->dq, s), "charge kernel");
+  if (!predict) return FVGB_OK;
+  double* f = m->w64.tmp;
+  double* b = m->dphi_tmp2;
+  double* r = m->dphi_tmp;
+  FVGB_TRY(launch_poisson_source(m, ne, ni, is_fp32(m), f, s), "source kernel");
+  if (fvgb_status st = poisson_rhs_impl(m, p->bcset_phi, f, b, s)) return st;
+  FVGB_TRY(cudaMemcpyAsync(m->phi_save, phi, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+  if (fvgb_status st = poisson_residual(m, p->bcset_phi, phi, b, r, s)) return st;
+  FVGB_TRY(launch_part_sumsq(m, r, m->warm_norms, s), "norm kernel");
+  if (fvgb_status st = fvgb_mpnn_predict(p->warm, m->dq, phi, m->dphi_pred, s)) return st;
+  FVGB_TRY(launch_axpy_d(m->dphi_pred, 1.0, phi, N, s), "update");
+  if (fvgb_status st = poisson_residual(m, p->bcset_phi, phi, b, r, s)) return st;
+  FVGB_TRY(launch_part_sumsq(m, r, m->warm_norms + P, s), "norm kernel");
+  return cuda_status(launch_choose_start(m, m->warm_norms, m->warm_norms + P, m->phi_save, phi,
+                                         m->warm_used, s), "choose kernel");
+}
+
 // Field, cell physics and the transport update of one streamer step (after the solve).
 fvgb_status streamer_transport(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, void* ni,
                                const double* phi, void* E, cudaStream_t s) {
@@ -736,10 +770,20 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
   const bool fp32_solve = p->solve.prec == FVGB_FP32 || p->solve.prec == FVGB_MIXED;
   if (fp32_solve && !is_fp32(m)) { set_error("FP32 inner solve needs a mesh uploaded with FVGB_FP32 or FVGB_MIXED"); return FVGB_EINVAL; }
   cudaStream_t s = (cudaStream_t)stream;
-  if (m->use_graph) return streamer_graph_steps(m, p, ne, ni, phi, E, nsteps, info, s);
+  int n0 = 0;
+  if (m->use_graph) {
+    if (!p->warm || m->have_q_prev) return streamer_graph_steps(m, p, ne, ni, phi, E, nsteps, info, s);
+    n0 = nsteps > 0 ? nsteps - 1 : 0;   // first step host-driven: it records the charge
+    nsteps = nsteps > 0 ? 1 : 0;
+  }
   const bool fp32 = is_fp32(m);
   double* f = m->w64.tmp;   // FP64 scratch of the mesh (unused by the FP64 transport path)
   for (int n = 0; n < nsteps; ++n) {
+    if (p->warm) {
+      fvgb_status st = warm_start(m, p, ne, ni, phi, m->have_q_prev, s);
+      if (st) return st;
+      m->have_q_prev = true;
+    }
     fvgb_status st = cuda_status(launch_poisson_source(m, ne, ni, fp32, f, s), "source kernel");
     if (st) return st;
     st = solve_impl(m, p->bcset_phi, f, phi, &p->solve, info ? info + n : nullptr, s);
@@ -747,6 +791,14 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
     st = streamer_transport(m, p, ne, ni, phi, E, s);
     if (st) return st;
   }
+  if (n0 > 0) return streamer_graph_steps(m, p, ne, ni, phi, E, n0, info ? info + 1 : nullptr, s);
+  return FVGB_OK;
+}
+
+fvgb_status fvgb_streamer_reset(fvgb_mesh m) {
+  if (fvgb_status st = check_mesh(m)) return st;
+  m->have_q_prev = false;
+  if (m->q_prev) FVGB_TRY(cudaMemset(m->q_prev, 0, m->topo.N * sizeof(double)), "memset");
   return FVGB_OK;
 }
 

@@ -139,6 +139,13 @@ struct fvgb_mesh_s {
   bool cg_pending = false;              // events recorded, elapsed time not yet read
   int use_graph = 0;                    // run streamer steps as one CUDA graph each
   fvgb::LaunchShape tune[fvgb::kTuneCount];  // launch shapes (autotuned or default)
+  double* q_prev = nullptr;             // [N] n_i - n_e of the previous streamer step
+  double* dq = nullptr;                 // [N] its change (learned warm start input)
+  double* dphi_pred = nullptr;          // [N] predicted potential increment
+  double* phi_save = nullptr;           // [N] previous potential (plain start)
+  double* warm_norms = nullptr;         // [2][P] residual norms of the two starts
+  int* warm_used = nullptr;             // [P] 1 where the learned start was kept
+  bool have_q_prev = false;
   fvgb::GraphState* graph = nullptr;    // captured step graph (graph.cu)
   std::vector<void*> allocs;
 };
@@ -189,6 +196,10 @@ cudaError_t launch_poisson_source(fvgb_mesh_s* m, const void* ne, const void* ni
                                   double* f, cudaStream_t s);
 cudaError_t launch_sumsq(fvgb_mesh_s* m, const double* x, int64_t n, double* out, cudaStream_t s);
 cudaError_t launch_integral(fvgb_mesh_s* m, const void* u, bool fp32, double* out, cudaStream_t s);
+cudaError_t launch_charge_delta(fvgb_mesh_s* m, const void* ne, const void* ni, bool fp32,
+                                double* q_prev, double* dq, cudaStream_t s);
+cudaError_t launch_choose_start(fvgb_mesh_s* m, const double* na, const double* nb, const double* saved,
+                                double* phi, int* used, cudaStream_t s);
 cudaError_t launch_axpy_d(const double* x, double a, double* y, int64_t n, cudaStream_t s);
 cudaError_t launch_add_to_double(const void* x, bool fp32, double* y, int64_t n, cudaStream_t s);
 cudaError_t launch_convert(const double* x, float* y, int64_t n, cudaStream_t s);
@@ -210,6 +221,8 @@ fvgb_status poisson_rhs_impl(fvgb_mesh m, int bcset, const double* f, double* b,
 template <typename T>
 fvgb_status step_T(fvgb_mesh m, const fvgb_tcoef* tc, T* u, double dt, int nsteps,
                    const double* alpha, int nstage, T* ni_out, cudaStream_t s);
+fvgb_status warm_start(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, void* ni, double* phi,
+                       bool predict, cudaStream_t s);
 fvgb_status streamer_transport(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, void* ni,
                                const double* phi, void* E, cudaStream_t s);
 

@@ -429,6 +429,45 @@ cudaError_t launch_integral(fvgb_mesh_s* m, const void* u, bool fp32, double* ou
   return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void k_charge_delta(int64_t N, const T* __restrict__ ne, const T* __restrict__ ni,
+                               double* __restrict__ q_prev, double* __restrict__ dq) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double q = (double)ni[i] - (double)ne[i];
+    dq[i] = q - q_prev[i];
+    q_prev[i] = q;
+  }
+}
+
+cudaError_t launch_charge_delta(fvgb_mesh_s* m, const void* ne, const void* ni, bool fp32,
+                                double* q_prev, double* dq, cudaStream_t s) {
+  const int64_t N = m->topo.N;
+  if (fp32) k_charge_delta<float><<<grid_for(N), kThreads, 0, s>>>(N, (const float*)ne, (const float*)ni, q_prev, dq);
+  else k_charge_delta<double><<<grid_for(N), kThreads, 0, s>>>(N, (const double*)ne, (const double*)ni, q_prev, dq);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// per part: keep the learned start only where its residual is smaller (block p = part p)
+__global__ void k_choose_start(const double* __restrict__ na, const double* __restrict__ nb,
+                               const int32_t* __restrict__ part_sc, const int64_t* __restrict__ sc_begin,
+                               const double* __restrict__ saved, double* __restrict__ phi,
+                               int* __restrict__ used) {
+  const int p = blockIdx.x;
+  const bool keep = nb[p] < na[p];   // false for NaN as well
+  if (threadIdx.x == 0) used[p] = keep ? 1 : 0;
+  if (keep) return;
+  const int64_t lo = sc_begin[part_sc[p]], hi = sc_begin[part_sc[p + 1]];
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) phi[i] = saved[i];
+}
+
+cudaError_t launch_choose_start(fvgb_mesh_s* m, const double* na, const double* nb, const double* saved,
+                                double* phi, int* used, cudaStream_t s) {
+  k_choose_start<<<m->parts.n_part, 256, 0, s>>>(na, nb, m->parts.part_sc, m->parts.sc_begin, saved, phi, used);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_axpy_d(const double* x, double a, double* y, int64_t n, cudaStream_t s) {
   k_axpy_d<<<grid_for(n), kThreads, 0, s>>>(x, a, y, n);
   count_launch();

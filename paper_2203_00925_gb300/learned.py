@@ -1,0 +1,68 @@
+"""Learned warm start for the Poisson solve of the streamer step: data generation with
+the plain solver, training with the library's own forward/backward/Adam kernels, and
+evaluation against the plain warm start (the previous potential).
+
+The network, its gradients and the optimiser run in libfvgb (fvgb_mpnn_*); this module
+only orders the calls and keeps the training pairs on the device.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import capi
+
+E_OVER_EPS0 = 1.602176634e-19 / 8.8541878128e-12
+
+
+def streamer_run(dm, case, mesh, dt, steps, solve, warm=None, record=False, graph=False):
+    """Run ``steps`` streamer steps of one case from its initial state (phi from 0).
+    Returns per-step solve infos and, when ``record``, the training pairs
+    (dq, phi_prev, dphi) of steps 1..steps-1 as FP64 device tensors."""
+    ne0, ni0 = case.initial(mesh)
+    ne, ni = dm.to_device(ne0), dm.to_device(ni0)
+    phi = torch.zeros(dm.n_cell, dtype=torch.float64, device=dm.device)
+    sp = capi.streamer_params(mu=case.mu, A=case.A, B=case.B, De=case.De, dt=dt, solve=solve,
+                              warm=warm)
+    capi.fvgb_streamer_reset(dm.handle)
+    capi.fvgb_set_graph_mode(dm.handle, graph)
+    infos, pairs = [], []
+    q_prev = None
+    for s in range(steps):
+        q = (ni.double() - ne.double()) if record else None
+        phi_prev = phi.clone() if record else None
+        infos += capi.fvgb_streamer_step(dm.handle, sp, ne, ni, phi, None, 1)
+        if record and q_prev is not None:
+            pairs.append((q - q_prev, phi_prev, phi - phi_prev))
+        q_prev = q
+    capi.fvgb_set_graph_mode(dm.handle, False)
+    return infos, pairs
+
+
+def scales_for(pairs, V, n_cell):
+    """Normalisation of inputs and target from the training pairs: RMS of the charge
+    feature (with mu^(2/3) taken as the mean cell size squared), of phi / V, of dphi / V."""
+    h2 = (1.0 / n_cell) ** (2.0 / 3.0)
+    rq = float(torch.sqrt(torch.mean(torch.stack([torch.mean(p[0] ** 2) for p in pairs]))))
+    rp = float(torch.sqrt(torch.mean(torch.stack([torch.mean(p[1] ** 2) for p in pairs]))))
+    rd = float(torch.sqrt(torch.mean(torch.stack([torch.mean(p[2] ** 2) for p in pairs]))))
+    s0 = max(E_OVER_EPS0 * rq * h2 / V, 1e-30)
+    return s0, max(rp / V, 1e-30), max(rd / V, 1e-30)
+
+
+def train(net, pairs, epochs=2, lr=1e-3, seed=0, log_every=0):
+    """Adam over the pairs in a seeded random order; returns the loss history."""
+    rng = np.random.default_rng(seed)
+    hist = []
+    for ep in range(epochs):
+        for k, i in enumerate(rng.permutation(len(pairs))):
+            dq, phi_prev, dphi = pairs[i]
+            want = log_every and (k % log_every == 0)
+            l = capi.fvgb_mpnn_train_step(net, dq, phi_prev, dphi, lr, want_loss=bool(want))
+            if want:
+                hist.append((ep, k, l))
+    return hist
+
+
+def mean_loss(net, pairs):
+    return float(np.mean([capi.fvgb_mpnn_loss_grad(net, *p, want_grad=False)[0] for p in pairs]))
