@@ -15,6 +15,28 @@ from . import capi
 E_OVER_EPS0 = 1.602176634e-19 / 8.8541878128e-12
 
 
+def init_params(seed):
+    """Seeded initial parameters (FP32): weight matrices uniform in +-sqrt(6 / fan_in),
+    the decoder vector in +-sqrt(3 / 64), biases zero; layout of fvgb_mpnn_set_params."""
+    rng = np.random.default_rng(seed)
+    blocks = [("W", 64, 2), ("b", 64, 0)]
+    for _ in range(3):
+        blocks += [("W", 64, 128), ("b", 64, 0)]
+    blocks += [("d", 64, 0), ("b", 1, 0)]
+    out = []
+    for kind, n, fan in blocks:
+        if kind == "W":
+            bound = np.sqrt(6.0 / fan)
+            out.append(rng.uniform(-bound, bound, size=(n, fan)).ravel())
+        elif kind == "d":
+            out.append(rng.uniform(-np.sqrt(3.0 / 64), np.sqrt(3.0 / 64), size=n))
+        else:
+            out.append(np.zeros(n))
+    theta = np.concatenate(out).astype(np.float32)
+    assert theta.size == capi.fvgb_mpnn_param_count()
+    return theta
+
+
 def streamer_run(dm, case, mesh, dt, steps, solve, warm=None, record=False, graph=False):
     """Run ``steps`` streamer steps of one case from its initial state (phi from 0).
     Returns per-step solve infos and, when ``record``, the training pairs
