@@ -285,6 +285,11 @@ typedef struct {
                             phi + prediction where that start has the smaller FP64
                             residual ||b - A phi||, from phi elsewhere (the solve still
                             converges to rtol either way) */
+  int32_t extrapolate;   /* 1: start each solve from the linear extrapolation in time
+                            2 phi^{n-1} - phi^{n-2} (after two steps on this mesh); with
+                            a network, the network then predicts the extrapolation's
+                            error from the change of the charge change (its second
+                            difference in time) */
 } fvgb_streamer_params;
 
 /* ne_dev, ni_dev: [n_cell] real; phi_dev: [n_cell] double (in: guess, out: last
@@ -344,8 +349,8 @@ fvgb_status fvgb_stats_enable(fvgb_mesh m, int32_t time_cg);
 /* Copy the counters into *out (host); reset = 1 zeroes them afterwards. */
 fvgb_status fvgb_stats_get(fvgb_mesh m, fvgb_stats* out, int32_t reset);
 
-/* Forget the space charge of the previous streamer step on this mesh (the next step
- * with a learned warm start then starts from phi alone and records the charge). */
+/* Forget the warm-start history (earlier charges and potentials) of this mesh: the next
+ * steps start from phi alone until the history is rebuilt. */
 fvgb_status fvgb_streamer_reset(fvgb_mesh m);
 
 /* ---- Learned warm start (no counterpart in the paper) --------------------------------

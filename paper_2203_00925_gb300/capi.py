@@ -78,7 +78,7 @@ class fvgb_solve_info(C.Structure):
 class fvgb_streamer_params(C.Structure):
     _fields_ = [("mu", C.c_double), ("A", C.c_double), ("B", C.c_double), ("De", C.c_double),
                 ("dt", C.c_double), ("bcset_ne", C.c_int32), ("bcset_phi", C.c_int32),
-                ("solve", fvgb_solve_opts), ("warm", C.c_void_p)]
+                ("solve", fvgb_solve_opts), ("warm", C.c_void_p), ("extrapolate", C.c_int32)]
 
 
 class fvgb_stats(C.Structure):
@@ -341,9 +341,10 @@ def fvgb_poisson_solve(m, bcset, f, phi, opts, stream=None, check=True):
 
 
 def streamer_params(mu=0.0382, A=4332.0, B=2.0e5, De=0.1, dt=1e-9, bcset_ne=0, bcset_phi=1,
-                    solve=None, warm=None):
+                    solve=None, warm=None, extrapolate=False):
     return fvgb_streamer_params(mu, A, B, De, dt, bcset_ne, bcset_phi,
-                                solve if solve is not None else solve_opts(), warm)
+                                solve if solve is not None else solve_opts(), warm,
+                                int(bool(extrapolate)))
 
 
 def fvgb_streamer_reset(m):

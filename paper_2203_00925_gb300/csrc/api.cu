@@ -371,24 +371,34 @@ fvgb_status solve_impl(fvgb_mesh m, int bcset, const double* f, double* phi,
 
 }  // namespace
 
-// Learned warm start: dq = (n_i - n_e) - previous; when predict, phi += prediction on
-// the parts where that start has the smaller FP64 residual ||b - A phi|| (the plain
-// start phi_prev elsewhere), so the solve from it is never started from a worse guess.
+bool warm_requested(const fvgb_streamer_params* p) { return p->warm || p->extrapolate; }
+
+// Warm start of the Poisson solve of a streamer step, given ``hist`` earlier steps:
+//  - charge history: dq = change of n_i - n_e since the previous step, d2q its change;
+//  - base start: phi (the previous potential), or with extrapolation and two earlier
+//    steps 2 phi - phi_old (linear in time);
+//  - learned correction (when p->warm): the network's increment from dq (base = phi) or
+//    from d2q (base = extrapolation, whose error is the increment's change), added on
+//    the parts where that start has the smaller FP64 residual ||b - A phi||.
 fvgb_status warm_start(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, void* ni, double* phi,
-                       bool predict, cudaStream_t s) {
+                       int hist, cudaStream_t s) {
   const int64_t N = m->topo.N;
   const int P = m->parts.n_part;
   if (!m->q_prev) {
     FVGB_TRY(dalloc(m, &m->q_prev, N), "allocation");
     FVGB_TRY(dalloc(m, &m->dq, N), "allocation");
+    FVGB_TRY(dalloc(m, &m->d2q, N), "allocation");
+    FVGB_TRY(dalloc(m, &m->phi_old, N), "allocation");
     FVGB_TRY(dalloc(m, &m->dphi_pred, N), "allocation");
     FVGB_TRY(dalloc(m, &m->phi_save, N), "allocation");
     FVGB_TRY(dalloc(m, &m->warm_norms, 2 * P), "allocation");
     FVGB_TRY(dalloc(m, &m->warm_used, P), "allocation");
-    FVGB_TRY(cudaMemsetAsync(m->q_prev, 0, N * sizeof(double), s), "memset");
   }
-  FVGB_TRY(launch_charge_delta(m, ne, ni, is_fp32(m), m->q_prev, m->dq, s), "charge kernel");
-  if (!predict) return FVGB_OK;
+  FVGB_TRY(launch_charge_hist(m, ne, ni, is_fp32(m), hist, m->q_prev, m->dq, m->d2q, s), "charge kernel");
+  const bool extrap = p->extrapolate && hist >= 2;
+  FVGB_TRY(launch_extrapolate(m, extrap, phi, m->phi_old, s), "extrapolation kernel");
+  const bool learn = p->warm && hist >= (p->extrapolate ? 2 : 1);
+  if (!learn) return FVGB_OK;
   double* f = m->w64.tmp;
   double* b = m->dphi_tmp2;
   double* r = m->dphi_tmp;
@@ -397,7 +407,8 @@ fvgb_status warm_start(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, voi
   FVGB_TRY(cudaMemcpyAsync(m->phi_save, phi, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
   if (fvgb_status st = poisson_residual(m, p->bcset_phi, phi, b, r, s)) return st;
   FVGB_TRY(launch_part_sumsq(m, r, m->warm_norms, s), "norm kernel");
-  if (fvgb_status st = fvgb_mpnn_predict(p->warm, m->dq, phi, m->dphi_pred, s)) return st;
+  if (fvgb_status st = fvgb_mpnn_predict(p->warm, p->extrapolate ? m->d2q : m->dq, m->phi_old,
+                                         m->dphi_pred, s)) return st;
   FVGB_TRY(launch_axpy_d(m->dphi_pred, 1.0, phi, N, s), "update");
   if (fvgb_status st = poisson_residual(m, p->bcset_phi, phi, b, r, s)) return st;
   FVGB_TRY(launch_part_sumsq(m, r, m->warm_norms + P, s), "norm kernel");
@@ -771,18 +782,21 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
   if (fp32_solve && !is_fp32(m)) { set_error("FP32 inner solve needs a mesh uploaded with FVGB_FP32 or FVGB_MIXED"); return FVGB_EINVAL; }
   cudaStream_t s = (cudaStream_t)stream;
   int n0 = 0;
+  const bool warm = warm_requested(p);
   if (m->use_graph) {
-    if (!p->warm || m->have_q_prev) return streamer_graph_steps(m, p, ne, ni, phi, E, nsteps, info, s);
-    n0 = nsteps > 0 ? nsteps - 1 : 0;   // first step host-driven: it records the charge
-    nsteps = nsteps > 0 ? 1 : 0;
+    // a captured step assumes a full warm-start history: build it with host-driven steps
+    const int need = warm ? std::max(0, 2 - m->warm_hist) : 0;
+    if (need == 0) return streamer_graph_steps(m, p, ne, ni, phi, E, nsteps, info, s);
+    n0 = std::max(0, nsteps - need);
+    nsteps = std::min(nsteps, need);
   }
   const bool fp32 = is_fp32(m);
   double* f = m->w64.tmp;   // FP64 scratch of the mesh (unused by the FP64 transport path)
   for (int n = 0; n < nsteps; ++n) {
-    if (p->warm) {
-      fvgb_status st = warm_start(m, p, ne, ni, phi, m->have_q_prev, s);
+    if (warm) {
+      fvgb_status st = warm_start(m, p, ne, ni, phi, m->warm_hist, s);
       if (st) return st;
-      m->have_q_prev = true;
+      m->warm_hist = std::min(2, m->warm_hist + 1);
     }
     fvgb_status st = cuda_status(launch_poisson_source(m, ne, ni, fp32, f, s), "source kernel");
     if (st) return st;
@@ -791,14 +805,14 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
     st = streamer_transport(m, p, ne, ni, phi, E, s);
     if (st) return st;
   }
-  if (n0 > 0) return streamer_graph_steps(m, p, ne, ni, phi, E, n0, info ? info + 1 : nullptr, s);
+  if (n0 > 0) return streamer_graph_steps(m, p, ne, ni, phi, E, n0, info ? info + nsteps : nullptr, s);
   return FVGB_OK;
 }
 
 fvgb_status fvgb_streamer_reset(fvgb_mesh m) {
   if (fvgb_status st = check_mesh(m)) return st;
-  m->have_q_prev = false;
-  if (m->q_prev) FVGB_TRY(cudaMemset(m->q_prev, 0, m->topo.N * sizeof(double)), "memset");
+  m->warm_hist = 0;
+  graph_invalidate(m);
   return FVGB_OK;
 }
 

@@ -145,7 +145,7 @@ fvgb_status build_graph(fvgb_mesh m, GraphState& g, const fvgb_streamer_params* 
     return s2;
   };
   // ---- before the loop
-  if (p->warm && (st = warm_start(m, p, ne, ni, phi, true, g.cs))) return bail(st);
+  if (warm_requested(p) && (st = warm_start(m, p, ne, ni, phi, 2, g.cs))) return bail(st);
   if ((st = cuda_status(launch_poisson_source(m, ne, ni, is_fp32(m), f, g.cs), "source kernel"))) return bail(st);
   if ((st = poisson_rhs_impl(m, p->bcset_phi, f, b, g.cs))) return bail(st);
   if ((st = cuda_status(launch_part_sumsq(m, b, g.bn2, g.cs), "norm kernel"))) return bail(st);

@@ -139,13 +139,16 @@ struct fvgb_mesh_s {
   bool cg_pending = false;              // events recorded, elapsed time not yet read
   int use_graph = 0;                    // run streamer steps as one CUDA graph each
   fvgb::LaunchShape tune[fvgb::kTuneCount];  // launch shapes (autotuned or default)
-  double* q_prev = nullptr;             // [N] n_i - n_e of the previous streamer step
-  double* dq = nullptr;                 // [N] its change (learned warm start input)
-  double* dphi_pred = nullptr;          // [N] predicted potential increment
-  double* phi_save = nullptr;           // [N] previous potential (plain start)
+  // warm-start history of the streamer (allocated when a warm start is requested)
+  double* q_prev = nullptr;             // [N] n_i - n_e of the previous step
+  double* dq = nullptr;                 // [N] latest change of n_i - n_e
+  double* d2q = nullptr;                // [N] its change since the step before
+  double* phi_old = nullptr;            // [N] potential of the step before the last
+  double* dphi_pred = nullptr;          // [N] learned correction
+  double* phi_save = nullptr;           // [N] start without the learned correction
   double* warm_norms = nullptr;         // [2][P] residual norms of the two starts
   int* warm_used = nullptr;             // [P] 1 where the learned start was kept
-  bool have_q_prev = false;
+  int warm_hist = 0;                    // streamer steps recorded in the history (capped at 2)
   fvgb::GraphState* graph = nullptr;    // captured step graph (graph.cu)
   std::vector<void*> allocs;
 };
@@ -196,8 +199,9 @@ cudaError_t launch_poisson_source(fvgb_mesh_s* m, const void* ne, const void* ni
                                   double* f, cudaStream_t s);
 cudaError_t launch_sumsq(fvgb_mesh_s* m, const double* x, int64_t n, double* out, cudaStream_t s);
 cudaError_t launch_integral(fvgb_mesh_s* m, const void* u, bool fp32, double* out, cudaStream_t s);
-cudaError_t launch_charge_delta(fvgb_mesh_s* m, const void* ne, const void* ni, bool fp32,
-                                double* q_prev, double* dq, cudaStream_t s);
+cudaError_t launch_charge_hist(fvgb_mesh_s* m, const void* ne, const void* ni, bool fp32, int hist,
+                               double* q_prev, double* dq, double* d2q, cudaStream_t s);
+cudaError_t launch_extrapolate(fvgb_mesh_s* m, bool extrap, double* phi, double* phi_old, cudaStream_t s);
 cudaError_t launch_choose_start(fvgb_mesh_s* m, const double* na, const double* nb, const double* saved,
                                 double* phi, int* used, cudaStream_t s);
 cudaError_t launch_axpy_d(const double* x, double a, double* y, int64_t n, cudaStream_t s);
@@ -222,7 +226,8 @@ template <typename T>
 fvgb_status step_T(fvgb_mesh m, const fvgb_tcoef* tc, T* u, double dt, int nsteps,
                    const double* alpha, int nstage, T* ni_out, cudaStream_t s);
 fvgb_status warm_start(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, void* ni, double* phi,
-                       bool predict, cudaStream_t s);
+                       int hist, cudaStream_t s);
+bool warm_requested(const fvgb_streamer_params* p);
 fvgb_status streamer_transport(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, void* ni,
                                const double* phi, void* E, cudaStream_t s);
 

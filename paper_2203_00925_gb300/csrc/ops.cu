@@ -429,21 +429,43 @@ cudaError_t launch_integral(fvgb_mesh_s* m, const void* u, bool fp32, double* ou
   return cudaGetLastError();
 }
 
+// Charge history of the warm start: q = n_i - n_e; with one earlier step dq = q - q_prev,
+// with two d2q = dq - dq_prev; then q_prev = q, dq_prev = dq (dq holds both).
 template <typename T>
-__global__ void k_charge_delta(int64_t N, const T* __restrict__ ne, const T* __restrict__ ni,
-                               double* __restrict__ q_prev, double* __restrict__ dq) {
+__global__ void k_charge_hist(int64_t N, const T* __restrict__ ne, const T* __restrict__ ni, int hist,
+                              double* __restrict__ q_prev, double* __restrict__ dq, double* __restrict__ d2q) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const double q = (double)ni[i] - (double)ne[i];
-    dq[i] = q - q_prev[i];
+    if (hist >= 1) {
+      const double d = q - q_prev[i];
+      if (hist >= 2) d2q[i] = d - dq[i];
+      dq[i] = d;
+    }
     q_prev[i] = q;
   }
 }
 
-cudaError_t launch_charge_delta(fvgb_mesh_s* m, const void* ne, const void* ni, bool fp32,
-                                double* q_prev, double* dq, cudaStream_t s) {
+cudaError_t launch_charge_hist(fvgb_mesh_s* m, const void* ne, const void* ni, bool fp32, int hist,
+                               double* q_prev, double* dq, double* d2q, cudaStream_t s) {
   const int64_t N = m->topo.N;
-  if (fp32) k_charge_delta<float><<<grid_for(N), kThreads, 0, s>>>(N, (const float*)ne, (const float*)ni, q_prev, dq);
-  else k_charge_delta<double><<<grid_for(N), kThreads, 0, s>>>(N, (const double*)ne, (const double*)ni, q_prev, dq);
+  if (fp32) k_charge_hist<float><<<grid_for(N), kThreads, 0, s>>>(N, (const float*)ne, (const float*)ni, hist, q_prev, dq, d2q);
+  else k_charge_hist<double><<<grid_for(N), kThreads, 0, s>>>(N, (const double*)ne, (const double*)ni, hist, q_prev, dq, d2q);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// phi_old <- phi and, when extrapolating, phi <- 2 phi - phi_old (linear in time)
+__global__ void k_extrapolate(int64_t N, int extrap, double* __restrict__ phi, double* __restrict__ phi_old) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double o = phi[i];
+    if (extrap) phi[i] = 2.0 * o - phi_old[i];
+    phi_old[i] = o;
+  }
+}
+
+cudaError_t launch_extrapolate(fvgb_mesh_s* m, bool extrap, double* phi, double* phi_old, cudaStream_t s) {
+  const int64_t N = m->topo.N;
+  k_extrapolate<<<grid_for(N), kThreads, 0, s>>>(N, extrap ? 1 : 0, phi, phi_old);
   count_launch();
   return cudaGetLastError();
 }

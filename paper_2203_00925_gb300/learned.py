@@ -37,28 +37,39 @@ def init_params(seed):
     return theta
 
 
-def streamer_run(dm, case, mesh, dt, steps, solve, warm=None, record=False, graph=False):
+def streamer_run(dm, case, mesh, dt, steps, solve, warm=None, extrapolate=False, record=False,
+                 graph=False):
     """Run ``steps`` streamer steps of one case from its initial state (phi from 0).
-    Returns per-step solve infos and, when ``record``, the training pairs
-    (dq, phi_prev, dphi) of steps 1..steps-1 as FP64 device tensors."""
+
+    Returns per-step solve infos and, when ``record``, two lists of training pairs as FP64
+    device tensors: (dq, phi_prev, dphi) for a start from the previous potential (steps
+    1..) and (d2q, phi_prev, dphi - dphi_prev) for a start from the linear extrapolation in
+    time (steps 2..), where dq is the change of n_i - n_e between step starts and d2q the
+    change of dq."""
     ne0, ni0 = case.initial(mesh)
     ne, ni = dm.to_device(ne0), dm.to_device(ni0)
     phi = torch.zeros(dm.n_cell, dtype=torch.float64, device=dm.device)
     sp = capi.streamer_params(mu=case.mu, A=case.A, B=case.B, De=case.De, dt=dt, solve=solve,
-                              warm=warm)
+                              warm=warm, extrapolate=extrapolate)
     capi.fvgb_streamer_reset(dm.handle)
     capi.fvgb_set_graph_mode(dm.handle, graph)
-    infos, pairs = [], []
-    q_prev = None
+    infos, plain_pairs, extrap_pairs = [], [], []
+    qh, ph = [], []          # charges at the last step starts, potentials of the last steps
     for s in range(steps):
-        q = (ni.double() - ne.double()) if record else None
-        phi_prev = phi.clone() if record else None
+        if record:
+            qh = (qh + [ni.double() - ne.double()])[-3:]
         infos += capi.fvgb_streamer_step(dm.handle, sp, ne, ni, phi, None, 1)
-        if record and q_prev is not None:
-            pairs.append((q - q_prev, phi_prev, phi - phi_prev))
-        q_prev = q
+        if record:
+            ph = (ph + [phi.clone()])[-3:]
+            if len(qh) >= 2:
+                plain_pairs.append((qh[-1] - qh[-2], ph[-2], ph[-1] - ph[-2]))
+            if len(qh) >= 3:
+                extrap_pairs.append(((qh[-1] - qh[-2]) - (qh[-2] - qh[-3]), ph[-2],
+                                     ph[-1] - 2.0 * ph[-2] + ph[-3]))
     capi.fvgb_set_graph_mode(dm.handle, False)
-    return infos, pairs
+    if record:
+        return infos, plain_pairs, extrap_pairs
+    return infos, []
 
 
 def scales_for(pairs, V, n_cell):

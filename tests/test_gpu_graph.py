@@ -83,3 +83,31 @@ def test_graph_counts_launches(dev):
     assert st["kernel_launches"] > 10 * 2
     assert st["solves"] == 2 and st["outer_its"] == sum(i["outer_its"] for i in infos)
     dm.free()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_extrapolated_start_graph_matches_host_and_saves_iterations(dev, prec):
+    capi, device = dev
+    m = jittered_cube(16, seed=301)
+    case = StreamerCase()
+    dm = device.DeviceMesh(m, [case.bc_ne(), case.bc_phi()], prec=prec)
+    ne0 = case.initial(m)[0]
+    solve = capi.solve_opts(rtol=1e-8, prec=capi.FVGB_FP64 if prec == "fp64" else capi.FVGB_FP32)
+    outs = {}
+    for graph, extrap in ((False, False), (False, True), (True, True)):
+        ne, ni = dm.to_device(ne0), dm.to_device(ne0)
+        phi = torch.zeros(dm.n_cell, dtype=torch.float64, device="cuda")
+        sp = capi.streamer_params(mu=case.mu, A=case.A, B=case.B, De=case.De, dt=case.dt(1.0 / 16),
+                                  solve=solve, extrapolate=extrap)
+        capi.fvgb_streamer_reset(dm.handle)
+        capi.fvgb_set_graph_mode(dm.handle, graph)
+        infos = capi.fvgb_streamer_step(dm.handle, sp, ne, ni, phi, None, 12)
+        torch.cuda.synchronize()
+        outs[(graph, extrap)] = (ne, ni, phi, infos)
+    for x, y in zip(outs[(False, True)][:3], outs[(True, True)][:3]):
+        assert torch.equal(x, y)
+    plain = sum(i["inner_its_total"] for i in outs[(False, False)][3][3:])
+    extr = sum(i["inner_its_total"] for i in outs[(False, True)][3][3:])
+    assert all(i["rel_res"] <= 1e-8 for i in outs[(False, True)][3])
+    assert extr < 0.6 * plain, (extr, plain)
+    dm.free()
