@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-transport", action="store_true")
+    ap.add_argument("--transport-only", default=None, choices=["fp32", "fp64", "both"],
+                    help="time only the transport kernels on the 6M-cell mesh (for profiling)")
     return ap.parse_args()
 
 
@@ -180,6 +183,74 @@ def profile_traffic(kernel, shash):
     return None
 
 
+TRANSPORT_K = 100          # 6 * 100^3 = 6,000,000 cells: every array well above L2
+TRANSPORT_SEED = 301
+
+
+def transport_kernels(capi, device, torch, stream, flush, precs, reps=10, warm=3):
+    """The transport operators on the 6M-cell mesh, each timed alone between CUDA events
+    with L2 flushed before every repetition; achieved GB/s from the algorithmic bytes
+    (each array element counted once, gathered neighbour values as cache hits)."""
+    import numpy as np
+    from synth.workloads import StreamerCase, streamer_mesh
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    hbm = float(peaks["hbm_gbs"])
+    case = StreamerCase()
+    mesh = streamer_mesh(TRANSPORT_K, TRANSPORT_SEED)
+    out = {"mesh": f"unit cube, {TRANSPORT_K}^3 x 6 Kuhn tets, seed {TRANSPORT_SEED}",
+           "peak_GBps": hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+           "l2": "flushed before each repetition (256 MiB write, untimed)"}
+    for prec in precs:
+        dm = device.DeviceMesh(mesh, [case.bc_ne(), case.bc_phi()], prec=prec)
+        N, F, V, NN = dm.n_cell, dm.n_face, dm.n_vert, dm.n_nbr
+        w = 8 if prec == "fp64" else 4
+        rng = np.random.default_rng(1)
+        cen = mesh.vertex_mean()
+        u = dm.to_device(np.sin(cen @ np.array([2.1, 1.3, 2.9])) + 0.1 * rng.random(N) + 1.0)
+        vel = dm.to_device(rng.normal(size=(3, N)))
+        src = dm.to_device(rng.normal(size=N))
+        g, uv, res = dm.empty(3, N), dm.empty(V), dm.empty(N)
+        tc = capi.tcoef(vel=vel, diff=0.1, src=src, bcset=0)
+        calls = {
+            # node-neighbour indices + u + M^-1 (6) + centre (3) + gradient out (3)
+            "gradient": (lambda: capi.fvgb_gradient(dm.handle, 1, u, g),
+                         4 * NN + N * 13 * w),
+            # star indices + weights (4 per cell) + u + vertex values out
+            "vertex_values": (lambda: capi.fvgb_vertex_values(dm.handle, 0, u, uv),
+                              4 * N * (4 + w) + N * w + V * w),
+            # vertex values, then per face L, R, A, B, C + 3 coefficients + area vector
+            # (3) + flux, then cell_face (4) + fluxes + u, velocity (3), source, 1/mu, out
+            "fv_residual": (lambda: capi.fvgb_fv_residual(dm.handle, tc, u, res),
+                            4 * N * (4 + w) + N * w + V * w
+                            + F * (20 + 7 * w) + V * w
+                            + N * (16 + 7 * w) + F * w),
+        }
+        r = {"cells": N, "faces": F, "vertices": V, "node_neighbour_entries": NN}
+        t_end = time.time() + 0.5                 # bring the clocks up before timing
+        while time.time() < t_end:
+            for fn, _ in calls.values():
+                fn()
+            torch.cuda.synchronize()
+        for name, (fn, nbytes) in calls.items():
+            for _ in range(warm):
+                fn()
+            ms = []
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            med = statistics.median(ms)
+            r[name] = {"ms": med, "algorithmic_bytes": nbytes, "GBps": nbytes / med / 1e6,
+                       "frac_of_measured_hbm": nbytes / med / 1e6 / hbm}
+        out[prec] = r
+        dm.free()
+    return out
+
+
 def gpu_arm(args, world, rank, local):
     import numpy as np
     import torch
@@ -196,6 +267,12 @@ def gpu_arm(args, world, rank, local):
     from paper_2203_00925_gb300 import capi, device
     from synth.workloads import StreamerCase, streamer_mesh
 
+    if args.transport_only:
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        precs = ["fp32", "fp64"] if args.transport_only == "both" else [args.transport_only]
+        print(json.dumps(transport_kernels(capi, device, torch, torch.cuda.current_stream(),
+                                           flush, precs)), flush=True)
+        return
     case = StreamerCase()
     mesh = streamer_mesh(K_MESH, MESH_SEED)
     dm = device.DeviceMesh(mesh, [case.bc_ne(), case.bc_phi()], prec="fp64")
@@ -409,6 +486,10 @@ def gpu_arm(args, world, rank, local):
         e2e = {"value": world * N * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": 3 * N * 8, "d2h_bytes_per_step": 3 * N * 8}
 
+    transport = None
+    if world == 1 and not args.no_transport:
+        transport = transport_kernels(capi, device, torch, stream, flush, ["fp32", "fp64"])
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         steps_cpu = 5
@@ -433,6 +514,7 @@ def gpu_arm(args, world, rank, local):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "variants": variants,
+            "transport_kernels": transport,
             "gpu_launches": stats["kernel_launches"],
             "clocks": clk,
         }

@@ -70,6 +70,7 @@ struct Work {
   T* vel = nullptr;    // [d][N]
   T* src = nullptr;    // [N]
   T* grad = nullptr;   // [d][N]
+  T* grec = nullptr;   // [N] packed gradient records (FP64: 4 words, FP32: 8 words)
   T* cg_r = nullptr;   // [N]
   T* cg_p = nullptr;
   T* cg_q = nullptr;

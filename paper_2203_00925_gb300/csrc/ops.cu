@@ -9,6 +9,7 @@
 // floating-point atomics).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
@@ -40,33 +41,120 @@ __device__ __forceinline__ float cdiff(const float* a, const float* alo, int64_t
   return (a[ia] - b[ib]) + (alo[ia] - blo[ib]);
 }
 
+// Explicitly rounded operations: the face flux is written with them so that its rounding
+// sequence (which products are fused) is fixed by the source, not by how the compiler
+// schedules a particular instantiation; every launch shape then gives the same bits.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // ---- Algorithm "grad": grad u_i = M_i^{-1} sum_j d_ij (u_j - u_i) ------------------------
+// The neighbour loop reads, per neighbour j, one packed 32-byte record (one memory sector)
+// holding u_j and the centre of j, written by k_grad_pack for this call:
+//   FP64: {u, x, y, z};  FP32: {u, x_hi, y_hi, z_hi, x_lo, y_lo, z_lo, 0}
+// (FP32 keeps each coordinate as a high + low float pair so that differences of nearby
+// centres keep FP32 relative accuracy). Unused components (2D) are 0.
+template <int D>
+__global__ void __launch_bounds__(1024)
+k_grad_pack(int64_t N, const double* __restrict__ cen, const double* __restrict__,
+            const double* __restrict__ u, double* __restrict__ rec) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double2* o = reinterpret_cast<double2*>(rec) + 2 * i;
+    o[0] = make_double2(u[i], cen[i]);
+    o[1] = make_double2(cen[N + i], D == 3 ? cen[2 * N + i] : 0.0);
+  }
+}
+template <int D>
+__global__ void __launch_bounds__(1024)
+k_grad_pack(int64_t N, const float* __restrict__ cen, const float* __restrict__ lo,
+            const float* __restrict__ u, float* __restrict__ rec) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float4* o = reinterpret_cast<float4*>(rec) + 2 * i;
+    o[0] = make_float4(u[i], cen[i], cen[N + i], D == 3 ? cen[2 * N + i] : 0.0f);
+    o[1] = make_float4(lo[i], lo[N + i], D == 3 ? lo[2 * N + i] : 0.0f, 0.0f);
+  }
+}
+
+// A neighbour's record, and its contribution d_ij (u_j - u_i) to J (the centre
+// difference from high and low parts in FP32).
+__device__ __forceinline__ void grad_load(const double* rec, int64_t j, double2& a, double2& b) {
+  const double2* r = reinterpret_cast<const double2*>(rec) + 2 * j;
+  a = __ldg(r);
+  b = __ldg(r + 1);
+}
+__device__ __forceinline__ void grad_load(const float* rec, int64_t j, float4& a, float4& b) {
+  const float4* r = reinterpret_cast<const float4*>(rec) + 2 * j;
+  a = __ldg(r);
+  b = __ldg(r + 1);
+}
+template <int D>
+__device__ __forceinline__ void grad_acc(const double2& a, const double2& b, const double2& ia,
+                                         const double2& ib, double* J) {
+  const double du = a.x - ia.x;
+  J[0] += (a.y - ia.y) * du;
+  J[1] += (b.x - ib.x) * du;
+  if (D == 3) J[2] += (b.y - ib.y) * du;
+}
+template <int D>
+__device__ __forceinline__ void grad_acc(const float4& a, const float4& b, const float4& ia,
+                                         const float4& ib, float* J) {
+  const float du = a.x - ia.x;
+  J[0] += ((a.y - ia.y) + (b.x - ib.x)) * du;
+  J[1] += ((a.z - ia.z) + (b.y - ib.y)) * du;
+  if (D == 3) J[2] += ((a.w - ia.w) + (b.z - ib.z)) * du;
+}
+
+template <typename T> struct GradVec;
+template <> struct GradVec<double> { using type = double2; };
+template <> struct GradVec<float> { using type = float4; };
+
 template <typename T, int D>
 __global__ void __launch_bounds__(1024)
 k_gradient(int64_t N, int64_t F, int64_t Fi, const int64_t* __restrict__ sptr,
-           const int32_t* __restrict__ sidx, const T* __restrict__ cen,
-           const T* __restrict__ cen_lo, const T* __restrict__ xf, const T* __restrict__ xf_lo,
-           const T* __restrict__ u, const T* __restrict__ minv, const int32_t* __restrict__ gptr,
-           const int32_t* __restrict__ gface, const T* __restrict__ bval, T* __restrict__ grad) {
+           const int32_t* __restrict__ sidx, const T* __restrict__ rec,
+           const T* __restrict__ cen, const T* __restrict__ cen_lo, const T* __restrict__ xf,
+           const T* __restrict__ xf_lo, const T* __restrict__ u, const T* __restrict__ minv,
+           const int32_t* __restrict__ gptr, const int32_t* __restrict__ gface,
+           const T* __restrict__ bval, T* __restrict__ grad) {
+  using Vec = typename GradVec<T>::type;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t sl = i >> 5;
     const int lane = (int)(i & 31);
-    const int64_t b0 = sptr[sl], b1 = sptr[sl + 1];
-    const T ui = u[i];
-    T J[D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) J[a] = T(0);
-    for (int64_t p = b0 + lane; p < b1; p += 32) {
-      const int32_t j = __ldg(sidx + p);
-      const T du = u[j] - ui;
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const T dx = cdiff(cen + a * N, cen_lo ? cen_lo + a * N : nullptr, j, cen + a * N,
-                           cen_lo ? cen_lo + a * N : nullptr, i);
-        J[a] += dx * du;
-      }
+    const int64_t b0 = sptr[sl];
+    const int width = (int)((sptr[sl + 1] - b0) >> 5);   // every row of a slice has it
+    const int32_t* col = sidx + b0 + lane;
+    Vec ia, ib;
+    grad_load(rec, i, ia, ib);
+    T J[3] = {T(0), T(0), T(0)};
+    int c = 0;
+    for (; c + 4 <= width; c += 4) {      // four independent gathers in flight
+      const int32_t j0 = __ldg(col + 32 * c), j1 = __ldg(col + 32 * (c + 1)),
+                    j2 = __ldg(col + 32 * (c + 2)), j3 = __ldg(col + 32 * (c + 3));
+      Vec a0, b0v, a1, b1v, a2, b2v, a3, b3v;
+      grad_load(rec, j0, a0, b0v);
+      grad_load(rec, j1, a1, b1v);
+      grad_load(rec, j2, a2, b2v);
+      grad_load(rec, j3, a3, b3v);
+      grad_acc<D>(a0, b0v, ia, ib, J);
+      grad_acc<D>(a1, b1v, ia, ib, J);
+      grad_acc<D>(a2, b2v, ia, ib, J);
+      grad_acc<D>(a3, b3v, ia, ib, J);
     }
+    for (; c < width; ++c) {
+      const int32_t j = __ldg(col + 32 * c);
+      Vec a, b;
+      grad_load(rec, j, a, b);
+      grad_acc<D>(a, b, ia, ib, J);
+    }
+    const T ui = u[i];
     for (int32_t t = gptr[i]; t < gptr[i + 1]; ++t) {
       const int32_t f = gface[t];
       const T du = bval[f - Fi] - ui;
@@ -101,9 +189,24 @@ k_vertex(int64_t V, const int64_t* __restrict__ sptr, const int32_t* __restrict_
        v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t sl = v >> 5;
     const int lane = (int)(v & 31);
-    const int64_t b0 = sptr[sl], b1 = sptr[sl + 1];
+    const int64_t b0 = sptr[sl];
+    const int width = (int)((sptr[sl + 1] - b0) >> 5);   // every row of a slice has it
+    const int32_t* col = sidx + b0 + lane;
+    const T* wcol = alpha + b0 + lane;
     T s = T(0);
-    for (int64_t p = b0 + lane; p < b1; p += 32) s += alpha[p] * u[__ldg(sidx + p)];
+    int c = 0;
+    for (; c + 4 <= width; c += 4) {      // four independent gathers in flight
+      const int32_t j0 = __ldg(col + 32 * c), j1 = __ldg(col + 32 * (c + 1)),
+                    j2 = __ldg(col + 32 * (c + 2)), j3 = __ldg(col + 32 * (c + 3));
+      const T w0 = wcol[32 * c], w1 = wcol[32 * (c + 1)], w2 = wcol[32 * (c + 2)],
+              w3 = wcol[32 * (c + 3)];
+      const T u0 = u[j0], u1 = u[j1], u2 = u[j2], u3 = u[j3];
+      s = fma_rn(w0, u0, s);
+      s = fma_rn(w1, u1, s);
+      s = fma_rn(w2, u2, s);
+      s = fma_rn(w3, u3, s);
+    }
+    for (; c < width; ++c) s = fma_rn(wcol[32 * c], u[__ldg(col + 32 * c)], s);
     const T g = vdir[v];
     if (g == g) s = homog ? T(0) : g;  // Dirichlet vertex (vdir is NaN elsewhere)
     uv[v] = s;
@@ -111,58 +214,96 @@ k_vertex(int64_t V, const int64_t* __restrict__ sptr, const int32_t* __restrict_
 }
 
 // ---- face flux: F = (V_f . S_f) u_up - D grad u_f . S_f (eq. 4, eq. 15, eq. "diamond") ----
-template <typename T, int D, bool CONV, bool VFIELD>
-__global__ void __launch_bounds__(1024)
+// Each thread takes K faces (block-contiguous, stride blockDim): it issues the streamed
+// face data of all K first, then all their gathers, then computes, so that K faces'
+// loads are in flight together. The arithmetic of one face does not depend on K.
+template <typename T, int D, bool CONV, bool VFIELD, int K>
+__global__ void __launch_bounds__(1024 / K)
 k_face(int64_t F, int64_t Fi, int64_t N, const int32_t* __restrict__ fL,
        const int32_t* __restrict__ fR, const int32_t* __restrict__ fvert,
        const T* __restrict__ S, const T* __restrict__ coef, const T* __restrict__ u,
        const T* __restrict__ uv, const T* __restrict__ vel, T vc0, T vc1, T vc2, T Dcoef,
        const int8_t* __restrict__ bkind, const T* __restrict__ bval, int homog,
        T* __restrict__ flux) {
-  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < F;
-       f += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t L = fL[f];
-    const T uL = u[L];
-    int kind = 3;  // interior
-    int32_t R = -1;
-    T uR;
-    if (f < Fi) {
-      R = fR[f];
-      uR = u[R];
-    } else {
-      kind = bkind[f - Fi];
-      if (kind == FVGB_BC_WALL) { flux[f] = T(0); continue; }
-      uR = kind == FVGB_BC_DIRICHLET ? (homog ? T(0) : bval[f - Fi]) : uL;
+  constexpr int kInterior = 3;
+  const int64_t per_block = (int64_t)blockDim.x * K;
+  for (int64_t base = blockIdx.x * per_block + threadIdx.x; base < F;
+       base += (int64_t)gridDim.x * per_block) {
+    int32_t L[K], R[K], vA[K], vB[K], vC[K];
+    int kind[K];
+    T s0[K], s1[K], s2[K], c0[K], c1[K], c2[K], gb[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {           // streamed face data (in bounds: clamped)
+      const int64_t f = min(base + (int64_t)k * blockDim.x, F - 1);
+      L[k] = fL[f];
+      if (f < Fi) {
+        R[k] = fR[f];
+        kind[k] = kInterior;
+        gb[k] = T(0);
+      } else {
+        R[k] = -1;
+        kind[k] = bkind[f - Fi];
+        gb[k] = homog ? T(0) : bval[f - Fi];
+      }
+      if (CONV) {
+        s0[k] = S[f]; s1[k] = S[F + f];
+        s2[k] = D == 3 ? S[2 * F + f] : T(0);
+      }
+      c0[k] = coef[f]; c1[k] = coef[F + f];
+      c2[k] = D == 3 ? coef[2 * F + f] : T(0);
+      vA[k] = fvert[f]; vB[k] = fvert[F + f];
+      vC[k] = D == 3 ? fvert[2 * F + f] : 0;
     }
-    T Ff = T(0);
-    if (CONV) {
-      T vf[3];
-      if (VFIELD) {
+    T uL[K], uR[K], ua[K], ub[K], uc[K], vl[K][3], vr[K][3];
+    const bool diff = Dcoef != T(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {           // gathers
+      uL[k] = u[L[k]];
+      uR[k] = R[k] >= 0 ? u[R[k]] : T(0);
+      if (CONV && VFIELD) {
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-          const T vl = vel[a * N + L];
-          const T vr = R >= 0 ? vel[a * N + R] : vl;
-          vf[a] = T(0.5) * (vl + vr);
+          vl[k][a] = vel[a * N + L[k]];
+          vr[k][a] = R[k] >= 0 ? vel[a * N + R[k]] : vl[k][a];
         }
-      } else {
-        vf[0] = vc0; vf[1] = vc1; vf[2] = vc2;
       }
-      T vn = vf[0] * S[f] + vf[1] * S[F + f];
-      if (D == 3) vn += vf[2] * S[2 * F + f];
-      Ff = vn * (vn >= T(0) ? uL : uR);
+      const bool need_uv = diff && (kind[k] == kInterior || kind[k] == FVGB_BC_DIRICHLET);
+      ua[k] = need_uv ? uv[vA[k]] : T(0);
+      ub[k] = need_uv ? uv[vB[k]] : T(0);
+      uc[k] = need_uv && D == 3 ? uv[vC[k]] : T(0);
     }
-    if (Dcoef != T(0) && (kind == 3 || kind == FVGB_BC_DIRICHLET)) {
-      T q;
-      if constexpr (D == 3) {
-        const T ua = uv[fvert[f]], ub = uv[fvert[F + f]], uc = uv[fvert[2 * F + f]];
-        q = coef[f] * (uR - uL) + coef[F + f] * (ua - uc) + coef[2 * F + f] * (ub - uc);
-      } else {
-        const T ua = uv[fvert[f]], ub = uv[fvert[F + f]];
-        q = coef[f] * (uR - uL) + coef[F + f] * (ub - ua);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t f = base + (int64_t)k * blockDim.x;
+      if (f >= F) break;
+      if (kind[k] == FVGB_BC_WALL) { flux[f] = T(0); continue; }
+      const T ul = uL[k];
+      const T ur = kind[k] == kInterior ? uR[k] : (kind[k] == FVGB_BC_DIRICHLET ? gb[k] : ul);
+      T Ff = T(0);
+      if (CONV) {
+        T vf[3];
+        if (VFIELD) {
+#pragma unroll
+          for (int a = 0; a < D; ++a) vf[a] = mul_rn(T(0.5), add_rn(vl[k][a], vr[k][a]));
+        } else {
+          vf[0] = vc0; vf[1] = vc1; vf[2] = vc2;
+        }
+        T vn = fma_rn(vf[1], s1[k], mul_rn(vf[0], s0[k]));
+        if (D == 3) vn = fma_rn(vf[2], s2[k], vn);
+        Ff = mul_rn(vn, vn >= T(0) ? ul : ur);
       }
-      Ff -= Dcoef * q;
+      if (diff && (kind[k] == kInterior || kind[k] == FVGB_BC_DIRICHLET)) {
+        T q = mul_rn(c0[k], sub_rn(ur, ul));
+        if constexpr (D == 3) {
+          q = fma_rn(c1[k], sub_rn(ua[k], uc[k]), q);
+          q = fma_rn(c2[k], sub_rn(ub[k], uc[k]), q);
+        } else {
+          q = fma_rn(c1[k], sub_rn(ub[k], ua[k]), q);
+        }
+        Ff = fma_rn(-Dcoef, q, Ff);
+      }
+      flux[f] = Ff;
     }
-    flux[f] = Ff;
   }
 }
 
@@ -318,13 +459,20 @@ cudaError_t launch_gradient(fvgb_mesh_s* m, int bcset, const T* u, T* grad, cuda
   const TopoDev& t = m->topo;
   GeoDev<T>& g = geo_of<T>(m);
   const BCDev<T>& b = g.bc[bcset];
-  if (t.dim == 3)
-    k_gradient<T, 3><<<shape_grid(m, kTuneGrad, t.N), m->tune[kTuneGrad].threads, 0, s>>>(t.N, t.F, t.Fi, t.nsell.ptr, t.nsell.idx,
-        g.cen, g.cen_lo, g.xf, g.xf_lo, u, b.minv, b.gptr, b.gface, b.bval, grad);
-  else
-    k_gradient<T, 2><<<shape_grid(m, kTuneGrad, t.N), m->tune[kTuneGrad].threads, 0, s>>>(t.N, t.F, t.Fi, t.nsell.ptr, t.nsell.idx,
-        g.cen, g.cen_lo, g.xf, g.xf_lo, u, b.minv, b.gptr, b.gface, b.bval, grad);
-  count_launch();
+  T* rec = work_of<T>(m).grec;
+  const unsigned gp = grid_for(t.N);
+  const unsigned gg = shape_grid(m, kTuneGrad, t.N);
+  const int tg = m->tune[kTuneGrad].threads;
+  if (t.dim == 3) {
+    k_grad_pack<3><<<gp, kThreads, 0, s>>>(t.N, g.cen, g.cen_lo, u, rec);
+    k_gradient<T, 3><<<gg, tg, 0, s>>>(t.N, t.F, t.Fi, t.nsell.ptr, t.nsell.idx, rec, g.cen,
+        g.cen_lo, g.xf, g.xf_lo, u, b.minv, b.gptr, b.gface, b.bval, grad);
+  } else {
+    k_grad_pack<2><<<gp, kThreads, 0, s>>>(t.N, g.cen, g.cen_lo, u, rec);
+    k_gradient<T, 2><<<gg, tg, 0, s>>>(t.N, t.F, t.Fi, t.nsell.ptr, t.nsell.idx, rec, g.cen,
+        g.cen_lo, g.xf, g.xf_lo, u, b.minv, b.gptr, b.gface, b.bval, grad);
+  }
+  count_launch(2);
   return cudaGetLastError();
 }
 
@@ -345,12 +493,27 @@ cudaError_t launch_face(fvgb_mesh_s* m, int bcset, const T* u, const T* uv, cons
   GeoDev<T>& g = geo_of<T>(m);
   const BCDev<T>& b = g.bc[bcset];
   const T v0 = vc ? (T)vc[0] : T(0), v1 = vc ? (T)vc[1] : T(0), v2 = vc ? (T)vc[2] : T(0);
-  const unsigned gr = shape_grid(m, kTuneFace, t.F);
-  const int tb = m->tune[kTuneFace].threads;
-#define FVGB_FACE(DD, CV, VF)                                                                   \
-  k_face<T, DD, CV, VF><<<gr, tb, 0, s>>>(t.F, t.Fi, t.N, t.fL, t.fR, t.fvert, g.S, g.coef, \
-                                                u, uv, vel, v0, v1, v2, (T)D, b.bkind, b.bval,  \
-                                                homog ? 1 : 0, flux)
+  // K faces per thread (FP64 face fluxes of an FP32 mesh, the Poisson residual, are bound
+  // by the FP64 pipe and take K = 1); blocks of at most 1024 / K threads (the kernel's launch bound)
+  auto face_grid = [&](int K, int& tb) {
+    tb = std::min(m->tune[kTuneFace].threads, 1024 / K);
+    return (unsigned)std::max<int64_t>(1, (t.F + (int64_t)tb * K - 1) / ((int64_t)tb * K));
+  };
+  const int ipt = sizeof(T) == 8 && is_fp32(m) ? 1 : m->tune[kTuneFace].ipt;
+  int tb = 0;
+#define FVGB_FACE_K(DD, CV, VF, KK)                                                         \
+  do {                                                                                      \
+    const unsigned gr_ = face_grid(KK, tb);                                                 \
+    k_face<T, DD, CV, VF, KK><<<gr_, tb, 0, s>>>(t.F, t.Fi, t.N, t.fL, t.fR, t.fvert, g.S,  \
+                                                 g.coef, u, uv, vel, v0, v1, v2, (T)D,      \
+                                                 b.bkind, b.bval, homog ? 1 : 0, flux);     \
+  } while (0)
+#define FVGB_FACE(DD, CV, VF)                                          \
+  do {                                                                 \
+    if (ipt >= 4) FVGB_FACE_K(DD, CV, VF, 4);                          \
+    else if (ipt == 2) FVGB_FACE_K(DD, CV, VF, 2);                     \
+    else FVGB_FACE_K(DD, CV, VF, 1);                                   \
+  } while (0)
   if (t.dim == 3) {
     if (!conv) FVGB_FACE(3, false, false);
     else if (vel) FVGB_FACE(3, true, true);
@@ -361,6 +524,7 @@ cudaError_t launch_face(fvgb_mesh_s* m, int bcset, const T* u, const T* uv, cons
     else FVGB_FACE(2, true, false);
   }
 #undef FVGB_FACE
+#undef FVGB_FACE_K
   count_launch();
   return cudaGetLastError();
 }
