@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-transport", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--transport-only", default=None, choices=["fp32", "fp64", "both"],
                     help="time only the transport kernels on the 6M-cell mesh (for profiling)")
     return ap.parse_args()
@@ -248,6 +249,65 @@ def transport_kernels(capi, device, torch, stream, flush, precs, reps=10, warm=3
                        "frac_of_measured_hbm": nbytes / med / 1e6 / hbm}
         out[prec] = r
         dm.free()
+    return out
+
+
+ENSEMBLE_MESHES, ENSEMBLE_SEED, ENSEMBLE_STEPS = 64, 5000, 50
+
+
+def ensemble_block(capi, device, torch, stream, warm, nets):
+    """64 independent meshes (cell counts log-uniform in 20k-1M, own seed position and
+    voltage each) packed into one index space and advanced together: mixed precision,
+    autotuned launch shapes, each step one CUDA graph; every part's solve to 1e-8."""
+    import numpy as np
+    from synth.workloads import ensemble_cases, streamer_mesh
+    cases = ensemble_cases(ENSEMBLE_MESHES, seed=ENSEMBLE_SEED)
+    t0 = time.time()
+    meshes = [streamer_mesh(k, seed) for k, seed, _ in cases]
+    dm = device.DeviceMesh(meshes, [[c.bc_ne(), c.bc_phi()] for _, _, c in cases], prec="mixed",
+                           ensemble=True)
+    upload_s = time.time() - t0
+    capi.fvgb_autotune(dm.handle)
+    ne0 = np.concatenate([c.initial(m)[0] for m, (_, _, c) in zip(meshes, cases)])
+    c0 = cases[0][2]
+    dt = min(c.dt(1.0 / k) for k, _, c in cases)
+    out = {"meshes": len(cases), "cells": dm.n_cell, "faces": dm.n_face,
+           "cells_min_max": [int(min(m.n_cell for m in meshes)), int(max(m.n_cell for m in meshes))],
+           "steps": ENSEMBLE_STEPS, "warmup": warm, "dt": dt, "build_and_upload_s": upload_s}
+    runs = {"mixed_graph": (None, False), "extrapolated_mixed_graph": (None, True)}
+    if nets is not None:
+        runs["learned_extrapolated_mixed_graph"] = (nets[True], True)
+    for name, (theta_sc, extrap) in runs.items():
+        net = None
+        if theta_sc is not None:
+            net = capi.fvgb_mpnn_create(dm.handle, 1)
+            capi.fvgb_mpnn_set_params(net, theta_sc[0])
+            capi.fvgb_mpnn_set_scales(net, c0.V, *theta_sc[1])
+        sp = capi.streamer_params(mu=c0.mu, A=c0.A, B=c0.B, De=c0.De, dt=dt, warm=net,
+                                  extrapolate=extrap,
+                                  solve=capi.solve_opts(rtol=RTOL, inner_rtol=0.1, prec=capi.FVGB_FP32))
+        ne, ni = dm.to_device(ne0), dm.to_device(ne0)
+        phi = torch.zeros(dm.n_cell, dtype=torch.float64, device="cuda")
+        capi.fvgb_streamer_reset(dm.handle)
+        capi.fvgb_set_graph_mode(dm.handle, True)
+        capi.fvgb_streamer_step(dm.handle, sp, ne, ni, phi, None, warm)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = capi.fvgb_streamer_step(dm.handle, sp, ne, ni, phi, None, ENSEMBLE_STEPS)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        rel, _, _ = capi.fvgb_solve_parts(dm.handle, dm.n_part)
+        out[name] = {"ms_per_step": ms / ENSEMBLE_STEPS, "value": dm.n_cell * ENSEMBLE_STEPS / (ms / 1e3),
+                     "max_rel_res_last_step_over_parts": float(np.max(rel)),
+                     "max_rel_res": max(i["rel_res"] for i in infos),
+                     "outer_its_per_step": sum(i["outer_its"] for i in infos) / len(infos),
+                     "inner_cg_its_per_step_max_part": sum(i["inner_its_total"] for i in infos) / len(infos)}
+        capi.fvgb_set_graph_mode(dm.handle, False)
+        if net:
+            capi.fvgb_mpnn_free(net)
+    dm.free()
     return out
 
 
@@ -486,6 +546,11 @@ def gpu_arm(args, world, rank, local):
         e2e = {"value": world * N * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": 3 * N * 8, "d2h_bytes_per_step": 3 * N * 8}
 
+    ensemble = None
+    if world == 1 and not args.no_ensemble:
+        ensemble = ensemble_block(capi, device, torch, stream, args.warmup,
+                                  nets if variants is not None else None)
+
     transport = None
     if world == 1 and not args.no_transport:
         transport = transport_kernels(capi, device, torch, stream, flush, ["fp32", "fp64"])
@@ -514,6 +579,7 @@ def gpu_arm(args, world, rank, local):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "variants": variants,
+            "ensemble": ensemble,
             "transport_kernels": transport,
             "gpu_launches": stats["kernel_launches"],
             "clocks": clk,

@@ -286,6 +286,13 @@ fvgb_status streamer_graph_steps(fvgb_mesh m, const fvgb_streamer_params* p, voi
     FVGB_TRY(cudaGraphLaunch(g.exec, s), "graph launch");
     FVGB_TRY(cudaMemcpyAsync(g.h_info + n, g.info, sizeof(StepInfoDev), cudaMemcpyDeviceToHost, s), "copy");
   }
+  // per-part results of the last solve, for fvgb_solve_parts
+  m->last_rel.assign(P, 0.0);
+  m->last_outer.assign(P, 0);
+  m->last_inner.assign(P, 0);
+  FVGB_TRY(cudaMemcpyAsync(m->last_rel.data(), g.rel, P * sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+  FVGB_TRY(cudaMemcpyAsync(m->last_outer.data(), g.outer, P * sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+  FVGB_TRY(cudaMemcpyAsync(m->last_inner.data(), g.inner, P * sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
   FVGB_TRY(cudaStreamSynchronize(s), "synchronize");
   fvgb_status first = FVGB_OK;
   for (int n = 0; n < nsteps; ++n) {

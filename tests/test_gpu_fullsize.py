@@ -9,6 +9,8 @@
   oracle's residual of the GPU potential over the whole mesh <= 1e-8, and n_e, n_i and
   E on 256 sampled cells, each from the oracle on the patch of cells it depends on,
   within 1e-5.
+* the 64-mesh ensemble (about 15.4M cells, mixed precision, graph mode, extrapolated
+  start): the same two checks on its smallest, a middle and its largest mesh.
 """
 import numpy as np
 import pytest
@@ -165,3 +167,57 @@ def test_streamer_step_6m_mixed_sampled(dev):
     assert rel(got_ne[sample], sne[pos]) < TOL32
     assert rel(got_ni[sample], sni[pos]) < TOL32
     assert rel(got_E[sample], sE[pos]) < TOL32
+
+
+def test_ensemble_64_meshes_sampled(dev):
+    """The 64-mesh ensemble (about 15.4M cells) as the benchmark runs it: mixed precision,
+    autotuned launch shapes, graph mode, extrapolated start. After three steps, on the
+    smallest, a middle and the largest mesh: the oracle's residual of that part's potential
+    (whole part) <= 1e-8, and n_e, n_i, E on sampled cells from the oracle on patches
+    within 1e-5. Every part's own relative residual <= 1e-8."""
+    capi, device = dev
+    from synth.workloads import ensemble_cases
+    cases = ensemble_cases(64, seed=5000)
+    meshes = [streamer_mesh(k, seed) for k, seed, _ in cases]
+    dm = device.DeviceMesh(meshes, [[c.bc_ne(), c.bc_phi()] for _, _, c in cases], prec="mixed",
+                           ensemble=True)
+    capi.fvgb_autotune(dm.handle)
+    c0 = cases[0][2]
+    dt = min(c.dt(1.0 / k) for k, _, c in cases)
+    sp = capi.streamer_params(mu=c0.mu, A=c0.A, B=c0.B, De=c0.De, dt=dt, extrapolate=True,
+                              solve=bench_solve(capi, "mixed"))
+    ne0 = np.concatenate([c.initial(m)[0] for m, (_, _, c) in zip(meshes, cases)])
+    ne, ni = dm.to_device(ne0), dm.to_device(ne0)
+    phi = torch.zeros(dm.n_cell, dtype=torch.float64, device="cuda")
+    capi.fvgb_streamer_reset(dm.handle)
+    capi.fvgb_set_graph_mode(dm.handle, True)
+    capi.fvgb_streamer_step(dm.handle, sp, ne, ni, phi, None, 2)
+    torch.cuda.synchronize()
+    ne_h = dm.to_host(ne).astype(np.float64)
+    ni_h = dm.to_host(ni).astype(np.float64)
+    E = dm.empty(3, dm.n_cell)
+    info = capi.fvgb_streamer_step(dm.handle, sp, ne, ni, phi, E, 1)[0]
+    torch.cuda.synchronize()
+    rel_parts, _, _ = capi.fvgb_solve_parts(dm.handle, dm.n_part)
+    phi_h, got_ne, got_ni, got_E = dm.to_host(phi), dm.to_host(ne), dm.to_host(ni), dm.to_host(E).T
+    dm.free()
+    assert info["rel_res"] <= 1e-8 and np.max(rel_parts) <= 1e-8
+    begin = np.concatenate([[0], np.cumsum([m.n_cell for m in meshes])])
+    sizes = np.array([m.n_cell for m in meshes])
+    order = np.argsort(sizes)
+    rng = np.random.default_rng(5064)
+    for p in (order[0], order[len(order) // 2], order[-1]):
+        m, case = meshes[p], cases[p][2]
+        sl = slice(begin[p], begin[p + 1])
+        prm = oracle_params(case)
+        g = geometry_of(m)
+        f = streamer.poisson_source(ne_h[sl], ni_h[sl])
+        assert poisson.relative_residual(g, streamer.bc_phi(prm), f, phi_h[sl]) <= 1.01e-8
+        del g
+        sample = np.unique(rng.choice(m.n_cell, 96, replace=False))
+        sub, ids, pos = patch(m, sample)
+        gs = geometry_of(sub)
+        sne, sni, _, sE, _ = streamer.step(gs, prm, ne_h[sl][ids], ni_h[sl][ids], dt, phi=phi_h[sl][ids])
+        assert rel(got_ne[sl][sample], sne[pos]) < TOL32
+        assert rel(got_ni[sl][sample], sni[pos]) < TOL32
+        assert rel(got_E[sl][sample], sE[pos]) < TOL32

@@ -31,7 +31,7 @@ def _run(capi, dm, case, ne0, ni0, nsteps, graph, prec):
     capi.fvgb_set_graph_mode(dm.handle, graph)
     infos = capi.fvgb_streamer_step(dm.handle, sp, ne, ni, phi, E, nsteps)
     torch.cuda.synchronize()
-    return ne, ni, phi, E, infos
+    return ne, ni, phi, E, infos, capi.fvgb_solve_parts(dm.handle, dm.n_part)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -58,6 +58,9 @@ def test_graph_step_matches_host_loop_bitwise(dev, prec, ensemble):
         assert ia["outer_its"] == ib["outer_its"] and ia["inner_its_total"] == ib["inner_its_total"]
         assert ia["rel_res"] == pytest.approx(ib["rel_res"], rel=1e-12)
         assert ib["rel_res"] <= 1e-9
+    # per-part results of the last solve are reported after graph steps too
+    for pa, pb in zip(a[5], b[5]):
+        np.testing.assert_allclose(pa, pb, rtol=1e-12)
     # the graph is recaptured for other arrays and still agrees
     c = _run(capi, dm, case, ne0, ni0, 4, True, prec)
     for x, y in zip(a[:4], c[:4]):
