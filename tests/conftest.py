@@ -28,3 +28,30 @@ def square12():
 def geometry_of(m):
     from oracle.geometry import Geometry
     return Geometry(m.dim, m.xyz, m.cells, m.bface_vert, m.bface_tag)
+
+
+ANNEX_BC = {1: ("dirichlet", 10.0), 2: ("dirichlet", 0.0), 3: ("neumann", 0.0),
+            4: ("neumann", 0.0), 5: ("neumann", 0.0), 6: ("neumann", 0.0)}
+
+
+def load_annex():
+    """The Annex Poisson example fixture: (mesh, expected cell values P = 10 (1 - x))."""
+    import numpy as np
+    from synth.meshgen import Mesh
+    path = os.path.join(ROOT, "tests", "golden", "annex_laplace.txt")
+    lines = [ln for ln in open(path) if not ln.startswith("#")]
+    pos = 0
+
+    def block():
+        nonlocal pos
+        n = int(lines[pos].split()[1])
+        rows = [ln.split() for ln in lines[pos + 1:pos + 1 + n]]
+        pos += 1 + n
+        return rows
+
+    xyz = np.array(block(), dtype=np.float64)
+    cells = np.array(block(), dtype=np.int32)
+    bf = np.array(block(), dtype=np.int64)
+    expected = np.array(block(), dtype=np.float64).ravel()
+    mesh = Mesh(3, xyz, cells, bf[:, :3].astype(np.int32), bf[:, 3].astype(np.int32), 1.0 / 3)
+    return mesh, expected

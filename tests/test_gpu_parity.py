@@ -222,6 +222,21 @@ def test_poisson_annex_on_gpu(dev):
     dm.free()
 
 
+def test_annex_golden_fixture_on_gpu(dev):
+    """The stored Annex example (tests/golden/annex_laplace.txt): the GPU solve gives the
+    closed-form cell values."""
+    capi, device = dev
+    from tests.conftest import ANNEX_BC, load_annex
+    m, expected = load_annex()
+    for prec in ("fp64", "mixed"):
+        dm = device.DeviceMesh(m, [ANNEX_BC], prec=prec)
+        phi = torch.zeros(dm.n_cell, dtype=torch.float64, device="cuda")
+        capi.fvgb_poisson_solve(dm.handle, 0, None, phi, capi.solve_opts(
+            rtol=1e-12, prec=capi.FVGB_FP64 if prec == "fp64" else capi.FVGB_FP32))
+        assert np.abs(dm.to_host(phi) - expected).max() < 1e-9
+        dm.free()
+
+
 def test_solver_error_paths(dev):
     capi, device = dev
     m, bcs = meshes()["cube7"]
