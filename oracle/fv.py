@@ -10,6 +10,11 @@ Readings (shared with the GPU library, which implements them on its own):
   Dirichlet boundary face R is the face centroid and u_R = g.
 * Upwind (eq. 15 with psi = 0): u_f = u_L when V_f.S_f >= 0, else u_R, with
   V_f = (V_L + V_R) / 2 for a cell-centred velocity.
+* MUSCL (eq. 15, recon = 1): the upwind side's value is reconstructed,
+  u_f = u_c + psi_c grad u_c . (x_f - x_c), with the least-squares gradient of
+  Algorithm "grad" (same boundary conditions) and the Barth-Jespersen limiter psi_c
+  (see ``bj_limiter``). A boundary ghost on the upwind side keeps its first-order
+  value (g on Dirichlet faces, u_L on Neumann faces).
 * Boundary kinds: "wall" - no flux at all; "neumann" (homogeneous) - the ghost
   copies the interior (u_R = u_L, V_R = V_L), no diffusive flux; "dirichlet" - the
   ghost value is g, V_R = V_L.
@@ -76,8 +81,56 @@ def face_velocity(geo, vel):
     return 0.5 * (vel[L] + VR)
 
 
-def face_flux(geo, bc, u, vel, D, coef=None, weights=None):
-    """F_f = (V_f.S_f) u_f - D grad u_f.S_f, oriented L -> R (eq. 4, eq. 15)."""
+def bj_limiter(geo, bc, u, grad):
+    """Barth-Jespersen limiter psi_i of eq. 15 (the paper names the limiter; this is its
+    standard definition, Barth and Jespersen 1989), with these readings of its stencil:
+
+    * bounds u_min_i, u_max_i: over u_i, the values of the cells sharing a face with T_i
+      and the boundary values g of T_i's Dirichlet faces (a wall or Neumann face adds
+      nothing: its ghost is absent or equals u_i);
+    * every face f of T_i (boundary faces included) has the unlimited increment
+      d_f = grad u_i . (x_f - x_i) and the ratio phi_f = min(1, (u_max_i - u_i) / d_f)
+      if d_f > 0, min(1, (u_min_i - u_i) / d_f) if d_f < 0, and 1 if d_f = 0;
+    * psi_i = min over the faces of T_i of phi_f.
+    """
+    u = np.asarray(u, dtype=np.float64)
+    grad = np.asarray(grad, dtype=np.float64)
+    L, R = geo.face_L, geo.face_R
+    inr = R >= 0
+    g = ls.dirichlet_values(geo, bc)
+    dirf = np.isfinite(g)
+    umax, umin = u.copy(), u.copy()
+    for a, b in ((L[inr], u[R[inr]]), (R[inr], u[L[inr]]), (L[dirf], g[dirf])):
+        np.maximum.at(umax, a, b)
+        np.minimum.at(umin, a, b)
+    psi = np.ones(geo.n_cell)
+    for cells, keep in ((L, np.ones(geo.n_face, dtype=bool)), (R, inr)):
+        c = cells[keep]
+        d = np.einsum("fi,fi->f", grad[c], geo.xf[keep] - geo.cen[c])
+        phi = np.ones(c.size)
+        pos, neg = d > 0.0, d < 0.0
+        phi[pos] = np.minimum(1.0, (umax[c[pos]] - u[c[pos]]) / d[pos])
+        phi[neg] = np.minimum(1.0, (umin[c[neg]] - u[c[neg]]) / d[neg])
+        np.minimum.at(psi, c, phi)
+    return psi
+
+
+def muscl_states(geo, bc, u, grad=None):
+    """(u_Lf, u_Rf, psi): the reconstructed values of the two cells of every face,
+    u_c + psi_c grad u_c . (x_f - x_c); u_Rf is NaN on boundary faces."""
+    u = np.asarray(u, dtype=np.float64)
+    grad = ls.ls_gradient(geo, bc, u) if grad is None else np.asarray(grad, dtype=np.float64)
+    psi = bj_limiter(geo, bc, u, grad)
+    L, R = geo.face_L, geo.face_R
+    Rs = np.maximum(R, 0)
+    uLf = u[L] + psi[L] * np.einsum("fi,fi->f", grad[L], geo.xf - geo.cen[L])
+    uRf = u[Rs] + psi[Rs] * np.einsum("fi,fi->f", grad[Rs], geo.xf - geo.cen[Rs])
+    return uLf, np.where(R >= 0, uRf, np.nan), psi
+
+
+def face_flux(geo, bc, u, vel, D, coef=None, weights=None, recon=0):
+    """F_f = (V_f.S_f) u_f - D grad u_f.S_f, oriented L -> R (eq. 4, eq. 15); recon = 1
+    takes u_f from the limited MUSCL reconstruction."""
     geo.check_bc(bc)
     u = np.asarray(u, dtype=np.float64)
     L, R = geo.face_L, geo.face_R
@@ -86,8 +139,13 @@ def face_flux(geo, bc, u, vel, D, coef=None, weights=None):
     kind = np.array(["interior"] * geo.n_face, dtype=object)
     for t, (k, _v) in bc.items():
         kind[(R < 0) & (geo.face_tag == t)] = k
-    uR = np.where(R >= 0, u[np.maximum(R, 0)], np.where(kind == "dirichlet", g, u[L]))
-    u_up = np.where(vn >= 0.0, u[L], uR)
+    ghost = np.where(kind == "dirichlet", g, u[L])
+    if recon:
+        uLf, uRf, _ = muscl_states(geo, bc, u)
+        u_up = np.where(vn >= 0.0, uLf, np.where(R >= 0, uRf, ghost))
+    else:
+        uR = np.where(R >= 0, u[np.maximum(R, 0)], ghost)
+        u_up = np.where(vn >= 0.0, u[L], uR)
     F = vn * u_up
     if D != 0.0:
         F = F - D * face_gradient_flux(geo, bc, u, coef, weights)
@@ -95,9 +153,9 @@ def face_flux(geo, bc, u, vel, D, coef=None, weights=None):
     return F
 
 
-def residual(geo, bc, u, vel, D, src=None, coef=None, weights=None):
+def residual(geo, bc, u, vel, D, src=None, coef=None, weights=None, recon=0):
     """R_i of eq. 4: (sum_{R(f)=i} F_f - sum_{L(f)=i} F_f) / mu_i + S_i."""
-    F = face_flux(geo, bc, u, vel, D, coef, weights)
+    F = face_flux(geo, bc, u, vel, D, coef, weights, recon)
     N = geo.n_cell
     inr = geo.face_R >= 0
     acc = np.bincount(geo.face_R[inr], weights=F[inr], minlength=N)
@@ -108,12 +166,13 @@ def residual(geo, bc, u, vel, D, src=None, coef=None, weights=None):
     return res
 
 
-def rk_step(geo, bc, u, vel, D, dt, alphas=(1.0,), src=None, coef=None, weights=None):
+def rk_step(geo, bc, u, vel, D, dt, alphas=(1.0,), src=None, coef=None, weights=None,
+            recon=0):
     """One time step of eq. 6 with stage coefficients ``alphas`` ((1,) = Euler)."""
     un = np.asarray(u, dtype=np.float64)
     uk = un
     for a in alphas:
-        uk = un + a * dt * residual(geo, bc, uk, vel, D, src, coef, weights)
+        uk = un + a * dt * residual(geo, bc, uk, vel, D, src, coef, weights, recon)
     return uk
 
 
