@@ -212,6 +212,9 @@ def transport_kernels(capi, device, torch, stream, flush, precs, reps=10, warm=3
         src = dm.to_device(rng.normal(size=N))
         g, uv, res = dm.empty(3, N), dm.empty(V), dm.empty(N)
         tc = capi.tcoef(vel=vel, diff=0.1, src=src, bcset=0)
+        tcm = capi.tcoef(vel=vel, diff=0.1, src=src, bcset=0, recon=1)
+        res_bytes = (4 * N * (4 + w) + N * w + V * w + F * (20 + 7 * w) + V * w
+                     + N * (16 + 7 * w) + F * w)
         calls = {
             # node-neighbour indices + u + M^-1 (6) + centre (3) + gradient out (3)
             "gradient": (lambda: capi.fvgb_gradient(dm.handle, 1, u, g),
@@ -221,10 +224,12 @@ def transport_kernels(capi, device, torch, stream, flush, precs, reps=10, warm=3
                               4 * N * (4 + w) + N * w + V * w),
             # vertex values, then per face L, R, A, B, C + 3 coefficients + area vector
             # (3) + flux, then cell_face (4) + fluxes + u, velocity (3), source, 1/mu, out
-            "fv_residual": (lambda: capi.fvgb_fv_residual(dm.handle, tc, u, res),
-                            4 * N * (4 + w) + N * w + V * w
-                            + F * (20 + 7 * w) + V * w
-                            + N * (16 + 7 * w) + F * w),
+            "fv_residual": (lambda: capi.fvgb_fv_residual(dm.handle, tc, u, res), res_bytes),
+            # MUSCL + Barth-Jespersen: + gradient, + limiter (cell_face, u, gradient in and
+            # out, face centroids), + the reconstruction's gradient and centre reads
+            "fv_residual_muscl": (lambda: capi.fvgb_fv_residual(dm.handle, tcm, u, res),
+                                  res_bytes + 4 * NN + N * 13 * w
+                                  + N * (16 + 7 * w) + 3 * w * F + 6 * w * N),
         }
         r = {"cells": N, "faces": F, "vertices": V, "node_neighbour_entries": NN}
         t_end = time.time() + 0.5                 # bring the clocks up before timing

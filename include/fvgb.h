@@ -173,8 +173,13 @@ fvgb_status fvgb_vertex_values(fvgb_mesh m, int32_t bcset, const void* u_dev, vo
 
 /* Transport coefficients of eq. 1: velocity (a per-cell field [dim][n_cell] real when
  * vel_dev is not NULL, else the constant vel_const), diffusivity D >= 0, source
- * S_i ([n_cell] real or NULL), boundary conditions bcset. recon must be 0 (first-order
- * upwind, eq. 15 with psi = 0). */
+ * S_i ([n_cell] real or NULL), boundary conditions bcset, and the convective face value
+ * of eq. 15: recon = 0 first-order upwind (psi = 0); recon = 1 MUSCL with the
+ * Barth-Jespersen limiter, u_up = u_c + psi_c grad u_c . (x_f - x_c) for the upwind cell c
+ * (grad from Algorithm "grad" with the same boundary conditions; psi_c = min over the
+ * cell's faces of min(1, (bound - u_c) / (grad u_c . (x_f - x_c))), the bounds being the
+ * max / min of u_c, its face neighbours and its Dirichlet values); a boundary ghost on
+ * the upwind side keeps its first-order value. Other values: FVGB_EINVAL. */
 typedef struct {
   const void* vel_dev;
   double vel_const[3];
@@ -186,7 +191,8 @@ typedef struct {
 
 /* Residual of eq. 4: res_i = (sum over faces entering i - leaving i of F_f) / mu_i + S_i,
  * F_f = (V_f . S_f) u_up - D grad u_f . S_f, V_f = (V_L + V_R)/2,
- * u_up = u_L if V_f . S_f >= 0 else u_R (eq. 15).
+ * u_up from the cell on the upwind side: L if V_f . S_f >= 0, else R (eq. 15; see
+ * fvgb_tcoef.recon).
  *  u_dev, res_dev: [n_cell] real, distinct buffers. */
 fvgb_status fvgb_fv_residual(fvgb_mesh m, const fvgb_tcoef* tc, const void* u_dev,
                              void* res_dev, void* stream);
@@ -196,7 +202,8 @@ fvgb_status fvgb_fv_residual(fvgb_mesh m, const fvgb_tcoef* tc, const void* u_de
  * such as a host program whose device memory is handed out by its own pool (a stray
  * cudaMalloc there can fail or fragment the pool) or a time-critical loop in which
  * cudaMalloc / cudaFree would add latency and implicit synchronisation. Arguments,
- * results and errors are those of fvgb_fv_residual.
+ * results and errors are those of fvgb_fv_residual, except that only first-order upwind
+ * is offered (recon != 0 gives FVGB_EUNSUPPORTED).
  *  - Scratch (the face fluxes and vertex values) lives in one fixed 8 MiB device array
  *    owned by the library, which every GPU that loads the library holds until the
  *    process exits. A mesh needs n_face + n_vert reals of it (rounded up to 256 bytes
@@ -270,8 +277,8 @@ fvgb_status fvgb_poisson_solve(fvgb_mesh m, int32_t bcset, const double* f_dev,
  * v = -mu E, alpha = A exp(-B/|E|) (0 at |E| = 0), S = alpha |v| n_e, constant D_e,
  * Lap phi = -(e/eps0)(n_i - n_e). Per step: solve for phi (warm start from phi_dev),
  * E = -grad phi (least-squares gradient, set bcset_phi), then
- * n_e += dt Res(n_e) (set bcset_ne, velocity field v, diffusivity D_e, source S) and
- * n_i += dt S. */
+ * n_e += dt Res(n_e) (set bcset_ne, velocity field v, diffusivity D_e, source S, face
+ * values per recon) and n_i += dt S. */
 typedef struct {
   double mu, A, B, De;
   double dt;
@@ -290,6 +297,8 @@ typedef struct {
                             a network, the network then predicts the extrapolation's
                             error from the change of the charge change (its second
                             difference in time) */
+  int32_t recon;         /* convective face value of the n_e transport (fvgb_tcoef.recon):
+                            0 first-order upwind, 1 MUSCL + Barth-Jespersen (eq. 15) */
 } fvgb_streamer_params;
 
 /* ne_dev, ni_dev: [n_cell] real; phi_dev: [n_cell] double (in: guess, out: last

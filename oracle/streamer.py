@@ -60,14 +60,15 @@ def cell_physics(p, E, ne):
     return v, S
 
 
-def step(geo, p, ne, ni, dt, phi=None, dense=False):
-    """One explicit Euler step of eq. 10; returns (ne, ni, phi, E, S)."""
+def step(geo, p, ne, ni, dt, phi=None, dense=False, recon=0):
+    """One explicit Euler step of eq. 10; returns (ne, ni, phi, E, S). recon = 1 takes the
+    convective face values of n_e from the MUSCL reconstruction (eq. 15)."""
     bphi = bc_phi(p)
     if phi is None:
         phi = poisson.solve(geo, bphi, poisson_source(ne, ni), dense=dense)
     E = -ls.ls_gradient(geo, bphi, phi)
     v, S = cell_physics(p, E, ne)
-    R = fv.residual(geo, bc_ne(), ne, v, p.De, src=S)
+    R = fv.residual(geo, bc_ne(), ne, v, p.De, src=S, recon=recon)
     return ne + dt * R, ni + dt * S, phi, E, S
 
 

@@ -78,7 +78,8 @@ class fvgb_solve_info(C.Structure):
 class fvgb_streamer_params(C.Structure):
     _fields_ = [("mu", C.c_double), ("A", C.c_double), ("B", C.c_double), ("De", C.c_double),
                 ("dt", C.c_double), ("bcset_ne", C.c_int32), ("bcset_phi", C.c_int32),
-                ("solve", fvgb_solve_opts), ("warm", C.c_void_p), ("extrapolate", C.c_int32)]
+                ("solve", fvgb_solve_opts), ("warm", C.c_void_p), ("extrapolate", C.c_int32),
+                ("recon", C.c_int32)]
 
 
 class fvgb_stats(C.Structure):
@@ -291,8 +292,13 @@ def fvgb_vertex_values(m, bcset, u, uv, stream=None):
 
 
 def tcoef(vel=None, vel_const=(0.0, 0.0, 0.0), diff=0.0, src=None, bcset=0, recon=0):
+    """fvgb_tcoef for device arrays ``vel`` ([dim][n_cell]) and ``src`` ([n_cell]) or None.
+    The struct holds raw pointers; it also keeps references to the arrays so that they
+    stay allocated for as long as the struct is in use."""
     vc = (C.c_double * 3)(*[float(v) for v in list(vel_const) + [0.0] * (3 - len(vel_const))])
-    return fvgb_tcoef(ptr(vel), vc, float(diff), ptr(src), int(bcset), int(recon))
+    tc = fvgb_tcoef(ptr(vel), vc, float(diff), ptr(src), int(bcset), int(recon))
+    tc._keep = (vel, src)
+    return tc
 
 
 def fvgb_fv_residual(m, tc, u, res, stream=None):
@@ -341,10 +347,10 @@ def fvgb_poisson_solve(m, bcset, f, phi, opts, stream=None, check=True):
 
 
 def streamer_params(mu=0.0382, A=4332.0, B=2.0e5, De=0.1, dt=1e-9, bcset_ne=0, bcset_phi=1,
-                    solve=None, warm=None, extrapolate=False):
+                    solve=None, warm=None, extrapolate=False, recon=0):
     return fvgb_streamer_params(mu, A, B, De, dt, bcset_ne, bcset_phi,
                                 solve if solve is not None else solve_opts(), warm,
-                                int(bool(extrapolate)))
+                                int(bool(extrapolate)), int(recon))
 
 
 def fvgb_streamer_reset(m):

@@ -211,13 +211,23 @@ bool is_fp32(fvgb_mesh m) { return m->prec != FVGB_FP64; }
 namespace {
 
 // ---- transport residual / step in precision T --------------------------------------------
+// MUSCL (eq. 15): least-squares gradient of u, limited in place
+template <typename T>
+fvgb_status limited_gradient(fvgb_mesh m, const fvgb_tcoef* tc, const T* u, cudaStream_t s) {
+  Work<T>& w = work_of<T>(m);
+  FVGB_TRY(launch_gradient<T>(m, tc->bcset, u, w.grad, s), "gradient kernel");
+  FVGB_TRY(launch_bj_limit<T>(m, tc->bcset, u, w.grad, s), "limiter kernel");
+  return FVGB_OK;
+}
+
 template <typename T>
 fvgb_status residual_T(fvgb_mesh m, const fvgb_tcoef* tc, const T* u, T* res, cudaStream_t s) {
   Work<T>& w = work_of<T>(m);
   const bool diff = tc->diff != 0.0;
+  if (tc->recon) FVGB_TRY_ST(limited_gradient<T>(m, tc, u, s));
   if (diff) FVGB_TRY(launch_vertex<T>(m, tc->bcset, u, w.uv, false, s), "vertex kernel");
   FVGB_TRY(launch_face<T>(m, tc->bcset, u, w.uv, (const T*)tc->vel_dev, tc->vel_const, true,
-                          tc->diff, false, w.flux, s), "face kernel");
+                          tc->diff, false, w.flux, s, tc->recon ? w.grad : nullptr), "face kernel");
   FVGB_TRY(launch_update<T>(m, kResidual, w.flux, (const T*)tc->src_dev, nullptr, 0.0, nullptr,
                             res, nullptr, s), "update kernel");
   return FVGB_OK;
@@ -234,9 +244,10 @@ fvgb_status step_T(fvgb_mesh m, const fvgb_tcoef* tc, T* u, double dt, int nstep
     for (int k = 0; k < nstage; ++k) {
       const bool last = k == nstage - 1;
       T* out = last ? u : (k % 2 == 0 ? w.stage : w.tmp);
+      if (tc->recon) FVGB_TRY_ST(limited_gradient<T>(m, tc, in, s));
       if (diff) FVGB_TRY(launch_vertex<T>(m, tc->bcset, in, w.uv, false, s), "vertex kernel");
       FVGB_TRY(launch_face<T>(m, tc->bcset, in, w.uv, (const T*)tc->vel_dev, tc->vel_const, true,
-                              tc->diff, false, w.flux, s), "face kernel");
+                              tc->diff, false, w.flux, s, tc->recon ? w.grad : nullptr), "face kernel");
       FVGB_TRY(launch_update<T>(m, kStep, w.flux, (const T*)tc->src_dev, u, alpha[k] * dt, nullptr,
                                 out, last ? ni_out : nullptr, s), "update kernel");
       in = out;
@@ -425,6 +436,7 @@ fvgb_status streamer_transport(fvgb_mesh m, const fvgb_streamer_params* p, void*
   std::memset(&tc, 0, sizeof(tc));
   tc.diff = p->De;
   tc.bcset = p->bcset_ne;
+  tc.recon = p->recon;
   static const double euler[1] = {1.0};
   if (is_fp32(m)) {
     Work<float>& w = m->w32;
@@ -727,7 +739,7 @@ fvgb_status fvgb_vertex_values(fvgb_mesh m, int32_t bcset, const void* u, void* 
 
 static fvgb_status check_tcoef(fvgb_mesh m, const fvgb_tcoef* tc) {
   if (!tc) { set_error("tcoef is null"); return FVGB_EINVAL; }
-  if (tc->recon != 0) { set_error("only first-order upwind (recon = 0) is implemented"); return FVGB_EUNSUPPORTED; }
+  if (tc->recon != 0 && tc->recon != 1) { set_error("recon must be 0 (upwind) or 1 (MUSCL + Barth-Jespersen)"); return FVGB_EINVAL; }
   if (!(tc->diff >= 0.0)) { set_error("diffusivity must be >= 0"); return FVGB_EINVAL; }
   return check_bcset(m, tc->bcset);
 }
@@ -779,7 +791,7 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
                                double* phi, void* E, int32_t nsteps, fvgb_solve_info* info,
                                void* stream) {
   if (fvgb_status st = check_mesh(m)) return st;
-  if (!p || !ne || !ni || !phi || nsteps < 0 || !opts_ok(&p->solve)) { set_error("bad streamer arguments"); return FVGB_EINVAL; }
+  if (!p || !ne || !ni || !phi || nsteps < 0 || !opts_ok(&p->solve) || (p->recon != 0 && p->recon != 1)) { set_error("bad streamer arguments"); return FVGB_EINVAL; }
   if (fvgb_status st = check_bcset(m, p->bcset_ne)) return st;
   if (fvgb_status st = check_bcset(m, p->bcset_phi)) return st;
   const bool fp32_solve = p->solve.prec == FVGB_FP32 || p->solve.prec == FVGB_MIXED;

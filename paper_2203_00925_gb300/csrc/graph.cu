@@ -115,8 +115,13 @@ __global__ void k_zero_parts(const double* __restrict__ bn2, const int32_t* __re
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) phi[i] = 0.0;
 }
 
+// field by field (padding bytes of a caller's struct may hold anything)
 bool same_params(const fvgb_streamer_params& a, const fvgb_streamer_params& b) {
-  return std::memcmp(&a, &b, sizeof(a)) == 0;
+  return a.mu == b.mu && a.A == b.A && a.B == b.B && a.De == b.De && a.dt == b.dt &&
+         a.bcset_ne == b.bcset_ne && a.bcset_phi == b.bcset_phi && a.solve.rtol == b.solve.rtol &&
+         a.solve.inner_rtol == b.solve.inner_rtol && a.solve.maxit_inner == b.solve.maxit_inner &&
+         a.solve.maxit_outer == b.solve.maxit_outer && a.solve.prec == b.solve.prec &&
+         a.warm == b.warm && a.extrapolate == b.extrapolate && a.recon == b.recon;
 }
 
 cudaError_t capture_error(cudaError_t e) { return e; }

@@ -184,11 +184,15 @@ template <typename T>
 cudaError_t launch_gradient(fvgb_mesh_s* m, int bcset, const T* u, T* grad, cudaStream_t s);
 template <typename T>
 cudaError_t launch_vertex(fvgb_mesh_s* m, int bcset, const T* u, T* uv, bool homog, cudaStream_t s);
-// face kernel: conv (use velocity), D (diffusion coefficient; -1 gives F = q)
+// face kernel: conv (use velocity), D (diffusion coefficient; -1 gives F = q); lgrad
+// (optional, with conv): limited gradient for the MUSCL reconstruction of eq. 15
 template <typename T>
 cudaError_t launch_face(fvgb_mesh_s* m, int bcset, const T* u, const T* uv, const T* vel,
                         const double* vel_const, bool conv, double D, bool homog, T* flux,
-                        cudaStream_t s);
+                        cudaStream_t s, const T* lgrad = nullptr);
+// Barth-Jespersen limiter: grad <- psi grad (eq. 15)
+template <typename T>
+cudaError_t launch_bj_limit(fvgb_mesh_s* m, int bcset, const T* u, T* grad, cudaStream_t s);
 enum UpdateMode { kResidual = 0, kStep = 1, kPoissonApply = 2, kPoissonResidual = 3, kPoissonRhs = 4 };
 template <typename T>
 cudaError_t launch_update(fvgb_mesh_s* m, int mode, const T* flux, const T* src, const T* base,
@@ -218,6 +222,12 @@ bool is_fp32(fvgb_mesh m);
 #define FVGB_TRY(expr, what)                                   \
   do {                                                         \
     fvgb_status st_ = cuda_status((expr), (what));             \
+    if (st_ != FVGB_OK) return st_;                            \
+  } while (0)
+// the same for an expression that already yields an fvgb_status
+#define FVGB_TRY_ST(expr)                                      \
+  do {                                                         \
+    fvgb_status st_ = (expr);                                  \
     if (st_ != FVGB_OK) return st_;                            \
   } while (0)
 fvgb_status poisson_residual(fvgb_mesh m, int bcset, const double* x, const double* b, double* r,

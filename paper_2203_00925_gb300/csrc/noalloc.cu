@@ -87,7 +87,7 @@ extern "C" fvgb_status fvgb_fv_residual_noalloc(fvgb_mesh m, const fvgb_tcoef* t
                                                 const void* u, void* res, void* stream) {
   if (!m) { set_error("null mesh handle"); return FVGB_EINVAL; }
   if (!tc) { set_error("tcoef is null"); return FVGB_EINVAL; }
-  if (tc->recon != 0) { set_error("only first-order upwind (recon = 0) is implemented"); return FVGB_EUNSUPPORTED; }
+  if (tc->recon != 0) { set_error("the allocation-free residual is first-order upwind only (recon = 0)"); return FVGB_EUNSUPPORTED; }
   if (!(tc->diff >= 0.0)) { set_error("diffusivity must be >= 0"); return FVGB_EINVAL; }
   if (tc->bcset < 0 || tc->bcset >= (int32_t)m->g64.bc.size()) { set_error("bcset index out of range"); return FVGB_EINVAL; }
   if (!u || !res || u == res) { set_error("u and res must be distinct device arrays"); return FVGB_EINVAL; }

@@ -213,18 +213,104 @@ k_vertex(int64_t V, const int64_t* __restrict__ sptr, const int32_t* __restrict_
   }
 }
 
+// ---- Barth-Jespersen limiter of eq. 15: grad u_i <- psi_i grad u_i ------------------------
+// Bounds over u_i, the face neighbours' values and the Dirichlet values of the cell's
+// boundary faces; psi_i = min over the cell's faces of min(1, (bound - u_i) / d_f) with
+// d_f = grad u_i . (x_f - x_i) (the upper bound where d_f > 0, the lower where d_f < 0).
+template <typename T, int D>
+__global__ void __launch_bounds__(256)
+k_bj_limit(int64_t N, int64_t F, int64_t Fi, const int32_t* __restrict__ cell_face,
+           const int32_t* __restrict__ fL, const int32_t* __restrict__ fR,
+           const T* __restrict__ u, const T* __restrict__ cen, const T* __restrict__ cen_lo,
+           const T* __restrict__ xf, const T* __restrict__ xf_lo,
+           const int8_t* __restrict__ bkind, const T* __restrict__ bval, T* __restrict__ grad) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const T ui = u[i];
+  T gi[3] = {grad[i], grad[N + i], D == 3 ? grad[2 * N + i] : T(0)};
+  T umax = ui, umin = ui;
+  int32_t fc[D + 1];
+#pragma unroll
+  for (int k = 0; k <= D; ++k) {
+    const int32_t e = cell_face[k * N + i];
+    const int32_t f = e >= 0 ? e : ~e;
+    fc[k] = f;
+    if (f < Fi) {
+      const T uj = u[e >= 0 ? fR[f] : fL[f]];
+      umax = fmax(umax, uj);
+      umin = fmin(umin, uj);
+    } else if (bkind[f - Fi] == FVGB_BC_DIRICHLET) {
+      const T g = bval[f - Fi];
+      umax = fmax(umax, g);
+      umin = fmin(umin, g);
+    }
+  }
+  // psi = min(1, min over faces of (bound - u_i) / d_f). The smallest ratio is tracked as
+  // a fraction num / den (both >= 0); in FP64 (costly division) the comparison is by
+  // cross-multiplication and the winner is divided once.
+  T num = T(1), den = T(1);
+#pragma unroll
+  for (int k = 0; k <= D; ++k) {
+    const int32_t f = fc[k];
+    T d = mul_rn(gi[0], cdiff(xf, xf_lo, f, cen, cen_lo, i));
+    d = fma_rn(gi[1], cdiff(xf + F, xf_lo ? xf_lo + F : nullptr, f, cen + N, cen_lo ? cen_lo + N : nullptr, i), d);
+    if (D == 3)
+      d = fma_rn(gi[2], cdiff(xf + 2 * F, xf_lo ? xf_lo + 2 * F : nullptr, f, cen + 2 * N,
+                              cen_lo ? cen_lo + 2 * N : nullptr, i), d);
+    if (d != T(0)) {
+      const T a = d > T(0) ? umax - ui : ui - umin;   // >= 0
+      const T b = fabs(d);
+      if constexpr (sizeof(T) == 8) {
+        if (a * den < num * b) { num = a; den = b; }
+      } else {                                           // FP32: products could overflow
+        if (a / b < num / den) { num = a; den = b; }
+      }
+    }
+  }
+  const T psi = num == T(1) && den == T(1) ? T(1) : num / den;
+#pragma unroll
+  for (int a = 0; a < D; ++a) grad[a * N + i] = mul_rn(psi, gi[a]);
+}
+
 // ---- face flux: F = (V_f . S_f) u_up - D grad u_f . S_f (eq. 4, eq. 15, eq. "diamond") ----
 // Each thread takes K faces (block-contiguous, stride blockDim): it issues the streamed
 // face data of all K first, then all their gathers, then computes, so that K faces'
 // loads are in flight together. The arithmetic of one face does not depend on K.
-template <typename T, int D, bool CONV, bool VFIELD, int K>
+// With RECON (MUSCL, eq. 15) the upwind cell's value is reconstructed at the face
+// centroid with the limited gradient lg: u_c + lg_c . (x_f - x_c); a boundary ghost on
+// the upwind side keeps its first-order value.
+struct Recon {
+  const void* lg = nullptr;      // [d][N] limited gradient
+  const void* cen = nullptr;     // [d][N]
+  const void* cen_lo = nullptr;  // [d][N] (FP32)
+  const void* xf = nullptr;      // [d][F]
+  const void* xf_lo = nullptr;   // [d][F] (FP32)
+};
+
+template <typename T, int D>
+__device__ __forceinline__ T recon_value(const Recon& rc, int64_t N, int64_t F, int64_t f,
+                                         int32_t c, T uc) {
+  const T* lg = (const T*)rc.lg;
+  const T* cen = (const T*)rc.cen;
+  const T* clo = (const T*)rc.cen_lo;
+  const T* xf = (const T*)rc.xf;
+  const T* xlo = (const T*)rc.xf_lo;
+  T t = mul_rn(lg[c], cdiff(xf, xlo, f, cen, clo, c));
+  t = fma_rn(lg[N + c], cdiff(xf + F, xlo ? xlo + F : nullptr, f, cen + N, clo ? clo + N : nullptr, c), t);
+  if (D == 3)
+    t = fma_rn(lg[2 * N + c], cdiff(xf + 2 * F, xlo ? xlo + 2 * F : nullptr, f, cen + 2 * N,
+                                    clo ? clo + 2 * N : nullptr, c), t);
+  return add_rn(uc, t);
+}
+
+template <typename T, int D, bool CONV, bool VFIELD, int K, bool RECON = false>
 __global__ void __launch_bounds__(1024 / K)
 k_face(int64_t F, int64_t Fi, int64_t N, const int32_t* __restrict__ fL,
        const int32_t* __restrict__ fR, const int32_t* __restrict__ fvert,
        const T* __restrict__ S, const T* __restrict__ coef, const T* __restrict__ u,
        const T* __restrict__ uv, const T* __restrict__ vel, T vc0, T vc1, T vc2, T Dcoef,
        const int8_t* __restrict__ bkind, const T* __restrict__ bval, int homog,
-       T* __restrict__ flux) {
+       T* __restrict__ flux, Recon rc) {
   constexpr int kInterior = 3;
   const int64_t per_block = (int64_t)blockDim.x * K;
   for (int64_t base = blockIdx.x * per_block + threadIdx.x; base < F;
@@ -290,7 +376,12 @@ k_face(int64_t F, int64_t Fi, int64_t N, const int32_t* __restrict__ fL,
         }
         T vn = fma_rn(vf[1], s1[k], mul_rn(vf[0], s0[k]));
         if (D == 3) vn = fma_rn(vf[2], s2[k], vn);
-        Ff = mul_rn(vn, vn >= T(0) ? ul : ur);
+        T up = vn >= T(0) ? ul : ur;
+        if (RECON) {
+          if (vn >= T(0)) up = recon_value<T, D>(rc, N, F, f, L[k], ul);
+          else if (kind[k] == kInterior) up = recon_value<T, D>(rc, N, F, f, R[k], ur);
+        }
+        Ff = mul_rn(vn, up);
       }
       if (diff && (kind[k] == kInterior || kind[k] == FVGB_BC_DIRICHLET)) {
         T q = mul_rn(c0[k], sub_rn(ur, ul));
@@ -487,11 +578,29 @@ cudaError_t launch_vertex(fvgb_mesh_s* m, int bcset, const T* u, T* uv, bool hom
 }
 
 template <typename T>
-cudaError_t launch_face(fvgb_mesh_s* m, int bcset, const T* u, const T* uv, const T* vel,
-                        const double* vc, bool conv, double D, bool homog, T* flux, cudaStream_t s) {
+cudaError_t launch_bj_limit(fvgb_mesh_s* m, int bcset, const T* u, T* grad, cudaStream_t s) {
   const TopoDev& t = m->topo;
   GeoDev<T>& g = geo_of<T>(m);
   const BCDev<T>& b = g.bc[bcset];
+  if (t.dim == 3)
+    k_bj_limit<T, 3><<<grid_for(t.N), kThreads, 0, s>>>(t.N, t.F, t.Fi, t.cell_face, t.fL, t.fR, u,
+        g.cen, g.cen_lo, g.xf, g.xf_lo, b.bkind, b.bval, grad);
+  else
+    k_bj_limit<T, 2><<<grid_for(t.N), kThreads, 0, s>>>(t.N, t.F, t.Fi, t.cell_face, t.fL, t.fR, u,
+        g.cen, g.cen_lo, g.xf, g.xf_lo, b.bkind, b.bval, grad);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_face(fvgb_mesh_s* m, int bcset, const T* u, const T* uv, const T* vel,
+                        const double* vc, bool conv, double D, bool homog, T* flux, cudaStream_t s,
+                        const T* lgrad) {
+  const TopoDev& t = m->topo;
+  GeoDev<T>& g = geo_of<T>(m);
+  const BCDev<T>& b = g.bc[bcset];
+  Recon rc;
+  if (lgrad) rc = Recon{lgrad, g.cen, g.cen_lo, g.xf, g.xf_lo};
   const T v0 = vc ? (T)vc[0] : T(0), v1 = vc ? (T)vc[1] : T(0), v2 = vc ? (T)vc[2] : T(0);
   // K faces per thread (FP64 face fluxes of an FP32 mesh, the Poisson residual, are bound
   // by the FP64 pipe and take K = 1); blocks of at most 1024 / K threads (the kernel's launch bound)
@@ -506,7 +615,13 @@ cudaError_t launch_face(fvgb_mesh_s* m, int bcset, const T* u, const T* uv, cons
     const unsigned gr_ = face_grid(KK, tb);                                                 \
     k_face<T, DD, CV, VF, KK><<<gr_, tb, 0, s>>>(t.F, t.Fi, t.N, t.fL, t.fR, t.fvert, g.S,  \
                                                  g.coef, u, uv, vel, v0, v1, v2, (T)D,      \
-                                                 b.bkind, b.bval, homog ? 1 : 0, flux);     \
+                                                 b.bkind, b.bval, homog ? 1 : 0, flux, rc); \
+  } while (0)
+#define FVGB_FACE_RECON(DD, VF)                                                            \
+  do {                                                                                     \
+    const unsigned gr_ = face_grid(1, tb);                                                 \
+    k_face<T, DD, true, VF, 1, true><<<gr_, tb, 0, s>>>(t.F, t.Fi, t.N, t.fL, t.fR, t.fvert, \
+        g.S, g.coef, u, uv, vel, v0, v1, v2, (T)D, b.bkind, b.bval, homog ? 1 : 0, flux, rc); \
   } while (0)
 #define FVGB_FACE(DD, CV, VF)                                          \
   do {                                                                 \
@@ -514,7 +629,15 @@ cudaError_t launch_face(fvgb_mesh_s* m, int bcset, const T* u, const T* uv, cons
     else if (ipt == 2) FVGB_FACE_K(DD, CV, VF, 2);                     \
     else FVGB_FACE_K(DD, CV, VF, 1);                                   \
   } while (0)
-  if (t.dim == 3) {
+  if (lgrad && conv) {
+    if (t.dim == 3) {
+      if (vel) FVGB_FACE_RECON(3, true);
+      else FVGB_FACE_RECON(3, false);
+    } else {
+      if (vel) FVGB_FACE_RECON(2, true);
+      else FVGB_FACE_RECON(2, false);
+    }
+  } else if (t.dim == 3) {
     if (!conv) FVGB_FACE(3, false, false);
     else if (vel) FVGB_FACE(3, true, true);
     else FVGB_FACE(3, true, false);
@@ -525,6 +648,7 @@ cudaError_t launch_face(fvgb_mesh_s* m, int bcset, const T* u, const T* uv, cons
   }
 #undef FVGB_FACE
 #undef FVGB_FACE_K
+#undef FVGB_FACE_RECON
   count_launch();
   return cudaGetLastError();
 }
@@ -701,7 +825,9 @@ cudaError_t launch_nonfinite_check(const double* x, int64_t n, int* flag, cudaSt
   template cudaError_t launch_gradient<T>(fvgb_mesh_s*, int, const T*, T*, cudaStream_t);     \
   template cudaError_t launch_vertex<T>(fvgb_mesh_s*, int, const T*, T*, bool, cudaStream_t); \
   template cudaError_t launch_face<T>(fvgb_mesh_s*, int, const T*, const T*, const T*,        \
-                                      const double*, bool, double, bool, T*, cudaStream_t);  \
+                                      const double*, bool, double, bool, T*, cudaStream_t,   \
+                                      const T*);                                              \
+  template cudaError_t launch_bj_limit<T>(fvgb_mesh_s*, int, const T*, T*, cudaStream_t);     \
   template cudaError_t launch_update<T>(fvgb_mesh_s*, int, const T*, const T*, const T*,      \
                                         double, const T*, T*, T*, cudaStream_t);              \
   template cudaError_t launch_cell_physics<T>(fvgb_mesh_s*, const T*, const T*, double,       \

@@ -9,6 +9,8 @@
   oracle's residual of the GPU potential over the whole mesh <= 1e-8, and n_e, n_i and
   E on 256 sampled cells, each from the oracle on the patch of cells it depends on,
   within 1e-5.
+* the MUSCL + Barth-Jespersen residual: every cell at 750k (FP64), 256 sampled cells at
+  6M (FP32).
 * the 64-mesh ensemble (about 15.4M cells, mixed precision, graph mode, extrapolated
   start): the same two checks on its smallest, a middle and its largest mesh.
 """
@@ -84,6 +86,12 @@ def test_operators_750k(dev, w750):
                                                  src=dm.to_device(src), bcset=0), ud, res)
     torch.cuda.synchronize()
     want = fv.residual(g, bcs[0], u, vel, 0.1, src=src, coef=coef, weights=w)
+    assert rel(dm.to_host(res), want) < TOL64
+    # MUSCL + Barth-Jespersen (eq. 15)
+    capi.fvgb_fv_residual(dm.handle, capi.tcoef(vel=dm.to_device(vel.T), diff=0.1,
+                                                src=dm.to_device(src), bcset=0, recon=1), ud, res)
+    torch.cuda.synchronize()
+    want = fv.residual(g, bcs[0], u, vel, 0.1, src=src, coef=coef, weights=w, recon=1)
     assert rel(dm.to_host(res), want) < TOL64
     y = dm.empty(dm.n_cell, dtype=torch.float64)
     b = dm.empty(dm.n_cell, dtype=torch.float64)
@@ -167,6 +175,34 @@ def test_streamer_step_6m_mixed_sampled(dev):
     assert rel(got_ne[sample], sne[pos]) < TOL32
     assert rel(got_ni[sample], sni[pos]) < TOL32
     assert rel(got_E[sample], sE[pos]) < TOL32
+
+
+def test_muscl_residual_6m_fp32_sampled(dev):
+    """MUSCL residual at 6M cells in FP32 (autotuned shapes), 256 sampled cells against the
+    oracle on the patches they depend on (two node-neighbour rings: the limited gradients
+    of the face neighbours), within 1e-5."""
+    capi, device = dev
+    mesh = streamer_mesh(100, 301)
+    case = StreamerCase()
+    dm = device.DeviceMesh(mesh, [case.bc_ne(), case.bc_phi()], prec="fp32")
+    capi.fvgb_autotune(dm.handle)
+    rng = np.random.default_rng(6001)
+    cen = mesh.vertex_mean()
+    u = np.sin(cen @ np.array([5.1, 3.3, 4.9])) + 0.2 * rng.normal(size=mesh.n_cell) + 2.0
+    vel = rng.normal(size=(mesh.n_cell, 3))
+    src = rng.normal(size=mesh.n_cell)
+    res = dm.empty(dm.n_cell)
+    capi.fvgb_fv_residual(dm.handle, capi.tcoef(vel=dm.to_device(vel.T), diff=0.1,
+                                                src=dm.to_device(src), bcset=0, recon=1),
+                          dm.to_device(u), res)
+    torch.cuda.synchronize()
+    got = dm.to_host(res)
+    dm.free()
+    sample = np.unique(rng.choice(mesh.n_cell, 256, replace=False))
+    sub, ids, pos = patch(mesh, sample, rings=2)
+    gs = geometry_of(sub)
+    want = fv.residual(gs, case.bc_ne(), u[ids], vel[ids], 0.1, src=src[ids], recon=1)
+    assert rel(got[sample], want[pos]) < TOL32
 
 
 def test_ensemble_64_meshes_sampled(dev):

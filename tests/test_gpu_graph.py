@@ -114,3 +114,28 @@ def test_extrapolated_start_graph_matches_host_and_saves_iterations(dev, prec):
     assert all(i["rel_res"] <= 1e-8 for i in outs[(False, True)][3])
     assert extr < 0.6 * plain, (extr, plain)
     dm.free()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_graph_muscl_matches_host(dev, prec):
+    """Streamer steps with MUSCL transport (recon = 1): graph mode gives the host loop's bits."""
+    capi, device = dev
+    m = jittered_cube(8, seed=201)
+    case = StreamerCase(sigma=0.15, peak=1e13)
+    dm = device.DeviceMesh(m, [case.bc_ne(), case.bc_phi()], prec=prec)
+    ne0 = case.initial(m)[0]
+    solve = capi.solve_opts(rtol=1e-9, prec=capi.FVGB_FP64 if prec == "fp64" else capi.FVGB_FP32)
+    outs = []
+    for graph in (False, True):
+        ne, ni = dm.to_device(ne0), dm.to_device(ne0 * 1.02)
+        phi = torch.zeros(dm.n_cell, dtype=torch.float64, device="cuda")
+        sp = capi.streamer_params(mu=case.mu, A=case.A, B=case.B, De=case.De, dt=2e-9,
+                                  solve=solve, recon=1)
+        capi.fvgb_set_graph_mode(dm.handle, graph)
+        capi.fvgb_streamer_step(dm.handle, sp, ne, ni, phi, None, 3)
+        torch.cuda.synchronize()
+        outs.append((ne, ni, phi))
+    capi.fvgb_set_graph_mode(dm.handle, False)
+    for x, y in zip(*outs):
+        assert torch.equal(x, y)
+    dm.free()

@@ -281,3 +281,73 @@ def test_streamer_steps(dev, prec):
     assert rel(dm.to_host(Ed).T, oE) < 1e-6
     assert all(i["rel_res"] <= 1e-10 for i in infos)
     dm.free()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_muscl_residual_and_steps(dev, prec):
+    """MUSCL + Barth-Jespersen (eq. 15): residual on a 3D mesh with every boundary kind,
+    then 200 Euler steps and 20 RK3 steps of the 2D Gaussian (walls) against the oracle,
+    mass conserved."""
+    capi, device = dev
+    tol = TOL64 if prec == "fp64" else TOL32
+    m, bcs = meshes()["cube7"]
+    g = geometry_of(m)
+    dm = device.DeviceMesh(m, bcs, prec=prec)
+    rng = np.random.default_rng(13)
+    u = smooth_field(g.cen, 7) + 2.0
+    vel = rng.normal(size=(g.n_cell, 3))
+    src = rng.normal(size=g.n_cell)
+    want = fv.residual(g, bcs[0], u, vel, 0.1, src=src, recon=1)
+    assert rel(want, fv.residual(g, bcs[0], u, vel, 0.1, src=src)) > 1e-3
+    res = dm.empty(dm.n_cell)
+    capi.fvgb_fv_residual(dm.handle, capi.tcoef(vel=dm.to_device(vel.T), diff=0.1,
+                                                src=dm.to_device(src), bcset=0, recon=1),
+                          dm.to_device(u), res)
+    torch.cuda.synchronize()
+    assert rel(dm.to_host(res), want) < tol
+    dm.free()
+    m, g, u0, vel, dt = _config1()
+    coef = fv.diamond_coefficients(g)
+    w = ls.vertex_weights(g)
+    dm = device.DeviceMesh(m, [WALLS2], prec=prec)
+    for alphas, n in (((1.0,), 200), ((0.5, 0.5, 1.0), 20)):
+        u = u0.copy()
+        for _ in range(n):
+            u = fv.rk_step(g, WALLS2, u, vel, 0.01, dt, alphas=alphas, coef=coef, weights=w, recon=1)
+        ud = dm.to_device(u0)
+        capi.fvgb_fv_step(dm.handle, capi.tcoef(vel_const=vel, diff=0.01, bcset=0, recon=1), ud, dt,
+                          n, stage_alpha=list(alphas))
+        torch.cuda.synchronize()
+        got = dm.to_host(ud)
+        assert rel(got, u) < tol
+        m0 = fv.mass(g, u0)
+        assert abs(capi.fvgb_integral(dm.handle, ud) - m0) <= (1e-13 if prec == "fp64" else 1e-5) * abs(m0)
+    dm.free()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_streamer_steps_muscl(dev, prec):
+    capi, device = dev
+    m = jittered_cube(6, seed=201)
+    g = geometry_of(m)
+    p = streamer.Params(sigma=0.12, peak=1e13, background=1e9, V=12500.0)
+    ne = gaussian(g.cen, p.centre, p.sigma, p.peak, p.background)
+    ni = ne * (1.0 + 0.05 * np.sin(7 * g.cen[:, 0]))
+    dt = 2e-9
+    one, oni = ne.copy(), ni.copy()
+    for _ in range(4):
+        one, oni, ophi, oE, _ = streamer.step(g, p, one, oni, dt, recon=1)
+    dm = device.DeviceMesh(m, [streamer.bc_ne(), streamer.bc_phi(p)],
+                           prec="fp64" if prec == "fp64" else "mixed")
+    ned, nid = dm.to_device(ne), dm.to_device(ni)
+    phid = torch.zeros(dm.n_cell, dtype=torch.float64, device="cuda")
+    sp = capi.streamer_params(mu=p.mu, A=p.A, B=p.B, De=p.De, dt=dt, recon=1,
+                              solve=capi.solve_opts(rtol=1e-10, prec=capi.FVGB_FP64 if prec == "fp64" else capi.FVGB_FP32))
+    infos = capi.fvgb_streamer_step(dm.handle, sp, ned, nid, phid, None, 4)
+    torch.cuda.synchronize()
+    tol = 1e-7 if prec == "fp64" else TOL32
+    assert rel(dm.to_host(phid), ophi) < 1e-7
+    assert rel(dm.to_host(ned), one) < tol
+    assert rel(dm.to_host(nid), oni) < tol
+    assert all(i["rel_res"] <= 1e-10 for i in infos)
+    dm.free()
