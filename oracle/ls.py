@@ -13,8 +13,8 @@ which implements them independently):
 * The elided f(A_x, A_y, A_z, D) of Algorithm "grad" is the solution of the normal
   equations M_i grad = J_i with M_i = sum d d^T, J_i = sum d (u_j - u_i),
   d = x_j - x_i (A = components of d, D = det M_i).
-* "Alpha: weight coming from the least square method" (Algorithm "ls"): the
-  weights of an unweighted linear least-squares fit u ~ a + b.(x - x_A) over the
+* The weights alpha of Algorithm "ls", which the paper attributes to a least-squares
+  method without giving it: the weights of an unweighted linear least-squares fit u ~ a + b.(x - x_A) over the
   cells around vertex A, u_A = a. When the fit is degenerate (fewer than d+1 cells,
   or the centred scatter matrix C of the cell centres has det C / (tr C / d)^d below
   1e-10) the weights are the plain mean 1/n. A vertex on a Dirichlet face takes the
