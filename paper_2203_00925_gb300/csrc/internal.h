@@ -171,6 +171,7 @@ inline Work<float>& work_of<float>(fvgb_mesh_s* m) { return m->w32; }
 
 constexpr int kRedBlocks = 1024;   // fixed grid of the deterministic reductions
 constexpr int kCgThreads = 512;    // threads per block of the persistent Poisson kernel
+constexpr int kCgBlocksPerSm = 1;  // resident blocks per SM of that kernel
 constexpr int kMaxParts = 128;     // parts of an ensemble mesh handled by one solve
 
 extern std::atomic<long long> g_kernel_launches;

@@ -62,21 +62,20 @@ __device__ bool grid_barrier(Barrier* bar, unsigned nblocks) {
   return ok != 0;
 }
 
-// Block-wide FP64 sum in a fixed order (shared-memory tree, finished by warp 0).
+// Block-wide FP64 sum in a fixed order: a shuffle tree inside each warp, then warp 0
+// sums the warp totals in warp order. Two block barriers. The result is valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
-  sh[threadIdx.x] = v;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();                      // the previous call's readers are done with sh
+  if (l == 0) sh[w] = v;
   __syncthreads();
-  for (unsigned s = blockDim.x >> 1; s >= 32; s >>= 1) {
-    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-    __syncthreads();
-  }
   double t = 0.0;
   if (threadIdx.x < 32) {
-    t = sh[threadIdx.x];
+    t = l < (int)(blockDim.x >> 5) ? sh[l] : 0.0;
     for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
   }
-  __syncthreads();
-  return t;  // valid in thread 0
+  return t;
 }
 
 template <typename T>
@@ -108,16 +107,26 @@ struct SolveArgs {
 };
 
 // Sum the per-sub-chunk partials of K quantities into per-part totals (shared memory
-// tot[k * P + p]), every part in sub-chunk order. Call after a grid barrier.
+// tot[k * P + p]), every part in sub-chunk order. Call after a grid barrier. The partials
+// are first staged in shared memory with one load per thread (one L2 round trip), then
+// each part is summed by one warp: lanes stride 32 over its sub-chunks, then a shuffle tree.
 template <typename T, int K>
-__device__ void part_totals(const SolveArgs<T>& a, const double* buf, double* tot) {
+__device__ void part_totals(const SolveArgs<T>& a, const double* buf, double* tot,
+                            double (*stage)[kCgThreads]) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const bool staged = a.n_sc <= (int)blockDim.x;
+  if (staged) {
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if ((int)threadIdx.x < a.n_sc) stage[k][threadIdx.x] = __ldcg(buf + (size_t)k * a.n_sc + threadIdx.x);
+    __syncthreads();
+  }
   for (int p = warp; p < a.n_part; p += nw) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       double t = 0.0;
       for (int sc = a.part_sc[p] + lane; sc < a.part_sc[p + 1]; sc += 32)
-        t += __ldcg(buf + (size_t)k * a.n_sc + sc);
+        t += staged ? stage[k][sc] : __ldcg(buf + (size_t)k * a.n_sc + sc);
       for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
       if (lane == 0) tot[k * a.n_part + p] = t;
     }
@@ -237,9 +246,12 @@ __device__ __forceinline__ T cg_phase_pq(const SolveArgs<T>& a, int64_t lo, int6
   return acc;
 }
 
+// One 512-thread block per SM (measured faster than two smaller-register blocks: fewer
+// grid-barrier arrivals and partial sums, more rows in flight per thread).
 template <typename T>
-__global__ void __launch_bounds__(kCgThreads) k_cg(SolveArgs<T> a) {
-  __shared__ double sh[kCgThreads];
+__global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> a) {
+  __shared__ double sh[32];
+  __shared__ double stage[2][kCgThreads];
   __shared__ double tot[2 * kMaxParts];
   __shared__ double s_rr[kMaxParts], s_rr0[kMaxParts];
   __shared__ T s_alpha[kMaxParts], s_beta[kMaxParts];
@@ -281,7 +293,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg(SolveArgs<T> a) {
     if (threadIdx.x == 0) { a.buf[sc] = t0; a.buf[a.n_sc + sc] = t1; }
   }
   if (!grid_barrier(a.bar, G)) goto done;
-  part_totals<T, 2>(a, a.buf, tot);
+  part_totals<T, 2>(a, a.buf, tot, stage);
   if (threadIdx.x == 0) s_flag = 0;
   __syncthreads();
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
@@ -308,7 +320,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg(SolveArgs<T> a) {
       if (threadIdx.x == 0) buf[sc] = t;
     }
     if (!grid_barrier(a.bar, G)) goto done;
-    part_totals<T, 1>(a, buf, tot);
+    part_totals<T, 1>(a, buf, tot, stage);
     ++total_its;
     if (threadIdx.x == 0) s_flag = 0;
     __syncthreads();
@@ -334,7 +346,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg(SolveArgs<T> a) {
       if (threadIdx.x == 0) buf[sc] = t;
     }
     if (!grid_barrier(a.bar, G)) goto done;
-    part_totals<T, 1>(a, buf, tot);
+    part_totals<T, 1>(a, buf, tot, stage);
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
       if (s_cg[p] != 0) continue;
       const double pq = tot[p];
@@ -361,7 +373,7 @@ done:
 // sub-chunks in order.
 __global__ void __launch_bounds__(kCgThreads) k_part_sumsq_partial(const double* __restrict__ v,
     const int32_t* __restrict__ blk_sc, const int64_t* __restrict__ sc_begin, double* __restrict__ buf) {
-  __shared__ double sh[kCgThreads];
+  __shared__ double sh[32];
   for (int sc = blk_sc[blockIdx.x]; sc < blk_sc[blockIdx.x + 1]; ++sc) {
     double l = 0.0;
     for (int64_t i = sc_begin[sc] + threadIdx.x; i < sc_begin[sc + 1]; i += blockDim.x) l += v[i] * v[i];
@@ -390,7 +402,8 @@ int solve_grid_size(fvgb_mesh_s* m) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, (const void*)k_cg<double>, kCgThreads, 0) != cudaSuccess)
     return 0;
   const int per_sm = a < b ? a : b;
-  return per_sm >= 1 ? m->num_sms : 0;   // one block per SM
+  if (per_sm < 1) return 0;
+  return (per_sm < kCgBlocksPerSm ? per_sm : kCgBlocksPerSm) * m->num_sms;
 }
 
 cudaError_t launch_part_sumsq(fvgb_mesh_s* m, const double* v, double* out, cudaStream_t s) {
