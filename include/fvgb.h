@@ -244,9 +244,17 @@ fvgb_status fvgb_poisson_rhs(fvgb_mesh m, int32_t bcset, const double* f_dev, do
 typedef struct {
   double rtol;          /* stop when ||b - A phi||_2 <= rtol ||b||_2 (FP64) */
   double inner_rtol;    /* inner CG reduces its residual by this factor (e.g. 0.1) */
-  int32_t maxit_inner;  /* per inner solve */
+  int32_t maxit_inner;  /* per inner CG solve */
   int32_t maxit_outer;  /* outer FP64 refinement steps */
-  int32_t prec;         /* inner CG arithmetic: FVGB_FP64 or FVGB_FP32 (mixed) */
+  int32_t prec;         /* inner solve arithmetic: FVGB_FP64 or FVGB_FP32 (mixed) */
+  int32_t inner;        /* inner solve of the two-point operator A_T: 0 conjugate gradients
+                           (to inner_rtol, at most maxit_inner iterations); k = 1..8: k
+                           V-cycles of smoothed-aggregation multigrid (damped Jacobi,
+                           hierarchy built on the host at the first such solve of the
+                           boundary set and precision - that call synchronises and may
+                           take seconds on large meshes - then kept with the mesh). The
+                           paper solves its Poisson systems with FGMRES + PETSc's
+                           aggregation multigrid (Tables "comp1", "comp2"). */
 } fvgb_solve_opts;
 
 typedef struct {
@@ -269,6 +277,10 @@ typedef struct {
  * Returns FVGB_ENOCONV (with info filled and phi the last iterate) if rtol is not met
  * within maxit_outer steps, FVGB_ENONFINITE on NaN/Inf, FVGB_ETIMEOUT if a grid-wide
  * barrier of the persistent CG kernel gave up. */
+/* Sizes of the multigrid levels built for (bcset, prec) (fine to coarsest) in sizes[0..cap);
+ * returns the number of levels, 0 when none has been built. */
+int32_t fvgb_amg_levels(fvgb_mesh m, int32_t bcset, int32_t prec, int64_t* sizes, int32_t cap);
+
 fvgb_status fvgb_poisson_solve(fvgb_mesh m, int32_t bcset, const double* f_dev,
                                double* phi_dev, const fvgb_solve_opts* opts,
                                fvgb_solve_info* info, void* stream);

@@ -18,8 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfvgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["ops.cu", "solver.cu", "api.cu", "graph.cu", "tune.cu", "mpnn.cu", "noalloc.cu"]
-CPP_SOURCES = ["mesh_host.cpp"]
+CU_SOURCES = ["ops.cu", "solver.cu", "api.cu", "graph.cu", "tune.cu", "mpnn.cu", "noalloc.cu", "amg.cu"]
+CPP_SOURCES = ["mesh_host.cpp", "amg_host.cpp"]
 
 
 def _nvcc():

@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "FVGB_OK", 1: "FVGB_EINVAL", 2: "FVGB_EMESH", 3: "FVGB_ENOMEM
 
 EXPORTED = [
     "fvgb_mesh_upload", "fvgb_mesh_upload_ensemble", "fvgb_mesh_parts", "fvgb_solve_parts",
+    "fvgb_amg_levels",
     "fvgb_mesh_free", "fvgb_mesh_info", "fvgb_mesh_cell_perm",
     "fvgb_mesh_vert_perm",
     "fvgb_permute", "fvgb_gradient", "fvgb_vertex_values", "fvgb_fv_residual",
@@ -63,7 +64,7 @@ class fvgb_tcoef(C.Structure):
 
 class fvgb_solve_opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("inner_rtol", C.c_double), ("maxit_inner", C.c_int32),
-                ("maxit_outer", C.c_int32), ("prec", C.c_int32)]
+                ("maxit_outer", C.c_int32), ("prec", C.c_int32), ("inner", C.c_int32)]
 
 
 class fvgb_solve_info(C.Structure):
@@ -99,6 +100,7 @@ _sig = {
                                             _vp, C.POINTER(_vp)]),
     "fvgb_mesh_parts": (C.c_int, [_vp, C.POINTER(_i32), _vp]),
     "fvgb_solve_parts": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "fvgb_amg_levels": (C.c_int32, [_vp, _i32, _i32, _vp, _i32]),
     "fvgb_mesh_free": (C.c_int, [_vp]),
     "fvgb_mesh_info": (C.c_int, [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64),
                                  C.POINTER(_i64)]),
@@ -333,8 +335,17 @@ def fvgb_poisson_rhs(m, bcset, f, b, stream=None):
                   "fvgb_poisson_rhs")
 
 
-def solve_opts(rtol=1e-8, inner_rtol=0.1, maxit_inner=20000, maxit_outer=200, prec=FVGB_FP64):
-    return fvgb_solve_opts(float(rtol), float(inner_rtol), int(maxit_inner), int(maxit_outer), int(prec))
+def solve_opts(rtol=1e-8, inner_rtol=0.1, maxit_inner=20000, maxit_outer=200, prec=FVGB_FP64, inner=0):
+    """inner = 0: conjugate gradients on A_T to inner_rtol; k > 0: k multigrid V-cycles."""
+    return fvgb_solve_opts(float(rtol), float(inner_rtol), int(maxit_inner), int(maxit_outer), int(prec),
+                           int(inner))
+
+
+def fvgb_amg_levels(m, bcset, prec):
+    import numpy as np
+    sizes = np.zeros(32, dtype=np.int64)
+    n = lib.fvgb_amg_levels(m, int(bcset), int(prec), ptr(sizes), 32)
+    return sizes[:n].tolist()
 
 
 def fvgb_poisson_solve(m, bcset, f, phi, opts, stream=None, check=True):

@@ -31,22 +31,6 @@ fvgb_status cuda_status(cudaError_t e, const char* what) {
 namespace {
 
 template <typename T>
-cudaError_t dalloc(fvgb_mesh_s* m, T** p, size_t count) {
-  void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
-  if (e == cudaSuccess) m->allocs.push_back(q);
-  *p = (T*)q;
-  return e;
-}
-
-template <typename T>
-cudaError_t dupload(fvgb_mesh_s* m, T** p, const std::vector<T>& h, cudaStream_t s) {
-  cudaError_t e = dalloc(m, p, h.size());
-  if (e != cudaSuccess || h.empty()) return e;
-  return cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s);
-}
-
-template <typename T>
 std::vector<T> cast(const std::vector<double>& v) {
   return std::vector<T>(v.begin(), v.end());
 }
@@ -187,6 +171,7 @@ cudaError_t setup_parts(fvgb_mesh_s* m, const std::vector<int64_t>& part_begin, 
 
 void release(fvgb_mesh_s* m) {
   graph_release(m);
+  amg_release(m);
   if (m->ev_cg0) cudaEventDestroy(m->ev_cg0);
   if (m->ev_cg1) cudaEventDestroy(m->ev_cg1);
   for (void* p : m->allocs) cudaFree(p);
@@ -291,6 +276,7 @@ fvgb_status solve_impl(fvgb_mesh m, int bcset, const double* f, double* phi,
   if (fp32 && !is_fp32(m)) { set_error("FP32 inner solve needs a mesh uploaded with FVGB_FP32 or FVGB_MIXED"); return FVGB_EINVAL; }
   double* b = m->dphi_tmp2;
   double* r = m->dphi_tmp;
+  if (o->inner > 0) FVGB_TRY_ST(amg_ensure(m, bcset, fp32, s));
   fvgb_status st = poisson_rhs_impl(m, bcset, f, b, s);
   if (st) return st;
   // host staging in pinned memory: [0, P) norms, [P, 2P) ints (active flags, inner its)
@@ -367,8 +353,8 @@ fvgb_status solve_impl(fvgb_mesh m, int bcset, const double* f, double* phi,
     m->stats.outer_its++;
     FVGB_TRY(cudaMemcpyAsync(m->parts.active, hact, P * sizeof(int), cudaMemcpyHostToDevice, s), "copy");
     if (m->time_cg) FVGB_TRY(cudaEventRecord(m->ev_cg0, s), "event");
-    if (fp32) FVGB_TRY(launch_cg<float>(m, bcset, r, o->inner_rtol, o->maxit_inner, s), "CG launch");
-    else FVGB_TRY(launch_cg<double>(m, bcset, r, o->inner_rtol, o->maxit_inner, s), "CG launch");
+    if (fp32) FVGB_TRY(launch_inner<float>(m, bcset, r, o, s), "inner solve");
+    else FVGB_TRY(launch_inner<double>(m, bcset, r, o, s), "inner solve");
     if (m->time_cg) {
       FVGB_TRY(cudaEventRecord(m->ev_cg1, s), "event");
       m->cg_pending = true;
@@ -461,7 +447,8 @@ namespace {
 
 bool opts_ok(const fvgb_solve_opts* o) {
   return o && o->rtol > 0.0 && o->inner_rtol > 0.0 && o->inner_rtol < 1.0 && o->maxit_inner > 0 &&
-         o->maxit_outer >= 0 && (o->prec == FVGB_FP64 || o->prec == FVGB_FP32 || o->prec == FVGB_MIXED);
+         o->maxit_outer >= 0 && (o->prec == FVGB_FP64 || o->prec == FVGB_FP32 || o->prec == FVGB_MIXED) &&
+         o->inner >= 0 && o->inner <= 8;
 }
 
 }  // namespace
@@ -682,6 +669,11 @@ fvgb_status fvgb_mesh_parts(fvgb_mesh m, int32_t* n_part, int64_t* cell_begin) {
   if (n_part) *n_part = m->parts.n_part;
   if (cell_begin) std::copy(m->part_cell_begin.begin(), m->part_cell_begin.end(), cell_begin);
   return FVGB_OK;
+}
+
+int32_t fvgb_amg_levels(fvgb_mesh m, int32_t bcset, int32_t prec, int64_t* sizes, int32_t cap) {
+  if (check_mesh(m) || !sizes || cap < 0) return 0;
+  return amg_levels(m, bcset, prec != FVGB_FP64, sizes, cap);
 }
 
 fvgb_status fvgb_solve_parts(fvgb_mesh m, double* rel_res, int32_t* outer_its, int32_t* inner_its) {

@@ -134,6 +134,8 @@ fvgb_status build_graph(fvgb_mesh m, GraphState& g, const fvgb_streamer_params* 
   double* f = m->w64.tmp;
   double* b = m->dphi_tmp2;
   double* r = m->dphi_tmp;
+  // the multigrid hierarchy is built (with host synchronisation) before the capture
+  if (p->solve.inner > 0) FVGB_TRY_ST(amg_ensure(m, p->bcset_phi, fp32_solve, g.cs));
   const long long k0 = g_kernel_launches.load();
   cudaGraph_t graph = nullptr;
   FVGB_TRY(cudaGraphCreate(&graph, 0), "graph create");
@@ -204,10 +206,10 @@ fvgb_status build_graph(fvgb_mesh m, GraphState& g, const fvgb_streamer_params* 
   };
   const int64_t N = m->topo.N;
   if (fp32_solve) {
-    if ((st = cuda_status(launch_cg<float>(m, p->bcset_phi, r, p->solve.inner_rtol, p->solve.maxit_inner, g.cs2), "CG"))) return bail2(st);
+    if ((st = cuda_status(launch_inner<float>(m, p->bcset_phi, r, &p->solve, g.cs2), "inner solve"))) return bail2(st);
     if ((st = cuda_status(launch_add_to_double(m->w32.cg_x, true, phi, N, g.cs2), "update"))) return bail2(st);
   } else {
-    if ((st = cuda_status(launch_cg<double>(m, p->bcset_phi, r, p->solve.inner_rtol, p->solve.maxit_inner, g.cs2), "CG"))) return bail2(st);
+    if ((st = cuda_status(launch_inner<double>(m, p->bcset_phi, r, &p->solve, g.cs2), "inner solve"))) return bail2(st);
     if ((st = cuda_status(launch_add_to_double(m->w64.cg_x, false, phi, N, g.cs2), "update"))) return bail2(st);
   }
   if ((st = poisson_residual(m, p->bcset_phi, phi, b, r, g.cs2))) return bail2(st);

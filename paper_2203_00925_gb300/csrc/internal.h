@@ -101,6 +101,7 @@ struct Barrier {
 };
 
 struct GraphState;
+struct AmgState;
 
 // Launch shape of a tunable kernel: threads per block and elements per thread.
 struct LaunchShape {
@@ -151,6 +152,7 @@ struct fvgb_mesh_s {
   int* warm_used = nullptr;             // [P] 1 where the learned start was kept
   int warm_hist = 0;                    // streamer steps recorded in the history (capped at 2)
   fvgb::GraphState* graph = nullptr;    // captured step graph (graph.cu)
+  fvgb::AmgState* amg = nullptr;        // multigrid hierarchies per boundary set (amg.cu)
   std::vector<void*> allocs;
 };
 
@@ -231,6 +233,31 @@ bool is_fp32(fvgb_mesh m);
     fvgb_status st_ = (expr);                                  \
     if (st_ != FVGB_OK) return st_;                            \
   } while (0)
+
+// Device allocation owned by the mesh (freed with it), and an upload of a host vector.
+template <typename T>
+cudaError_t dalloc(fvgb_mesh_s* m, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, (count > 0 ? count : 1) * sizeof(T));
+  if (e == cudaSuccess) m->allocs.push_back(q);
+  *p = (T*)q;
+  return e;
+}
+template <typename T>
+cudaError_t dupload(fvgb_mesh_s* m, T** p, const std::vector<T>& h, cudaStream_t s) {
+  cudaError_t e = dalloc(m, p, h.size());
+  if (e != cudaSuccess || h.empty()) return e;
+  return cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+// amg.cu: multigrid inner solve (hierarchy built on first use per boundary set and
+// precision; host synchronisation, so not during stream capture)
+fvgb_status amg_ensure(fvgb_mesh m, int bcset, bool fp32, cudaStream_t s);
+void amg_release(fvgb_mesh m);
+int amg_levels(fvgb_mesh m, int bcset, bool fp32, int64_t* sizes, int cap);
+template <typename T>
+cudaError_t launch_amg_inner(fvgb_mesh_s* m, int bcset, const double* r, int cycles, cudaStream_t s);
+
 fvgb_status poisson_residual(fvgb_mesh m, int bcset, const double* x, const double* b, double* r,
                              cudaStream_t s);
 fvgb_status poisson_rhs_impl(fvgb_mesh m, int bcset, const double* f, double* b, cudaStream_t s);
@@ -255,6 +282,16 @@ int solve_grid_size(fvgb_mesh_s* m);
 template <typename T>
 cudaError_t launch_cg(fvgb_mesh_s* m, int bcset, const double* r, double inner_rtol, int maxit,
                       cudaStream_t s);
+
+// the inner solve of the Poisson refinement loop selected by o->inner (result in
+// work_of<T>(m).cg_x, bookkeeping in parts.out_inner / d_cg_info)
+template <typename T>
+cudaError_t launch_inner(fvgb_mesh_s* m, int bcset, const double* r, const fvgb_solve_opts* o,
+                         cudaStream_t s) {
+  if (o->inner > 0) return launch_amg_inner<T>(m, bcset, r, o->inner, s);
+  return launch_cg<T>(m, bcset, r, o->inner_rtol, o->maxit_inner, s);
+}
+
 cudaError_t launch_part_sumsq(fvgb_mesh_s* m, const double* v, double* out, cudaStream_t s);
 
 }  // namespace fvgb

@@ -73,7 +73,10 @@ def test_ensemble_layout_and_transport_bitwise(dev):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_ensemble_poisson_parts_converge_independently(dev, prec):
+@pytest.mark.parametrize("inner", [0, 2])
+def test_ensemble_poisson_parts_converge_independently(dev, prec, inner):
+    """Per-part stopping with the CG inner solve (inner = 0) and with multigrid V-cycles
+    (inner = 2; the hierarchy never mixes parts)."""
     capi, device = dev
     meshes, cases = _ensemble()
     bcs = [[c.bc_ne(), c.bc_phi()] for c in cases]
@@ -82,9 +85,10 @@ def test_ensemble_poisson_parts_converge_independently(dev, prec):
     fs = [-1e3 * (i + 1) * gaussian(g.cen, (0.5, 0.5, 0.5), 0.2) for i, g in enumerate(geos)]
     fd = ens.to_device(np.concatenate(fs), torch.float64)
     phi = torch.zeros(ens.n_cell, dtype=torch.float64, device="cuda")
-    opts = capi.solve_opts(rtol=1e-9, prec=capi.FVGB_FP64 if prec == "fp64" else capi.FVGB_FP32)
+    opts = capi.solve_opts(rtol=1e-9, prec=capi.FVGB_FP64 if prec == "fp64" else capi.FVGB_FP32,
+                           inner=inner)
     st, info = capi.fvgb_poisson_solve(ens.handle, 1, fd, phi, opts)
-    relres, outer, inner = capi.fvgb_solve_parts(ens.handle, 3)
+    relres, outer, its = capi.fvgb_solve_parts(ens.handle, 3)
     assert np.all(relres <= 1e-9) and np.all(outer >= 1)
     got = ens.to_host(phi)
     off = 0
@@ -95,7 +99,7 @@ def test_ensemble_poisson_parts_converge_independently(dev, prec):
         off += g.n_cell
     # a second solve from the solution: no outer step needed for any part
     st, info = capi.fvgb_poisson_solve(ens.handle, 1, fd, phi, opts)
-    relres, outer, inner = capi.fvgb_solve_parts(ens.handle, 3)
+    relres, outer, its = capi.fvgb_solve_parts(ens.handle, 3)
     assert np.all(outer == 0)
     ens.free()
 

@@ -139,3 +139,38 @@ def test_graph_muscl_matches_host(dev, prec):
     for x, y in zip(*outs):
         assert torch.equal(x, y)
     dm.free()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_graph_multigrid_inner_matches_host(dev, prec):
+    """Streamer steps with the multigrid inner solve: graph mode (V-cycles captured in the
+    loop body) gives the host loop's bits, for a single mesh and an ensemble."""
+    capi, device = dev
+    for ensemble in (False, True):
+        if ensemble:
+            meshes = [jittered_cube(k, seed=5000 + k) for k in (9, 6, 7)]
+            cases = [StreamerCase(V=V, centre=(0.5, 0.5, 0.8), sigma=0.15, peak=1e13) for V in (15e3, 25e3, 19e3)]
+            dm = device.DeviceMesh(meshes, [[c.bc_ne(), c.bc_phi()] for c in cases], prec=prec, ensemble=True)
+            ne0 = np.concatenate([c.initial(m)[0] for m, c in zip(meshes, cases)])
+            case = cases[0]
+        else:
+            m = jittered_cube(10, seed=201)
+            case = StreamerCase(sigma=0.15, peak=1e13)
+            dm = device.DeviceMesh(m, [case.bc_ne(), case.bc_phi()], prec=prec)
+            ne0 = case.initial(m)[0]
+        solve = capi.solve_opts(rtol=1e-9, inner=2, prec=capi.FVGB_FP64 if prec == "fp64" else capi.FVGB_FP32)
+        outs = []
+        for graph in (False, True):
+            ne, ni = dm.to_device(ne0), dm.to_device(ne0 * 1.02)
+            phi = torch.zeros(dm.n_cell, dtype=torch.float64, device="cuda")
+            sp = capi.streamer_params(mu=case.mu, A=case.A, B=case.B, De=case.De, dt=2e-9, solve=solve)
+            capi.fvgb_set_graph_mode(dm.handle, graph)
+            infos = capi.fvgb_streamer_step(dm.handle, sp, ne, ni, phi, None, 3)
+            torch.cuda.synchronize()
+            outs.append((ne, ni, phi, infos))
+        capi.fvgb_set_graph_mode(dm.handle, False)
+        for x, y in zip(outs[0][:3], outs[1][:3]):
+            assert torch.equal(x, y)
+        for ia, ib in zip(outs[0][3], outs[1][3]):
+            assert ia["outer_its"] == ib["outer_its"] and ib["rel_res"] <= 1e-9
+        dm.free()

@@ -351,3 +351,44 @@ def test_streamer_steps_muscl(dev, prec):
     assert rel(dm.to_host(nid), oni) < tol
     assert all(i["rel_res"] <= 1e-10 for i in infos)
     dm.free()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_poisson_solve_multigrid_inner(dev, prec):
+    """Multigrid V-cycles as the inner solve: the same convergence guarantees (oracle
+    residual, distance to the direct solution), far fewer outer steps than the CG needs
+    inner iterations, a hierarchy that coarsens, bitwise reproducible."""
+    capi, device = dev
+    m, bcs = meshes()["cube7"]
+    g = geometry_of(m)
+    dm = device.DeviceMesh(m, bcs, prec="fp64" if prec == "fp64" else "mixed")
+    f = -1e3 * gaussian(g.cen, (0.5, 0.5, 0.6), 0.2)
+    want = poisson.solve(g, PHI3, f)
+    fd = dm.to_device(f, torch.float64)
+    opts = capi.solve_opts(rtol=1e-8, inner=2, prec=capi.FVGB_FP64 if prec == "fp64" else capi.FVGB_FP32)
+    phi = torch.zeros(dm.n_cell, dtype=torch.float64, device="cuda")
+    st, info = capi.fvgb_poisson_solve(dm.handle, 1, fd, phi, opts)
+    torch.cuda.synchronize()
+    got = dm.to_host(phi)
+    assert info.rel_res <= 1e-8
+    assert poisson.relative_residual(g, PHI3, f, got) <= 1.01e-8
+    assert rel(got, want) < 1e-6
+    assert 1 <= info.outer_its <= 40 and info.inner_its_total == 2 * info.outer_its
+    sizes = capi.fvgb_amg_levels(dm.handle, 1, capi.FVGB_FP64 if prec == "fp64" else capi.FVGB_FP32)
+    assert sizes[0] == dm.n_cell and sizes == sorted(sizes, reverse=True) and sizes[-1] <= 640
+    phi2 = torch.zeros_like(phi)
+    capi.fvgb_poisson_solve(dm.handle, 1, fd, phi2, opts)
+    assert torch.equal(phi, phi2)
+    dm.free()
+    # a mesh larger than the coarsest size: several levels
+    m2 = jittered_cube(12, seed=5)
+    g2 = geometry_of(m2)
+    dm2 = device.DeviceMesh(m2, [PHI3])
+    f2 = -1e3 * gaussian(g2.cen, (0.4, 0.5, 0.7), 0.15)
+    phi = torch.zeros(dm2.n_cell, dtype=torch.float64, device="cuda")
+    st, info = capi.fvgb_poisson_solve(dm2.handle, 0, dm2.to_device(f2, torch.float64), phi,
+                                       capi.solve_opts(rtol=1e-8, inner=2))
+    torch.cuda.synchronize()
+    assert poisson.relative_residual(g2, PHI3, f2, dm2.to_host(phi)) <= 1.01e-8
+    assert len(capi.fvgb_amg_levels(dm2.handle, 0, capi.FVGB_FP64)) >= 3
+    dm2.free()
