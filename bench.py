@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-transport", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--inner", type=int, default=0,
+                    help="inner solve of the headline run: 0 conjugate gradients (default), "
+                         "k > 0 k multigrid V-cycles per outer step")
     ap.add_argument("--transport-only", default=None, choices=["fp32", "fp64", "both"],
                     help="time only the transport kernels on the 6M-cell mesh (for profiling)")
     return ap.parse_args()
@@ -279,10 +282,11 @@ def ensemble_block(capi, device, torch, stream, warm, nets):
     out = {"meshes": len(cases), "cells": dm.n_cell, "faces": dm.n_face,
            "cells_min_max": [int(min(m.n_cell for m in meshes)), int(max(m.n_cell for m in meshes))],
            "steps": ENSEMBLE_STEPS, "warmup": warm, "dt": dt, "build_and_upload_s": upload_s}
-    runs = {"mixed_graph": (None, False), "extrapolated_mixed_graph": (None, True)}
+    runs = {"mixed_graph": (None, False, 0), "extrapolated_mixed_graph": (None, True, 0),
+            "multigrid_extrapolated_mixed_graph": (None, True, 2)}
     if nets is not None:
-        runs["learned_extrapolated_mixed_graph"] = (nets[True], True)
-    for name, (theta_sc, extrap) in runs.items():
+        runs["learned_extrapolated_mixed_graph"] = (nets[True], True, 0)
+    for name, (theta_sc, extrap, inner) in runs.items():
         net = None
         if theta_sc is not None:
             net = capi.fvgb_mpnn_create(dm.handle, 1)
@@ -290,7 +294,8 @@ def ensemble_block(capi, device, torch, stream, warm, nets):
             capi.fvgb_mpnn_set_scales(net, c0.V, *theta_sc[1])
         sp = capi.streamer_params(mu=c0.mu, A=c0.A, B=c0.B, De=c0.De, dt=dt, warm=net,
                                   extrapolate=extrap,
-                                  solve=capi.solve_opts(rtol=RTOL, inner_rtol=0.1, prec=capi.FVGB_FP32))
+                                  solve=capi.solve_opts(rtol=RTOL, inner_rtol=0.1, prec=capi.FVGB_FP32,
+                                                        inner=inner))
         ne, ni = dm.to_device(ne0), dm.to_device(ne0)
         phi = torch.zeros(dm.n_cell, dtype=torch.float64, device="cuda")
         capi.fvgb_streamer_reset(dm.handle)
@@ -345,7 +350,8 @@ def gpu_arm(args, world, rank, local):
     ne0, ni0 = case.initial(mesh)
     dt = case.dt(1.0 / K_MESH)
     sp = capi.streamer_params(mu=case.mu, A=case.A, B=case.B, De=case.De, dt=dt,
-                              solve=capi.solve_opts(rtol=RTOL, inner_rtol=0.1, prec=capi.FVGB_FP64))
+                              solve=capi.solve_opts(rtol=RTOL, inner_rtol=0.1, prec=capi.FVGB_FP64,
+                                                    inner=args.inner))
     ne, ni = dm.to_device(ne0), dm.to_device(ni0)
     phi = torch.zeros(N, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -402,6 +408,8 @@ def gpu_arm(args, world, rank, local):
     kname = "k_cg<double,4>"
     prof = profile_traffic(kname, source_hash("solver.cu"))
     traffic = prof["dram_bytes_per_launch"] if prof else None
+    if args.inner > 0:          # no CG launches: the CG roofline does not apply
+        achieved = None
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_tflops,
                 "unit": "TFLOP/s", "frac": achieved / peak_tflops if achieved else None,
                 "traffic": traffic,
@@ -455,7 +463,7 @@ def gpu_arm(args, world, rank, local):
         del pairs_p, pairs_x
         train_s = time.time() - t_train0
 
-        def run_variant(prec, graph, warm, extrap=False):
+        def run_variant(prec, graph, warm, extrap=False, inner=0):
             dmv = device.DeviceMesh(mesh, [case.bc_ne(), case.bc_phi()], prec=prec)
             if prec != "fp64":
                 capi.fvgb_autotune(dmv.handle)
@@ -467,7 +475,7 @@ def gpu_arm(args, world, rank, local):
                 capi.fvgb_mpnn_set_scales(net, case.V, *scales)
             spv = capi.streamer_params(
                 mu=case.mu, A=case.A, B=case.B, De=case.De, dt=dt, warm=net, extrapolate=extrap,
-                solve=capi.solve_opts(rtol=RTOL, inner_rtol=0.1,
+                solve=capi.solve_opts(rtol=RTOL, inner_rtol=0.1, inner=inner,
                                       prec=capi.FVGB_FP64 if prec == "fp64" else capi.FVGB_FP32))
             nev, niv = dmv.to_device(ne0), dmv.to_device(ni0)
             phiv = torch.zeros(N, dtype=torch.float64, device="cuda")
@@ -500,7 +508,8 @@ def gpu_arm(args, world, rank, local):
                      "events (no L2 flush between steps); 'extrapolated': the solve starts from "
                      "2 phi^{n-1} - phi^{n-2}; 'learned': the network's correction of the start (from "
                      "the previous potential, or of the extrapolation), kept per part only where it "
-                     "lowers the FP64 residual; networks trained on this mesh from plain runs of "
+                     "lowers the FP64 residual; 'multigrid': 2 smoothed-aggregation V-cycles per "
+                     "outer step instead of the inner CG; networks trained on this mesh from plain runs of "
                      f"{TRAIN_SEEDS} other seed positions x {TRAIN_STEPS} steps ({n_pairs[0]} / "
                      f"{n_pairs[1]} pairs, {TRAIN_EPOCHS} epochs of Adam, {train_s:.1f} s)"),
             "plain_fp64_inner_cg_its_per_step": plain_inner,
@@ -512,6 +521,9 @@ def gpu_arm(args, world, rank, local):
             "learned_extrapolated_fp64": run_variant("fp64", False, True, True),
             "extrapolated_mixed_graph": run_variant("mixed", True, False, True),
             "learned_extrapolated_mixed_graph": run_variant("mixed", True, True, True),
+            "multigrid_fp64": run_variant("fp64", False, False, False, 2),
+            "multigrid_mixed_graph": run_variant("mixed", True, False, False, 2),
+            "multigrid_extrapolated_mixed_graph": run_variant("mixed", True, False, True, 2),
         }
 
     # ---- end to end through the public API with host buffers ------------------------------
@@ -573,7 +585,10 @@ def gpu_arm(args, world, rank, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": N, "faces": dm.n_face,
+            "config": {"workload": WORKLOAD if args.inner == 0 else WORKLOAD.replace(
+                           "FP64 inner CG on the two-point operator",
+                           f"{args.inner} multigrid V-cycles per outer step"),
+                       "cells": N, "faces": dm.n_face,
                        "node_neighbour_entries": dm.n_nbr, "poisson_rtol": RTOL,
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
                        "parallelism": "replicas" if world > 1 else "single GPU",

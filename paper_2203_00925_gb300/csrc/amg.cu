@@ -8,7 +8,7 @@
 // V-cycle on level l with right-hand side b (zero initial guess), damped Jacobi w = 2/3:
 //   x = w D^-1 b;  r = b - A x;  b_{l+1} = R r;  x_{l+1} = V-cycle(l+1);  x += P x_{l+1};
 //   x_out = x + w D^-1 (b - A x);   on the coarsest level x = A^-1 b (dense inverse).
-// Every kernel writes each output element from one thread or one warp summing in a
+// Every kernel writes each output element from one thread or one lane group summing in a
 // fixed order, so the cycle is bitwise reproducible and can be captured in a graph.
 #include <cuda_runtime.h>
 
@@ -26,7 +26,7 @@ struct CsrDev {
   int64_t* ptr = nullptr;
   int32_t* idx = nullptr;
   T* val = nullptr;
-  bool warp_rows = false;   // one warp per row (long rows) instead of one thread
+  int lanes = 1;            // threads per row: 1, 4, 8 or 32 (from the mean row length)
 };
 
 template <typename T>
@@ -72,40 +72,27 @@ __global__ void k_amg_jacobi0(int64_t n, const T* __restrict__ dinv, const T* __
   if (i < n) x[i] = w * dinv[i] * b[i];
 }
 
-// Row sum sum_a M[i, a] v[a] of one row, thread or warp variant.
-template <typename T>
-__device__ __forceinline__ T row_dot_thread(const int64_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                                            const T* __restrict__ val, const T* __restrict__ v, int64_t i) {
-  T s = T(0);
-  for (int64_t a = ptr[i]; a < ptr[i + 1]; ++a) s += val[a] * v[idx[a]];
-  return s;
-}
-template <typename T>
-__device__ __forceinline__ T row_dot_warp(const int64_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                                          const T* __restrict__ val, const T* __restrict__ v, int64_t i, int lane) {
-  T s = T(0);
-  for (int64_t a = ptr[i] + lane; a < ptr[i + 1]; a += 32) s += val[a] * v[idx[a]];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  return __shfl_sync(0xffffffffu, s, 0);
-}
-
-// mode 0: y = M v; 1: y += M v; 2: y = b - M v (residual); 3: y = x + w dinv (b - M x)
-template <typename T, bool WARP>
+// mode 0: y = M v; 1: y += M v; 2: y = b - M v (residual); 3: y = x + w dinv (b - M x).
+// LANES consecutive threads share a row: lane l sums entries l, l + LANES, ..., then a
+// shuffle tree over the group (fixed order).
+template <typename T, int LANES>
 __global__ void __launch_bounds__(kAmgThreads)
 k_amg_csr(int64_t n, const int64_t* __restrict__ ptr, const int32_t* __restrict__ idx,
           const T* __restrict__ val, const T* __restrict__ v, const T* __restrict__ b,
           const T* __restrict__ dinv, T w, int mode, T* __restrict__ y) {
-  int64_t i;
-  int lane = 0;
-  if (WARP) {
-    i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    lane = threadIdx.x & 31;
-  } else {
-    i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i = t / LANES;
+  const int lane = (int)(t % LANES);
+  const bool valid = i < n;
+  T s = T(0);
+  if (valid)
+    for (int64_t a = ptr[i] + lane; a < ptr[i + 1]; a += LANES) s += val[a] * v[idx[a]];
+  if (LANES > 1) {
+    // every lane of the warp takes part in the shuffles (rows past n contribute 0)
+#pragma unroll
+    for (int o = LANES / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, LANES);
   }
-  if (i >= n) return;
-  const T s = WARP ? row_dot_warp(ptr, idx, val, v, i, lane) : row_dot_thread(ptr, idx, val, v, i);
-  if (WARP && lane != 0) return;
+  if (!valid || lane != 0) return;
   if (mode == 0) y[i] = s;
   else if (mode == 1) y[i] += s;
   else if (mode == 2) y[i] = b[i] - s;
@@ -153,12 +140,13 @@ template <typename T>
 cudaError_t csr_launch(const CsrDev<T>& M, const T* v, const T* b, const T* dinv, T w, int mode, T* y,
                        cudaStream_t s) {
   if (M.n == 0) return cudaSuccess;
-  if (M.warp_rows)
-    k_amg_csr<T, true><<<blocks_for(M.n * 32, kAmgThreads), kAmgThreads, 0, s>>>(M.n, M.ptr, M.idx, M.val,
-                                                                              v, b, dinv, w, mode, y);
-  else
-    k_amg_csr<T, false><<<blocks_for(M.n, kAmgThreads), kAmgThreads, 0, s>>>(M.n, M.ptr, M.idx, M.val, v,
-                                                                          b, dinv, w, mode, y);
+  const unsigned g = blocks_for(M.n * M.lanes, kAmgThreads);
+  switch (M.lanes) {
+    case 32: k_amg_csr<T, 32><<<g, kAmgThreads, 0, s>>>(M.n, M.ptr, M.idx, M.val, v, b, dinv, w, mode, y); break;
+    case 8: k_amg_csr<T, 8><<<g, kAmgThreads, 0, s>>>(M.n, M.ptr, M.idx, M.val, v, b, dinv, w, mode, y); break;
+    case 4: k_amg_csr<T, 4><<<g, kAmgThreads, 0, s>>>(M.n, M.ptr, M.idx, M.val, v, b, dinv, w, mode, y); break;
+    default: k_amg_csr<T, 1><<<g, kAmgThreads, 0, s>>>(M.n, M.ptr, M.idx, M.val, v, b, dinv, w, mode, y); break;
+  }
   count_launch();
   return cudaGetLastError();
 }
@@ -168,7 +156,8 @@ cudaError_t upload_csr(fvgb_mesh_s* m, const HostCsr& h, CsrDev<T>& d, cudaStrea
   d.n = h.n;
   d.m = h.m;
   d.nnz = (int64_t)h.idx.size();
-  d.warp_rows = h.n > 0 && d.nnz > 12 * h.n;
+  const double mean = h.n > 0 ? (double)d.nnz / (double)h.n : 0.0;
+  d.lanes = mean <= 6.0 ? 1 : mean <= 24.0 ? 4 : mean <= 64.0 ? 8 : 32;
   cudaError_t e;
   if ((e = dupload(m, &d.ptr, h.ptr, s))) return e;
   if ((e = dupload(m, &d.idx, h.idx, s))) return e;
