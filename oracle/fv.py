@@ -158,7 +158,7 @@ def residual(geo, bc, u, vel, D, src=None, coef=None, weights=None, recon=0):
     F = face_flux(geo, bc, u, vel, D, coef, weights, recon)
     N = geo.n_cell
     inr = geo.face_R >= 0
-    acc = np.bincount(geo.face_R[inr], weights=F[inr], minlength=N)
+    acc = np.bincount(geo.face_R[inr], weights=F[inr], minlength=N).astype(np.float64)
     acc -= np.bincount(geo.face_L, weights=F, minlength=N)
     res = acc / geo.vol
     if src is not None:

@@ -284,7 +284,8 @@ cudaError_t launch_amg_inner(fvgb_mesh_s* m, int bcset, const double* r, int cyc
   count_launch();
   if ((e = cudaGetLastError())) return e;
   if ((e = vcycle(a, 0, a.t0, w.cg_x, s))) return e;
-  for (int c = 1; c < cycles; ++c) {
+  // with no levels (a mesh of at most kAmgCoarseMax cells) the dense solve is exact
+  for (int c = 1; c < cycles && !a.lv.empty(); ++c) {
     if ((e = csr_launch(a.lv[0].A, w.cg_x, a.t0, a.lv[0].dinv, T(0), 2, a.t1, s))) return e;
     if ((e = vcycle(a, 0, a.t1, a.t2, s))) return e;
     k_amg_add<T><<<blocks_for(N, kAmgThreads), kAmgThreads, 0, s>>>(N, a.t2, w.cg_x);

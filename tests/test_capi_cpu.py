@@ -92,6 +92,22 @@ def test_malformed_meshes_are_rejected_on_the_host(capi):
     assert st in (capi.FVGB_EINVAL, capi.FVGB_EMESH)
 
 
+def _single_tet():
+    from synth.meshgen import Mesh
+    xyz = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    cells = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    bface = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]], dtype=np.int32)
+    return Mesh(3, xyz, cells, bface, np.array([1, 2, 3, 4], dtype=np.int32), 1.0)
+
+
+def test_singular_gradient_stencil_is_rejected_on_the_host(capi):
+    """A lone tetrahedron has no node neighbours: with Neumann faces only, its
+    least-squares gradient (Algorithm "grad") has no points and the upload refuses it;
+    with Dirichlet faces the ghost points make it well defined (checked on the GPU)."""
+    st, msg = _upload(capi, _single_tet(), bcs=[{t: (capi_kind("neumann"), 0.0) for t in range(1, 5)}])
+    assert st == capi.FVGB_EMESH and "singular" in msg
+
+
 def test_null_handle_calls_fail_cleanly(capi):
     assert capi.lib.fvgb_gradient(None, 0, None, None, None) == capi.FVGB_EINVAL
     assert capi.lib.fvgb_poisson_solve(None, 0, None, None, None, None, None) == capi.FVGB_EINVAL
