@@ -28,12 +28,14 @@ UNIT = "cell-updates/s"
 K_MESH = 50                 # 6 * 50^3 = 750,000 cells
 MESH_SEED = 201
 RTOL = 1e-8
+INNER_RTOL = 0.2            # inner CG reduction per outer step (measured fastest of 0.03-0.5)
 ORACLE_SAMPLE_K = 12        # 10,368 cells, same recipe
 TRAIN_SEEDS, TRAIN_STEPS, TRAIN_EPOCHS = 8, 50, 5   # learned warm start training set
 WORKLOAD = ("3D electron drift-diffusion + Poisson, FP64 plain method: unit cube, 50^3 "
             "jittered hexes x 6 Kuhn tets (750,000 cells), seed at (0.5,0.5,0.9), V = 12.5 kV, "
             "Poisson to rel. residual 1e-8 each step (FP64 defect correction + FP64 inner CG "
-            "on the two-point operator, warm start from the previous potential)")
+            "on the two-point operator reducing its residual 5x per outer step, warm start from "
+            "the previous potential)")
 
 
 def parse():
@@ -294,7 +296,7 @@ def ensemble_block(capi, device, torch, stream, warm, nets):
             capi.fvgb_mpnn_set_scales(net, c0.V, *theta_sc[1])
         sp = capi.streamer_params(mu=c0.mu, A=c0.A, B=c0.B, De=c0.De, dt=dt, warm=net,
                                   extrapolate=extrap,
-                                  solve=capi.solve_opts(rtol=RTOL, inner_rtol=0.1, prec=capi.FVGB_FP32,
+                                  solve=capi.solve_opts(rtol=RTOL, inner_rtol=INNER_RTOL, prec=capi.FVGB_FP32,
                                                         inner=inner))
         ne, ni = dm.to_device(ne0), dm.to_device(ne0)
         phi = torch.zeros(dm.n_cell, dtype=torch.float64, device="cuda")
@@ -350,7 +352,7 @@ def gpu_arm(args, world, rank, local):
     ne0, ni0 = case.initial(mesh)
     dt = case.dt(1.0 / K_MESH)
     sp = capi.streamer_params(mu=case.mu, A=case.A, B=case.B, De=case.De, dt=dt,
-                              solve=capi.solve_opts(rtol=RTOL, inner_rtol=0.1, prec=capi.FVGB_FP64,
+                              solve=capi.solve_opts(rtol=RTOL, inner_rtol=INNER_RTOL, prec=capi.FVGB_FP64,
                                                     inner=args.inner))
     ne, ni = dm.to_device(ne0), dm.to_device(ni0)
     phi = torch.zeros(N, dtype=torch.float64, device="cuda")
@@ -442,7 +444,7 @@ def gpu_arm(args, world, rank, local):
                   for _ in range(TRAIN_SEEDS)]
         pairs_p, pairs_x = [], []
         for c in tcases:
-            _, pp, px = learned.streamer_run(dm, c, mesh, dt, TRAIN_STEPS, capi.solve_opts(rtol=RTOL),
+            _, pp, px = learned.streamer_run(dm, c, mesh, dt, TRAIN_STEPS, capi.solve_opts(rtol=RTOL, inner_rtol=INNER_RTOL),
                                              record=True)
             pairs_p += pp
             pairs_x += px
@@ -475,7 +477,7 @@ def gpu_arm(args, world, rank, local):
                 capi.fvgb_mpnn_set_scales(net, case.V, *scales)
             spv = capi.streamer_params(
                 mu=case.mu, A=case.A, B=case.B, De=case.De, dt=dt, warm=net, extrapolate=extrap,
-                solve=capi.solve_opts(rtol=RTOL, inner_rtol=0.1, inner=inner,
+                solve=capi.solve_opts(rtol=RTOL, inner_rtol=INNER_RTOL, inner=inner,
                                       prec=capi.FVGB_FP64 if prec == "fp64" else capi.FVGB_FP32))
             nev, niv = dmv.to_device(ne0), dmv.to_device(ni0)
             phiv = torch.zeros(N, dtype=torch.float64, device="cuda")
@@ -586,7 +588,7 @@ def gpu_arm(args, world, rank, local):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD if args.inner == 0 else WORKLOAD.replace(
-                           "FP64 inner CG on the two-point operator",
+                           "FP64 inner CG on the two-point operator reducing its residual 5x per outer step",
                            f"{args.inner} multigrid V-cycles per outer step"),
                        "cells": N, "faces": dm.n_face,
                        "node_neighbour_entries": dm.n_nbr, "poisson_rtol": RTOL,

@@ -57,7 +57,7 @@ def oracle_params(case):
 
 
 def bench_solve(capi, prec):
-    return capi.solve_opts(rtol=1e-8, inner_rtol=0.1,
+    return capi.solve_opts(rtol=1e-8, inner_rtol=0.2,
                            prec=capi.FVGB_FP64 if prec == "fp64" else capi.FVGB_FP32)
 
 
