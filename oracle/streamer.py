@@ -15,7 +15,10 @@ replace them with (SI units, lengths in metres):
   the other sides;
 * one explicit Euler step: solve Poisson with n^k, E = -grad V (least-squares cell
   gradient with the Dirichlet ghost points), fluxes and source with n_e^k, then
-  n_e^{k+1} = n_e^k + dt R(n_e^k), n_p^{k+1} = n_p^k + dt S_e.
+  n_e^{k+1} = n_e^k + dt R(n_e^k), n_p^{k+1} = n_p^k + dt S_e;
+* the three-stage scheme of eq. 6 applies that update per stage, with the Poisson
+  solve, the field and the source recomputed from the stage densities:
+  n^(j) = n^k + alpha_j dt Res(n^(j-1)), alpha = (1/2, 1/2, 1), n^{k+1} = n^(3).
 
 The ion density is written n_i here (the paper's n_p).
 """
@@ -60,16 +63,22 @@ def cell_physics(p, E, ne):
     return v, S
 
 
-def step(geo, p, ne, ni, dt, phi=None, dense=False, recon=0):
-    """One explicit Euler step of eq. 10; returns (ne, ni, phi, E, S). recon = 1 takes the
-    convective face values of n_e from the MUSCL reconstruction (eq. 15)."""
+def step(geo, p, ne, ni, dt, phi=None, dense=False, recon=0, alphas=(1.0,)):
+    """One step of eq. 10; returns (ne, ni, phi, E, S) of the last stage. alphas = (1,) is
+    explicit Euler, (0.5, 0.5, 1) the three stages of eq. 6 (Poisson solved per stage). A
+    given phi replaces the first stage's solve. recon = 1 takes the convective face values
+    of n_e from the MUSCL reconstruction (eq. 15)."""
     bphi = bc_phi(p)
-    if phi is None:
-        phi = poisson.solve(geo, bphi, poisson_source(ne, ni), dense=dense)
-    E = -ls.ls_gradient(geo, bphi, phi)
-    v, S = cell_physics(p, E, ne)
-    R = fv.residual(geo, bc_ne(), ne, v, p.De, src=S, recon=recon)
-    return ne + dt * R, ni + dt * S, phi, E, S
+    ne0, ni0 = np.asarray(ne, dtype=np.float64), np.asarray(ni, dtype=np.float64)
+    ne_k, ni_k = ne0, ni0
+    for j, a in enumerate(alphas):
+        if j > 0 or phi is None:
+            phi = poisson.solve(geo, bphi, poisson_source(ne_k, ni_k), dense=dense)
+        E = -ls.ls_gradient(geo, bphi, phi)
+        v, S = cell_physics(p, E, ne_k)
+        R = fv.residual(geo, bc_ne(), ne_k, v, p.De, src=S, recon=recon)
+        ne_k, ni_k = ne0 + a * dt * R, ni0 + a * dt * S
+    return ne_k, ni_k, phi, E, S
 
 
 def time_step(p, h):

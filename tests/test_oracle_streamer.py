@@ -45,3 +45,35 @@ def test_no_field_reduces_to_diffusion():
     assert np.abs(E).max() < 1e-20 and np.all(S == 0.0)
     want = ne + 1e-7 * fv.residual(g, streamer.bc_ne(), ne, np.zeros(3), p.De)
     assert np.allclose(ne1, want, rtol=1e-14)
+
+
+RK3 = (0.5, 0.5, 1.0)
+
+
+def test_three_stage_step_without_field_is_the_transport_rk3():
+    """With zero mobility (no drift, no ionisation source) the eq. 6 stages of the streamer
+    step are those of the transport step, pinned against its stage polynomial."""
+    g, p, ne = _setup(4)
+    p.V, p.mu = 0.0, 0.0
+    ne1, ni1, phi, E, S = streamer.step(g, p, ne, ne.copy(), 1e-7, alphas=RK3)
+    want = fv.rk_step(g, streamer.bc_ne(), ne, np.zeros(3), p.De, 1e-7, alphas=RK3)
+    assert np.allclose(ne1, want, rtol=1e-14) and np.array_equal(ni1, ne)
+
+
+def test_three_stage_charge_balance():
+    """The last stage updates from the step's start with alpha = 1 and the field solved from
+    the stage-2 densities, so the total charge changes by exactly dt times the n_e outflow
+    of the stage-2 state under that field."""
+    g, p, ne = _setup()
+    ni = ne * 1.01
+    dt = 1e-9
+    ne2, ni2, _, _, _ = streamer.step(g, p, ne, ni, dt, alphas=RK3[:2])
+    ne3, ni3, phi3, E3, S3 = streamer.step(g, p, ne, ni, dt, alphas=RK3)
+    dq = fv.mass(g, ni3 - ne3) - fv.mass(g, ni - ne)
+    want = dt * streamer.boundary_outflow(g, p, ne2, -p.mu * E3)
+    assert abs(dq - want) <= 1e-12 * fv.mass(g, ne)
+    # and phi3 solves Poisson for the stage-2 charge (one solve per stage)
+    assert poisson.relative_residual(g, streamer.bc_phi(p), streamer.poisson_source(ne2, ni2), phi3) < 1e-10
+    # the stages differ from one Euler step
+    ne_e, _, _, _, _ = streamer.step(g, p, ne, ni, dt)
+    assert np.abs(ne_e - ne3).max() > 1e-6 * np.abs(ne3 - ne).max()
