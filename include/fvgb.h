@@ -311,6 +311,12 @@ typedef struct {
                             difference in time) */
   int32_t recon;         /* convective face value of the n_e transport (fvgb_tcoef.recon):
                             0 first-order upwind, 1 MUSCL + Barth-Jespersen (eq. 15) */
+  int32_t stages;        /* time scheme: 0 or 1 explicit Euler; 3 the three stages of eq. 6
+                            (alpha = 1/2, 1/2, 1), each with its own Poisson solve (from the
+                            previous stage's phi), field and source from the stage densities;
+                            the step's solve info then sums the stages' iterations and keeps
+                            their largest residual; phi and E on return are the last stage's.
+                            Three-stage steps run host-driven also in graph mode. */
 } fvgb_streamer_params;
 
 /* ne_dev, ni_dev: [n_cell] real; phi_dev: [n_cell] double (in: guess, out: last

@@ -80,7 +80,7 @@ class fvgb_streamer_params(C.Structure):
     _fields_ = [("mu", C.c_double), ("A", C.c_double), ("B", C.c_double), ("De", C.c_double),
                 ("dt", C.c_double), ("bcset_ne", C.c_int32), ("bcset_phi", C.c_int32),
                 ("solve", fvgb_solve_opts), ("warm", C.c_void_p), ("extrapolate", C.c_int32),
-                ("recon", C.c_int32)]
+                ("recon", C.c_int32), ("stages", C.c_int32)]
 
 
 class fvgb_stats(C.Structure):
@@ -358,10 +358,10 @@ def fvgb_poisson_solve(m, bcset, f, phi, opts, stream=None, check=True):
 
 
 def streamer_params(mu=0.0382, A=4332.0, B=2.0e5, De=0.1, dt=1e-9, bcset_ne=0, bcset_phi=1,
-                    solve=None, warm=None, extrapolate=False, recon=0):
+                    solve=None, warm=None, extrapolate=False, recon=0, stages=1):
     return fvgb_streamer_params(mu, A, B, De, dt, bcset_ne, bcset_phi,
                                 solve if solve is not None else solve_opts(), warm,
-                                int(bool(extrapolate)), int(recon))
+                                int(bool(extrapolate)), int(recon), int(stages))
 
 
 def fvgb_streamer_reset(m):

@@ -243,6 +243,23 @@ fvgb_status step_T(fvgb_mesh m, const fvgb_tcoef* tc, T* u, double dt, int nstep
 template fvgb_status step_T<float>(fvgb_mesh, const fvgb_tcoef*, float*, double, int, const double*, int, float*, cudaStream_t);
 template fvgb_status step_T<double>(fvgb_mesh, const fvgb_tcoef*, double*, double, int, const double*, int, double*, cudaStream_t);
 
+namespace {
+// One stage of eq. 6 for the transport: u = base + adt Res(u) (the residual at the current
+// u; the update reads base, so u may be overwritten in place) and ni += adt S.
+template <typename T>
+fvgb_status transport_stage(fvgb_mesh m, const fvgb_tcoef* tc, const T* base, T* u, T* ni, double adt,
+                            cudaStream_t s) {
+  Work<T>& w = work_of<T>(m);
+  if (tc->recon) FVGB_TRY_ST(limited_gradient<T>(m, tc, u, s));
+  if (tc->diff != 0.0) FVGB_TRY(launch_vertex<T>(m, tc->bcset, u, w.uv, false, s), "vertex kernel");
+  FVGB_TRY(launch_face<T>(m, tc->bcset, u, w.uv, (const T*)tc->vel_dev, tc->vel_const, true,
+                          tc->diff, false, w.flux, s, tc->recon ? w.grad : nullptr), "face kernel");
+  FVGB_TRY(launch_update<T>(m, kStep, w.flux, (const T*)tc->src_dev, base, adt, nullptr, u, ni, s),
+           "update kernel");
+  return FVGB_OK;
+}
+}  // namespace
+
 // FP64 full diamond operator pieces
 fvgb_status poisson_residual(fvgb_mesh m, int bcset, const double* x, const double* b, double* r,
                              cudaStream_t s) {
@@ -412,6 +429,39 @@ fvgb_status warm_start(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, voi
   FVGB_TRY(launch_part_sumsq(m, r, m->warm_norms + P, s), "norm kernel");
   return cuda_status(launch_choose_start(m, m->warm_norms, m->warm_norms + P, m->phi_save, phi,
                                          m->warm_used, s), "choose kernel");
+}
+
+// Field, cell physics and one transport stage of eq. 6 (after the stage's solve):
+// ne = ne0 + alpha dt Res(ne), ni = ni0 + alpha dt S, with the field from phi and the
+// source from the current ne.
+fvgb_status streamer_transport_stage(fvgb_mesh m, const fvgb_streamer_params* p, const void* ne0,
+                                     const void* ni0, void* ne, void* ni, const double* phi, void* E,
+                                     double alpha, cudaStream_t s) {
+  const int64_t N = m->topo.N;
+  fvgb_tcoef tc;
+  std::memset(&tc, 0, sizeof(tc));
+  tc.diff = p->De;
+  tc.bcset = p->bcset_ne;
+  tc.recon = p->recon;
+  if (is_fp32(m)) {
+    Work<float>& w = m->w32;
+    FVGB_TRY(launch_convert(phi, w.tmp, N, s), "convert");
+    FVGB_TRY(launch_gradient<float>(m, p->bcset_phi, w.tmp, w.grad, s), "gradient kernel");
+    FVGB_TRY(launch_cell_physics<float>(m, w.grad, (const float*)ne, p->mu, p->A, p->B, (float*)E,
+                                        w.vel, w.src, s), "cell kernel");
+    FVGB_TRY(cudaMemcpyAsync(ni, ni0, N * sizeof(float), cudaMemcpyDeviceToDevice, s), "copy");
+    tc.vel_dev = w.vel;
+    tc.src_dev = w.src;
+    return transport_stage<float>(m, &tc, (const float*)ne0, (float*)ne, (float*)ni, alpha * p->dt, s);
+  }
+  Work<double>& w = m->w64;
+  FVGB_TRY(launch_gradient<double>(m, p->bcset_phi, phi, w.grad, s), "gradient kernel");
+  FVGB_TRY(launch_cell_physics<double>(m, w.grad, (const double*)ne, p->mu, p->A, p->B, (double*)E,
+                                       w.vel, w.src, s), "cell kernel");
+  FVGB_TRY(cudaMemcpyAsync(ni, ni0, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+  tc.vel_dev = w.vel;
+  tc.src_dev = w.src;
+  return transport_stage<double>(m, &tc, (const double*)ne0, (double*)ne, (double*)ni, alpha * p->dt, s);
 }
 
 // Field, cell physics and the transport update of one streamer step (after the solve).
@@ -783,7 +833,8 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
                                double* phi, void* E, int32_t nsteps, fvgb_solve_info* info,
                                void* stream) {
   if (fvgb_status st = check_mesh(m)) return st;
-  if (!p || !ne || !ni || !phi || nsteps < 0 || !opts_ok(&p->solve) || (p->recon != 0 && p->recon != 1)) { set_error("bad streamer arguments"); return FVGB_EINVAL; }
+  if (!p || !ne || !ni || !phi || nsteps < 0 || !opts_ok(&p->solve) || (p->recon != 0 && p->recon != 1) ||
+      (p->stages != 0 && p->stages != 1 && p->stages != 3)) { set_error("bad streamer arguments"); return FVGB_EINVAL; }
   if (fvgb_status st = check_bcset(m, p->bcset_ne)) return st;
   if (fvgb_status st = check_bcset(m, p->bcset_phi)) return st;
   const bool fp32_solve = p->solve.prec == FVGB_FP32 || p->solve.prec == FVGB_MIXED;
@@ -791,7 +842,8 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
   cudaStream_t s = (cudaStream_t)stream;
   int n0 = 0;
   const bool warm = warm_requested(p);
-  if (m->use_graph) {
+  const int stages = p->stages == 3 ? 3 : 1;
+  if (m->use_graph && stages == 1) {
     // a captured step assumes a full warm-start history: build it with host-driven steps
     const int need = warm ? std::max(0, 2 - m->warm_hist) : 0;
     if (need == 0) return streamer_graph_steps(m, p, ne, ni, phi, E, nsteps, info, s);
@@ -806,12 +858,38 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
       if (st) return st;
       m->warm_hist = std::min(2, m->warm_hist + 1);
     }
-    fvgb_status st = cuda_status(launch_poisson_source(m, ne, ni, fp32, f, s), "source kernel");
-    if (st) return st;
-    st = solve_impl(m, p->bcset_phi, f, phi, &p->solve, info ? info + n : nullptr, s);
-    if (st) return st;
-    st = streamer_transport(m, p, ne, ni, phi, E, s);
-    if (st) return st;
+    if (stages == 1) {
+      fvgb_status st = cuda_status(launch_poisson_source(m, ne, ni, fp32, f, s), "source kernel");
+      if (st) return st;
+      st = solve_impl(m, p->bcset_phi, f, phi, &p->solve, info ? info + n : nullptr, s);
+      if (st) return st;
+      st = streamer_transport(m, p, ne, ni, phi, E, s);
+      if (st) return st;
+      continue;
+    }
+    // three stages of eq. 6, each with its own Poisson solve (from the previous stage's phi)
+    const size_t bytes = (size_t)m->topo.N * (fp32 ? sizeof(float) : sizeof(double));
+    if (!m->rk_ne0) {
+      FVGB_TRY(dalloc(m, (unsigned char**)&m->rk_ne0, bytes), "allocation");
+      FVGB_TRY(dalloc(m, (unsigned char**)&m->rk_ni0, bytes), "allocation");
+    }
+    FVGB_TRY(cudaMemcpyAsync(m->rk_ne0, ne, bytes, cudaMemcpyDeviceToDevice, s), "copy");
+    FVGB_TRY(cudaMemcpyAsync(m->rk_ni0, ni, bytes, cudaMemcpyDeviceToDevice, s), "copy");
+    static const double kAlpha[3] = {0.5, 0.5, 1.0};
+    fvgb_solve_info acc{0, 0, 0.0, 0.0};
+    for (int k = 0; k < 3; ++k) {
+      fvgb_solve_info si{0, 0, 0.0, 0.0};
+      fvgb_status st = cuda_status(launch_poisson_source(m, ne, ni, fp32, f, s), "source kernel");
+      if (!st) st = solve_impl(m, p->bcset_phi, f, phi, &p->solve, &si, s);
+      acc.outer_its += si.outer_its;
+      acc.inner_its_total += si.inner_its_total;
+      acc.rel_res = std::max(acc.rel_res, si.rel_res);
+      acc.bnorm = si.bnorm;
+      if (info) info[n] = acc;
+      if (st) return st;
+      st = streamer_transport_stage(m, p, m->rk_ne0, m->rk_ni0, ne, ni, phi, E, kAlpha[k], s);
+      if (st) return st;
+    }
   }
   if (n0 > 0) return streamer_graph_steps(m, p, ne, ni, phi, E, n0, info ? info + nsteps : nullptr, s);
   return FVGB_OK;

@@ -121,7 +121,8 @@ bool same_params(const fvgb_streamer_params& a, const fvgb_streamer_params& b) {
          a.bcset_ne == b.bcset_ne && a.bcset_phi == b.bcset_phi && a.solve.rtol == b.solve.rtol &&
          a.solve.inner_rtol == b.solve.inner_rtol && a.solve.maxit_inner == b.solve.maxit_inner &&
          a.solve.maxit_outer == b.solve.maxit_outer && a.solve.prec == b.solve.prec &&
-         a.warm == b.warm && a.extrapolate == b.extrapolate && a.recon == b.recon;
+         a.warm == b.warm && a.extrapolate == b.extrapolate && a.recon == b.recon &&
+         a.stages == b.stages;
 }
 
 cudaError_t capture_error(cudaError_t e) { return e; }

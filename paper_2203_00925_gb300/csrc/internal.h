@@ -153,6 +153,8 @@ struct fvgb_mesh_s {
   int warm_hist = 0;                    // streamer steps recorded in the history (capped at 2)
   fvgb::GraphState* graph = nullptr;    // captured step graph (graph.cu)
   fvgb::AmgState* amg = nullptr;        // multigrid hierarchies per boundary set (amg.cu)
+  void* rk_ne0 = nullptr;               // [N] n_e, n_i at the start of a three-stage streamer step
+  void* rk_ni0 = nullptr;
   std::vector<void*> allocs;
 };
 

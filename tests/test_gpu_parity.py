@@ -392,3 +392,43 @@ def test_poisson_solve_multigrid_inner(dev, prec):
     assert poisson.relative_residual(g2, PHI3, f2, dm2.to_host(phi)) <= 1.01e-8
     assert len(capi.fvgb_amg_levels(dm2.handle, 0, capi.FVGB_FP64)) >= 3
     dm2.free()
+
+
+@pytest.mark.parametrize("prec,recon", [("fp64", 0), ("mixed", 0), ("fp64", 1)])
+def test_streamer_three_stage_steps(dev, prec, recon):
+    """The eq. 6 three-stage streamer step (a Poisson solve per stage) against the oracle's,
+    and graph mode (which runs such steps host-driven) gives the same bits."""
+    capi, device = dev
+    m = jittered_cube(6, seed=201)
+    g = geometry_of(m)
+    p = streamer.Params(sigma=0.12, peak=1e13, background=1e9, V=12500.0)
+    ne = gaussian(g.cen, p.centre, p.sigma, p.peak, p.background)
+    ni = ne * (1.0 + 0.05 * np.sin(7 * g.cen[:, 0]))
+    dt, nsteps = 2e-9, 3
+    one, oni = ne.copy(), ni.copy()
+    for _ in range(nsteps):
+        one, oni, ophi, oE, _ = streamer.step(g, p, one, oni, dt, recon=recon, alphas=(0.5, 0.5, 1.0))
+    dm = device.DeviceMesh(m, [streamer.bc_ne(), streamer.bc_phi(p)],
+                           prec="fp64" if prec == "fp64" else "mixed")
+    outs = []
+    for graph in (False, True):
+        ned, nid = dm.to_device(ne), dm.to_device(ni)
+        phid = torch.zeros(dm.n_cell, dtype=torch.float64, device="cuda")
+        Ed = dm.empty(3, dm.n_cell)
+        sp = capi.streamer_params(mu=p.mu, A=p.A, B=p.B, De=p.De, dt=dt, recon=recon, stages=3,
+                                  solve=capi.solve_opts(rtol=1e-10, prec=capi.FVGB_FP64 if prec == "fp64" else capi.FVGB_FP32))
+        capi.fvgb_set_graph_mode(dm.handle, graph)
+        infos = capi.fvgb_streamer_step(dm.handle, sp, ned, nid, phid, Ed, nsteps)
+        torch.cuda.synchronize()
+        outs.append((ned, nid, phid, Ed))
+        assert all(i["rel_res"] <= 1e-10 and i["outer_its"] >= 3 for i in infos[1:])
+    capi.fvgb_set_graph_mode(dm.handle, False)
+    ned, nid, phid, Ed = outs[0]
+    tol = 1e-7 if prec == "fp64" else TOL32
+    assert rel(dm.to_host(phid), ophi) < 1e-7
+    assert rel(dm.to_host(ned), one) < tol
+    assert rel(dm.to_host(nid), oni) < tol
+    assert rel(dm.to_host(Ed).T, oE) < 1e-6
+    for x, y in zip(outs[0], outs[1]):
+        assert torch.equal(x, y)
+    dm.free()
