@@ -34,14 +34,16 @@ def _cell_vertex_incidence(geo):
     return sp.csr_matrix((np.ones(N * k), (rows, geo.cells.ravel())), shape=(N, geo.n_vert))
 
 
-def node_neighbour_pairs(geo):
-    """(i, j) for every cell j != i sharing >= 1 vertex with cell i (a set)."""
+def node_neighbour_pairs(geo, with_counts=False):
+    """(i, j) for every cell j != i sharing >= 1 vertex with cell i (a set); with_counts
+    also returns the number of vertices they share."""
     C2V = _cell_vertex_incidence(geo)
     P = (C2V @ C2V.T).tocoo()
     keep = P.row != P.col
     i, j = P.row[keep].astype(np.int64), P.col[keep].astype(np.int64)
+    w = np.rint(P.data[keep]).astype(np.int64)
     o = np.lexsort((j, i))
-    return i[o], j[o]
+    return (i[o], j[o], w[o]) if with_counts else (i[o], j[o])
 
 
 def dirichlet_values(geo, bc):
@@ -53,11 +55,13 @@ def dirichlet_values(geo, bc):
     return g
 
 
-def ghost_point_pairs(geo, bc):
-    """(i, f) for every Dirichlet boundary face f sharing >= 1 vertex with cell i."""
+def ghost_point_pairs(geo, bc, with_counts=False):
+    """(i, f) for every Dirichlet boundary face f sharing >= 1 vertex with cell i;
+    with_counts also returns the number of vertices they share."""
     fd = geo.faces_with_kind(bc, "dirichlet")
     if fd.size == 0:
-        return np.zeros(0, np.int64), np.zeros(0, np.int64)
+        z = np.zeros(0, np.int64)
+        return (z, z, z) if with_counts else (z, z)
     C2V = _cell_vertex_incidence(geo)
     nv = geo.face_vert.shape[1]
     F2V = sp.csr_matrix((np.ones(fd.size * nv), (np.repeat(np.arange(fd.size), nv),
@@ -65,8 +69,9 @@ def ghost_point_pairs(geo, bc):
                         shape=(fd.size, geo.n_vert))
     Q = (C2V @ F2V.T).tocoo()
     i, f = Q.row.astype(np.int64), fd[Q.col]
+    w = np.rint(Q.data).astype(np.int64)
     o = np.lexsort((f, i))
-    return i[o], f[o]
+    return (i[o], f[o], w[o]) if with_counts else (i[o], f[o])
 
 
 def ls_gradient(geo, bc, u):
@@ -90,6 +95,36 @@ def ls_gradient(geo, bc, u):
         J[:, a] = np.bincount(i, weights=dx[:, a] * du, minlength=N)
         for b in range(d):
             M[:, a, b] = np.bincount(i, weights=dx[:, a] * dx[:, b], minlength=N)
+    return np.linalg.solve(M, J[:, :, None])[:, :, 0]
+
+
+def ls_gradient_vertex(geo, bc, u):
+    """Multiplicity-weighted variant of Algorithm "grad" (not in the paper; the
+    vertex-factorised gradient): every node neighbour j of T_i, and every Dirichlet ghost
+    point of Algorithm "grad", counts once per vertex it shares with T_i -
+    grad u_i = M_i^{-1} J_i with M_i = sum m d d^T, J_i = sum m d (u_j - u_i). This is the
+    sum over the vertices A of T_i of the stencil of the cells (and Dirichlet faces) around
+    A; it is exact for linear fields like Algorithm "grad"."""
+    geo.check_bc(bc)
+    u = np.asarray(u, dtype=np.float64)
+    d = geo.dim
+    i, j, w = node_neighbour_pairs(geo, with_counts=True)
+    dx = geo.cen[j] - geo.cen[i]
+    du = u[j] - u[i]
+    gi, gf, gw = ghost_point_pairs(geo, bc, with_counts=True)
+    if gi.size:
+        g = dirichlet_values(geo, bc)
+        dx = np.concatenate([dx, geo.xf[gf] - geo.cen[gi]])
+        du = np.concatenate([du, g[gf] - u[gi]])
+        i = np.concatenate([i, gi])
+        w = np.concatenate([w, gw])
+    N = geo.n_cell
+    M = np.zeros((N, d, d))
+    J = np.zeros((N, d))
+    for a in range(d):
+        J[:, a] = np.bincount(i, weights=w * dx[:, a] * du, minlength=N)
+        for b in range(d):
+            M[:, a, b] = np.bincount(i, weights=w * dx[:, a] * dx[:, b], minlength=N)
     return np.linalg.solve(M, J[:, :, None])[:, :, 0]
 
 
