@@ -227,6 +227,11 @@ def transport_kernels(capi, device, torch, stream, flush, precs, reps=10, warm=3
             # star indices + weights (4 per cell) + u + vertex values out
             "vertex_values": (lambda: capi.fvgb_vertex_values(dm.handle, 0, u, uv),
                               4 * N * (4 + w) + N * w + V * w),
+            # multiplicity-weighted variant: records (value, centre) + per-vertex sums over the
+            # stars (star indices, 5 sums out) + per cell its vertices' sums and geometry
+            "gradient_vertex": (lambda: capi.fvgb_gradient_vertex(dm.handle, 1, u, g),
+                                N * (4 * w) + 4 * N * 4 + V * (4 + 3 * w + 5 * w)
+                                + N * (16 + 6 * w + 3 * w) + V * (3 * w + 5 * w)),
             # vertex values, then per face L, R, A, B, C + 3 coefficients + area vector
             # (3) + flux, then cell_face (4) + fluxes + u, velocity (3), source, 1/mu, out
             "fv_residual": (lambda: capi.fvgb_fv_residual(dm.handle, tc, u, res), res_bytes),

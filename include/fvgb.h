@@ -164,6 +164,15 @@ fvgb_status fvgb_permute(fvgb_mesh m, const void* src_dev, void* dst_dev, int32_
 fvgb_status fvgb_gradient(fvgb_mesh m, int32_t bcset, const void* u_dev, void* grad_dev,
                           void* stream);
 
+/* Multiplicity-weighted variant of the gradient of Algorithm "grad" (not in the paper;
+ * the vertex-factorised form): every neighbour cell j, and every Dirichlet ghost point,
+ * counts once per vertex it shares with cell i - grad u_i = Mv_i^{-1} sum m_ij d_ij
+ * (u_j - u_i). Exact for linear fields like fvgb_gradient but a different stencil weighting,
+ * computed as per-vertex sums over the cells around each vertex (a fraction of the
+ * node-neighbour gathers). Arguments and layout as fvgb_gradient. */
+fvgb_status fvgb_gradient_vertex(fvgb_mesh m, int32_t bcset, const void* u_dev, void* grad_dev,
+                                 void* stream);
+
 /* Least-squares vertex values of Algorithm "ls": u_A = sum_c alpha_{A,c} u_c over the
  * cells around vertex A (linear least-squares fit; mean when the fit is degenerate);
  * vertices on a Dirichlet face of set bcset take g.

@@ -32,7 +32,7 @@ EXPORTED = [
     "fvgb_amg_levels",
     "fvgb_mesh_free", "fvgb_mesh_info", "fvgb_mesh_cell_perm",
     "fvgb_mesh_vert_perm",
-    "fvgb_permute", "fvgb_gradient", "fvgb_vertex_values", "fvgb_fv_residual",
+    "fvgb_permute", "fvgb_gradient", "fvgb_gradient_vertex", "fvgb_vertex_values", "fvgb_fv_residual",
     "fvgb_fv_residual_noalloc",
     "fvgb_fv_step", "fvgb_poisson_apply", "fvgb_poisson_rhs", "fvgb_poisson_solve",
     "fvgb_streamer_step", "fvgb_streamer_reset", "fvgb_set_graph_mode",
@@ -108,6 +108,7 @@ _sig = {
     "fvgb_mesh_vert_perm": (C.c_int, [_vp, _vp]),
     "fvgb_permute": (C.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _vp]),
     "fvgb_gradient": (C.c_int, [_vp, _i32, _vp, _vp, _vp]),
+    "fvgb_gradient_vertex": (C.c_int, [_vp, _i32, _vp, _vp, _vp]),
     "fvgb_vertex_values": (C.c_int, [_vp, _i32, _vp, _vp, _vp]),
     "fvgb_fv_residual": (C.c_int, [_vp, C.POINTER(fvgb_tcoef), _vp, _vp, _vp]),
     "fvgb_fv_residual_noalloc": (C.c_int, [_vp, C.POINTER(fvgb_tcoef), _vp, _vp, _vp]),
@@ -286,6 +287,11 @@ def fvgb_permute(m, src, dst, n_comp, elem_bytes, to_internal, stream=None):
 
 def fvgb_gradient(m, bcset, u, grad, stream=None):
     return _check(lib.fvgb_gradient(m, bcset, ptr(u), ptr(grad), stream_handle(stream)), "fvgb_gradient")
+
+
+def fvgb_gradient_vertex(m, bcset, u, grad, stream=None):
+    return _check(lib.fvgb_gradient_vertex(m, bcset, ptr(u), ptr(grad), stream_handle(stream)),
+                  "fvgb_gradient_vertex")
 
 
 def fvgb_vertex_values(m, bcset, u, uv, stream=None):

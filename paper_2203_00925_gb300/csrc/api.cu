@@ -90,6 +90,15 @@ cudaError_t upload_geo(fvgb_mesh_s* m, const HostMesh& h, const std::vector<doub
   if (lo && (e = dupload(m, &g.xf_lo, lo_part(h.xf), s))) return e;
   if ((e = dupload(m, &g.coef, cast<T>(h.coef), s))) return e;
   if ((e = dupload(m, &g.valpha, cast<T>(sw), s))) return e;
+  {
+    const int d = h.dim;
+    std::vector<double> xv((size_t)d * h.V);
+    for (int64_t v = 0; v < h.V; ++v)
+      for (int a = 0; a < d; ++a) xv[a * h.V + v] = h.xyz[v * d + a];
+    if ((e = dupload(m, &g.xv, hi_part(xv), s))) return e;
+    if (lo && (e = dupload(m, &g.xv_lo, lo_part(xv), s))) return e;
+    if ((e = dupload(m, &g.vs1, cast<T>(h.vs1), s))) return e;
+  }
   g.bc.resize(h.bcs.size());
   for (size_t k = 0; k < h.bcs.size(); ++k) {
     const BCSetHost& b = h.bcs[k];
@@ -99,6 +108,8 @@ cudaError_t upload_geo(fvgb_mesh_s* m, const HostMesh& h, const std::vector<doub
     if ((e = dupload(m, &d.minv, cast<T>(b.minv), s))) return e;
     if ((e = dupload(m, &d.gptr, b.gptr, s))) return e;
     if ((e = dupload(m, &d.gface, b.gface, s))) return e;
+    if ((e = dupload(m, &d.gmult, b.gmult, s))) return e;
+    if ((e = dupload(m, &d.minv_v, cast<T>(b.minv_v), s))) return e;
     if ((e = dupload(m, &d.vdir, cast<T>(b.vdir), s))) return e;
     if ((e = dupload(m, &d.at_nbr, b.at_nbr, s))) return e;
     if ((e = dupload(m, &d.at_coef, cast<T>(b.at_coef), s))) return e;
@@ -119,6 +130,7 @@ cudaError_t alloc_work(fvgb_mesh_s* m, Work<T>& w) {
   if ((e = dalloc(m, &w.src, t.N))) return e;
   if ((e = dalloc(m, &w.grad, t.dim * t.N))) return e;
   if ((e = dalloc(m, &w.grec, (sizeof(T) == 4 ? 8 : 4) * t.N))) return e;
+  if ((e = dalloc(m, &w.vsum, 5 * t.V))) return e;
   if ((e = dalloc(m, &w.cg_r, t.N))) return e;
   if ((e = dalloc(m, &w.cg_p, t.N))) return e;
   if ((e = dalloc(m, &w.cg_q, t.N))) return e;
@@ -629,6 +641,12 @@ static fvgb_status upload_impl(int32_t dim, int64_t n_vert, const double* xyz, i
   if ((e = dupload(m, &t.fvert, h.fvert, s))) return fail(e, "upload");
   if ((e = dupload(m, &t.cell_face, h.cell_face, s))) return fail(e, "upload");
   if ((e = dupload(m, &t.cell_perm, h.cell_perm, s))) return fail(e, "upload");
+  if ((e = dupload(m, &t.cverts, h.cells, s))) return fail(e, "upload");
+  {
+    std::vector<int32_t> vc(h.V);
+    for (int64_t v = 0; v < h.V; ++v) vc[v] = h.vptr[v + 1] - h.vptr[v];
+    if ((e = dupload(m, &t.vcount, vc, s))) return fail(e, "upload");
+  }
   std::vector<int64_t> sptr;
   std::vector<int32_t> sidx;
   build_sell(h.nptr, h.nidx, nullptr, h.N, true, sptr, sidx, nullptr);
@@ -768,6 +786,16 @@ fvgb_status fvgb_gradient(fvgb_mesh m, int32_t bcset, const void* u, void* grad,
   cudaStream_t s = (cudaStream_t)stream;
   if (is_fp32(m)) return cuda_status(launch_gradient<float>(m, bcset, (const float*)u, (float*)grad, s), "gradient kernel");
   return cuda_status(launch_gradient<double>(m, bcset, (const double*)u, (double*)grad, s), "gradient kernel");
+}
+
+fvgb_status fvgb_gradient_vertex(fvgb_mesh m, int32_t bcset, const void* u, void* grad, void* stream) {
+  if (fvgb_status st = check_mesh(m)) return st;
+  if (fvgb_status st = check_bcset(m, bcset)) return st;
+  if (!u || !grad) { set_error("null array"); return FVGB_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (is_fp32(m))
+    return cuda_status(launch_gradient_vertex<float>(m, bcset, (const float*)u, (float*)grad, s), "gradient kernels");
+  return cuda_status(launch_gradient_vertex<double>(m, bcset, (const double*)u, (double*)grad, s), "gradient kernels");
 }
 
 fvgb_status fvgb_vertex_values(fvgb_mesh m, int32_t bcset, const void* u, void* uv, void* stream) {

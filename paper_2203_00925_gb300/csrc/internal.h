@@ -27,6 +27,8 @@ struct BCDev {
   T* minv = nullptr;         // [nsym][N]
   int32_t* gptr = nullptr;   // [N+1]
   int32_t* gface = nullptr;  // ghost faces
+  int32_t* gmult = nullptr;  // vertices each ghost face shares with the cell
+  T* minv_v = nullptr;       // [nsym][N] inverse of the multiplicity-weighted normal matrix
   T* vdir = nullptr;         // [V] NaN = not Dirichlet
   int32_t* at_nbr = nullptr; // [N][4] (unused slot: the cell itself)
   T* at_coef = nullptr;      // [N][4] (unused slot: 0)
@@ -45,6 +47,9 @@ struct GeoDev {
   T* xf_lo = nullptr;    // [d][F] (FP32 only)
   T* coef = nullptr;     // [d][F]
   T* valpha = nullptr;   // SELL-padded weights, aligned with vsell.idx
+  T* xv = nullptr;       // [d][V] vertex coordinates (high part in FP32)
+  T* xv_lo = nullptr;    // [d][V] low part (FP32 only)
+  T* vs1 = nullptr;      // [d][V] sum over the cells around A of (x_c - x_A)
   std::vector<BCDev<T>> bc;
 };
 
@@ -56,6 +61,8 @@ struct TopoDev {
   int32_t* fvert = nullptr;      // [d][F]
   int32_t* cell_face = nullptr;  // [d+1][N]
   int32_t* cell_perm = nullptr;  // [N] internal -> caller
+  int32_t* cverts = nullptr;     // [N][d+1] vertices of each cell
+  int32_t* vcount = nullptr;     // [V] cells around each vertex
   Sell nsell;                    // node neighbours of each cell (padded with the cell)
   Sell vsell;                    // cells around each vertex (padded, weight 0)
 };
@@ -71,6 +78,7 @@ struct Work {
   T* src = nullptr;    // [N]
   T* grad = nullptr;   // [d][N]
   T* grec = nullptr;   // [N] packed gradient records (FP64: 4 words, FP32: 8 words)
+  T* vsum = nullptr;   // [5][V] per-vertex sums of the multiplicity-weighted gradient
   T* cg_r = nullptr;   // [N]
   T* cg_p = nullptr;
   T* cg_q = nullptr;
@@ -187,6 +195,9 @@ fvgb_status cuda_status(cudaError_t e, const char* what);
 // ops.cu -------------------------------------------------------------------------------
 template <typename T>
 cudaError_t launch_gradient(fvgb_mesh_s* m, int bcset, const T* u, T* grad, cudaStream_t s);
+// multiplicity-weighted (vertex-factorised) variant of the least-squares gradient
+template <typename T>
+cudaError_t launch_gradient_vertex(fvgb_mesh_s* m, int bcset, const T* u, T* grad, cudaStream_t s);
 template <typename T>
 cudaError_t launch_vertex(fvgb_mesh_s* m, int bcset, const T* u, T* uv, bool homog, cudaStream_t s);
 // face kernel: conv (use velocity), D (diffusion coefficient; -1 gives F = q); lgrad

@@ -430,6 +430,12 @@ int build_host_mesh(int dim, int64_t n_vert, const double* xyz_in, int64_t n_cel
     for (int64_t i = 0; i < N; ++i)
       for (int k = 0; k < nv; ++k) m.vcell[fill[m.cells[i * nv + k]]++] = (int32_t)i;
   }
+  // sum over the cells around each vertex of (x_c - x_A): the multiplicity-weighted
+  // gradient's per-vertex geometry
+  m.vs1.assign((size_t)d * V, 0.0);
+  for (int64_t v = 0; v < V; ++v)
+    for (int32_t t = m.vptr[v]; t < m.vptr[v + 1]; ++t)
+      for (int a = 0; a < d; ++a) m.vs1[a * V + v] += m.cen[a * N + m.vcell[t]] - m.xyz[v * d + a];
 
   // ---- node-neighbour sets ----------------------------------------------------------------
   m.nptr.assign(N + 1, 0);
@@ -536,7 +542,7 @@ int build_host_mesh(int dim, int64_t n_vert, const double* xyz_in, int64_t n_cel
     }
     // ghost points per cell: Dirichlet faces sharing a vertex with the cell
     B.gptr.assign(N + 1, 0);
-    std::vector<std::vector<int32_t>> gl(N);
+    std::vector<std::vector<int32_t>> gl(N), gm(N);
 #pragma omp parallel for schedule(dynamic, 4096)
     for (int64_t i = 0; i < N; ++i) {
       for (int k = 0; k < nv; ++k) {
@@ -544,13 +550,28 @@ int build_host_mesh(int dim, int64_t n_vert, const double* xyz_in, int64_t n_cel
         gl[i].insert(gl[i].end(), dface.begin() + dptr[v], dface.begin() + dptr[v + 1]);
       }
       std::sort(gl[i].begin(), gl[i].end());
-      gl[i].erase(std::unique(gl[i].begin(), gl[i].end()), gl[i].end());
+      // each face appears once per vertex it shares with the cell: keep one, count them
+      std::vector<int32_t>& g = gl[i];
+      size_t w = 0;
+      for (size_t r = 0; r < g.size();) {
+        size_t e = r;
+        while (e < g.size() && g[e] == g[r]) ++e;
+        gm[i].push_back((int32_t)(e - r));
+        g[w++] = g[r];
+        r = e;
+      }
+      g.resize(w);
     }
     for (int64_t i = 0; i < N; ++i) B.gptr[i + 1] = B.gptr[i] + (int32_t)gl[i].size();
     B.gface.resize(B.gptr[N]);
-    for (int64_t i = 0; i < N; ++i) std::copy(gl[i].begin(), gl[i].end(), B.gface.begin() + B.gptr[i]);
+    B.gmult.resize(B.gptr[N]);
+    for (int64_t i = 0; i < N; ++i) {
+      std::copy(gl[i].begin(), gl[i].end(), B.gface.begin() + B.gptr[i]);
+      std::copy(gm[i].begin(), gm[i].end(), B.gmult.begin() + B.gptr[i]);
+    }
     // inverse normal matrices of the least-squares gradient
     B.minv.resize((size_t)nsym * N);
+    B.minv_v.resize((size_t)nsym * N);
     bool singular = false;
 #pragma omp parallel for reduction(|| : singular)
     for (int64_t i = 0; i < N; ++i) {
@@ -572,6 +593,29 @@ int build_host_mesh(int dim, int64_t n_vert, const double* xyz_in, int64_t n_cel
       double inv[6];
       if (!sym_inverse(d, M, inv)) { singular = true; continue; }
       for (int k = 0; k < nsym; ++k) B.minv[k * N + i] = inv[k];
+      // multiplicity-weighted variant: the stencils around the cell's vertices
+      double Mv[9] = {0};
+      auto addv = [&](const double* dx, double wgt) {
+        for (int a = 0; a < d; ++a)
+          for (int b = 0; b < d; ++b) Mv[a * d + b] += wgt * dx[a] * dx[b];
+      };
+      for (int k = 0; k < nv; ++k) {
+        const int32_t v = m.cells[i * nv + k];
+        for (int32_t t = m.vptr[v]; t < m.vptr[v + 1]; ++t) {
+          const int32_t c = m.vcell[t];
+          if (c == i) continue;
+          double dx[3];
+          for (int a = 0; a < d; ++a) dx[a] = m.cen[a * N + c] - m.cen[a * N + i];
+          addv(dx, 1.0);
+        }
+      }
+      for (int32_t t = B.gptr[i]; t < B.gptr[i + 1]; ++t) {
+        double dx[3];
+        for (int a = 0; a < d; ++a) dx[a] = m.xf[a * F + B.gface[t]] - m.cen[a * N + i];
+        addv(dx, (double)B.gmult[t]);
+      }
+      if (!sym_inverse(d, Mv, inv)) { singular = true; continue; }
+      for (int k = 0; k < nsym; ++k) B.minv_v[k * N + i] = inv[k];
     }
     if (singular) { err = "singular least-squares gradient stencil"; return kEMESH; }
     // two-point operator A_T: four slots per cell (cell-major); an unused slot points

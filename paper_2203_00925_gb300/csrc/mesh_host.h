@@ -15,6 +15,8 @@ struct BCSetHost {
   std::vector<double> minv;       // SoA [nsym][N] inverse of the LS normal matrix M_i
   std::vector<int32_t> gptr;      // [N+1] Dirichlet ghost points of each cell (CSR)
   std::vector<int32_t> gface;     //        boundary face index (global face id)
+  std::vector<int32_t> gmult;     //        vertices the face shares with the cell
+  std::vector<double> minv_v;     // SoA [nsym][N] inverse of the multiplicity-weighted matrix
   std::vector<double> vdir;       // [V] Dirichlet vertex value, NaN when not Dirichlet
   std::vector<int32_t> at_nbr;    // [N][4] two-point operator: neighbour (the cell itself if none)
   std::vector<double> at_coef;    // [N][4] off-diagonal coefficient c1 (0 if none)
@@ -41,6 +43,7 @@ struct HostMesh {
   std::vector<int32_t> nptr, nidx;      // node-neighbour sets (CSR, sorted)
   std::vector<int32_t> vptr, vcell;     // cells around each vertex (CSR, sorted)
   std::vector<double> valpha;           // LS interpolation weight of each (vertex, cell)
+  std::vector<double> vs1;              // SoA [dim][V] sum over the cells around A of (x_c - x_A)
   std::vector<BCSetHost> bcs;
   std::vector<int64_t> part_cell_begin; // [P+1] internal cell range of each part
 };

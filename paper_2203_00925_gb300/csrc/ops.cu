@@ -179,6 +179,119 @@ k_gradient(int64_t N, int64_t F, int64_t Fi, const int64_t* __restrict__ sptr,
   }
 }
 
+// ---- multiplicity-weighted least-squares gradient (vertex-factorised variant) ---------------
+// grad u_i = Mv_i^{-1} J_i, J_i = sum over the vertices A of T_i, over the cells c around A,
+// of (x_c - x_i)(u_c - u_i), plus each Dirichlet ghost point once per shared vertex. Per
+// vertex, with y_c = x_c - x_A and a reference value u0 (the first cell around A):
+//   S2 = sum (u_c - u0), S3 = sum y_c (u_c - u0)   (pass 1, over the vertex's star),
+//   S1 = sum y_c, n = #cells                       (geometry, uploaded),
+// and per cell, with y = x_i - x_A, delta = u_i - u0 (pass 2):
+//   J_i += S3 - delta S1 - y S2 + n y delta.
+// The offsets x_A and u0 keep every term of the size of the differences it stands for.
+__device__ __forceinline__ void vdiff(const double2& a, const double2& b, const double* xa, double* y) {
+  y[0] = a.y - xa[0]; y[1] = b.x - xa[1]; y[2] = b.y - xa[2];
+}
+__device__ __forceinline__ void vdiff(const float4& a, const float4& b, const float* xa, float* y) {
+  y[0] = (a.y - xa[0]) + (b.x - xa[3]); y[1] = (a.z - xa[1]) + (b.y - xa[4]); y[2] = (a.w - xa[2]) + (b.z - xa[5]);
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256)
+k_vgrad_vertex(int64_t V, const int64_t* __restrict__ sptr, const int32_t* __restrict__ sidx,
+               const int32_t* __restrict__ vcount, const T* __restrict__ rec, const T* __restrict__ xv,
+               const T* __restrict__ xv_lo, T* __restrict__ vsum) {
+  using Vec = typename GradVec<T>::type;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = v >> 5;
+    const int lane = (int)(v & 31);
+    const int32_t* col = sidx + sptr[sl] + lane;
+    const int n = vcount[v];
+    T xa[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      xa[a] = xv[a * V + v];
+      if (xv_lo) xa[3 + a] = xv_lo[a * V + v];
+    }
+    Vec a0, b0;
+    grad_load(rec, __ldg(col), a0, b0);
+    const T u0 = a0.x;
+    T s2 = T(0), s3[3] = {T(0), T(0), T(0)};
+    for (int k = 0; k < n; ++k) {
+      Vec a, b;
+      grad_load(rec, __ldg(col + 32 * k), a, b);
+      T y[3];
+      vdiff(a, b, xa, y);
+      const T du = a.x - u0;
+      s2 += du;
+#pragma unroll
+      for (int c = 0; c < D; ++c) s3[c] += y[c] * du;
+    }
+    vsum[v] = u0;
+    vsum[V + v] = s2;
+#pragma unroll
+    for (int c = 0; c < D; ++c) vsum[(2 + c) * V + v] = s3[c];
+  }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256)
+k_vgrad_cell(int64_t N, int64_t V, int64_t F, int64_t Fi, const int32_t* __restrict__ cverts,
+             const T* __restrict__ rec, const T* __restrict__ xv, const T* __restrict__ xv_lo,
+             const int32_t* __restrict__ vcount, const T* __restrict__ vs1, const T* __restrict__ vsum,
+             const T* __restrict__ minv, const int32_t* __restrict__ gptr,
+             const int32_t* __restrict__ gface, const int32_t* __restrict__ gmult,
+             const T* __restrict__ cen, const T* __restrict__ cen_lo, const T* __restrict__ xf,
+             const T* __restrict__ xf_lo, const T* __restrict__ bval, T* __restrict__ grad) {
+  using Vec = typename GradVec<T>::type;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    Vec ia, ib;
+    grad_load(rec, i, ia, ib);
+    const T ui = ia.x;
+    T J[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int k = 0; k <= D; ++k) {
+      const int32_t A = cverts[i * (D + 1) + k];
+      T xa[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        xa[a] = xv[a * V + A];
+        if (xv_lo) xa[3 + a] = xv_lo[a * V + A];
+      }
+      T y[3];
+      vdiff(ia, ib, xa, y);
+      const T n = (T)vcount[A];
+      const T delta = ui - vsum[A];
+      const T s2 = vsum[V + A];
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        J[a] += vsum[(2 + a) * V + A] - delta * vs1[a * V + A] - y[a] * s2 + n * y[a] * delta;
+    }
+    for (int32_t t = gptr[i]; t < gptr[i + 1]; ++t) {
+      const int32_t f = gface[t];
+      const T du = (T)gmult[t] * (bval[f - Fi] - ui);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const T dx = cdiff(xf + a * F, xf_lo ? xf_lo + a * F : nullptr, f, cen + a * N,
+                           cen_lo ? cen_lo + a * N : nullptr, i);
+        J[a] += dx * du;
+      }
+    }
+    if constexpr (D == 3) {
+      const T m0 = minv[i], m1 = minv[N + i], m2 = minv[2 * N + i], m3 = minv[3 * N + i],
+              m4 = minv[4 * N + i], m5 = minv[5 * N + i];
+      grad[i] = m0 * J[0] + m1 * J[1] + m2 * J[2];
+      grad[N + i] = m1 * J[0] + m3 * J[1] + m4 * J[2];
+      grad[2 * N + i] = m2 * J[0] + m4 * J[1] + m5 * J[2];
+    } else {
+      const T m0 = minv[i], m1 = minv[N + i], m2 = minv[2 * N + i];
+      grad[i] = m0 * J[0] + m1 * J[1];
+      grad[N + i] = m1 * J[0] + m2 * J[1];
+    }
+  }
+}
+
 // ---- Algorithm "ls": u_A = sum_c alpha_{A,c} u_c; Dirichlet vertices take g --------------
 template <typename T>
 __global__ void __launch_bounds__(1024)
@@ -568,6 +681,30 @@ cudaError_t launch_gradient(fvgb_mesh_s* m, int bcset, const T* u, T* grad, cuda
 }
 
 template <typename T>
+cudaError_t launch_gradient_vertex(fvgb_mesh_s* m, int bcset, const T* u, T* grad, cudaStream_t s) {
+  const TopoDev& t = m->topo;
+  GeoDev<T>& g = geo_of<T>(m);
+  const BCDev<T>& b = g.bc[bcset];
+  Work<T>& w = work_of<T>(m);
+  const unsigned gv = grid_for(t.V), gc = grid_for(t.N);
+  if (t.dim == 3) {
+    k_grad_pack<3><<<grid_for(t.N), kThreads, 0, s>>>(t.N, g.cen, g.cen_lo, u, w.grec);
+    k_vgrad_vertex<T, 3><<<gv, kThreads, 0, s>>>(t.V, t.vsell.ptr, t.vsell.idx, t.vcount, w.grec, g.xv,
+                                                 g.xv_lo, w.vsum);
+    k_vgrad_cell<T, 3><<<gc, kThreads, 0, s>>>(t.N, t.V, t.F, t.Fi, t.cverts, w.grec, g.xv, g.xv_lo, t.vcount,
+        g.vs1, w.vsum, b.minv_v, b.gptr, b.gface, b.gmult, g.cen, g.cen_lo, g.xf, g.xf_lo, b.bval, grad);
+  } else {
+    k_grad_pack<2><<<grid_for(t.N), kThreads, 0, s>>>(t.N, g.cen, g.cen_lo, u, w.grec);
+    k_vgrad_vertex<T, 2><<<gv, kThreads, 0, s>>>(t.V, t.vsell.ptr, t.vsell.idx, t.vcount, w.grec, g.xv,
+                                                 g.xv_lo, w.vsum);
+    k_vgrad_cell<T, 2><<<gc, kThreads, 0, s>>>(t.N, t.V, t.F, t.Fi, t.cverts, w.grec, g.xv, g.xv_lo, t.vcount,
+        g.vs1, w.vsum, b.minv_v, b.gptr, b.gface, b.gmult, g.cen, g.cen_lo, g.xf, g.xf_lo, b.bval, grad);
+  }
+  count_launch(3);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_vertex(fvgb_mesh_s* m, int bcset, const T* u, T* uv, bool homog, cudaStream_t s) {
   const TopoDev& t = m->topo;
   GeoDev<T>& g = geo_of<T>(m);
@@ -823,6 +960,7 @@ cudaError_t launch_nonfinite_check(const double* x, int64_t n, int* flag, cudaSt
 
 #define FVGB_INST(T)                                                                          \
   template cudaError_t launch_gradient<T>(fvgb_mesh_s*, int, const T*, T*, cudaStream_t);     \
+  template cudaError_t launch_gradient_vertex<T>(fvgb_mesh_s*, int, const T*, T*, cudaStream_t); \
   template cudaError_t launch_vertex<T>(fvgb_mesh_s*, int, const T*, T*, bool, cudaStream_t); \
   template cudaError_t launch_face<T>(fvgb_mesh_s*, int, const T*, const T*, const T*,        \
                                       const double*, bool, double, bool, T*, cudaStream_t,   \

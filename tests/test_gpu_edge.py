@@ -62,6 +62,9 @@ def test_single_cell_mesh(dev, which):
     capi.fvgb_vertex_values(dm.handle, 0, ud, uvd)
     torch.cuda.synchronize()
     assert rel(dm.to_host(gd).T, ls.ls_gradient(g, bc, u)) < TOL64
+    capi.fvgb_gradient_vertex(dm.handle, 0, ud, gd)
+    torch.cuda.synchronize()
+    assert rel(dm.to_host(gd).T, ls.ls_gradient_vertex(g, bc, u)) < TOL64
     assert rel(dm.vert_to_host(uvd), ls.vertex_values(g, bc, u)) < TOL64
     vel = np.array([0.3, -0.7, 0.2])[:d]
     res = dm.empty(1)

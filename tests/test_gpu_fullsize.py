@@ -77,6 +77,9 @@ def test_operators_750k(dev, w750):
     torch.cuda.synchronize()
     w = ls.vertex_weights(g)
     assert rel(dm.to_host(gd).T, ls.ls_gradient(g, bcs[1], u)) < TOL64
+    capi.fvgb_gradient_vertex(dm.handle, 1, ud, gd)
+    torch.cuda.synchronize()
+    assert rel(dm.to_host(gd).T, ls.ls_gradient_vertex(g, bcs[1], u)) < TOL64
     assert rel(dm.vert_to_host(uvd), ls.vertex_values(g, bcs[1], u, weights=w)) < TOL64
     coef = fv.diamond_coefficients(g)
     vel = rng.normal(size=(g.n_cell, 3))

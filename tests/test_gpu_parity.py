@@ -82,6 +82,26 @@ def test_gradient_and_vertex_values(dev, name, prec):
     dm.free()
 
 
+@pytest.mark.parametrize("name", ["square50", "cube7"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_gradient_vertex_factorised(dev, name, prec):
+    """The multiplicity-weighted (vertex-factorised) gradient against the oracle's plain
+    sum over cell pairs weighted by their shared vertices, with both boundary sets."""
+    capi, device = dev
+    m, bcs = meshes()[name]
+    g = geometry_of(m)
+    dm = device.DeviceMesh(m, bcs, prec=prec)
+    tol = TOL64 if prec == "fp64" else TOL32
+    u = smooth_field(g.cen, 9)
+    ud = dm.to_device(u)
+    for k, bc in enumerate(bcs):
+        gd = dm.empty(m.dim, dm.n_cell)
+        capi.fvgb_gradient_vertex(dm.handle, k, ud, gd)
+        torch.cuda.synchronize()
+        assert rel(dm.to_host(gd).T, ls.ls_gradient_vertex(g, bc, u)) < tol
+    dm.free()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_residual_all_boundary_kinds(dev, prec):
     capi, device = dev
