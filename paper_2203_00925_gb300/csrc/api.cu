@@ -668,7 +668,11 @@ static fvgb_status upload_impl(int32_t dim, int64_t n_vert, const double* xyz, i
   if ((e = dalloc(m, &m->dzero, h.N))) return fail(e, "allocation");
   if ((e = cudaMemsetAsync(m->dzero, 0, h.N * sizeof(double), s))) return fail(e, "memset");
   if ((e = dalloc(m, &m->barrier, 1))) return fail(e, "allocation");
+  // zeroed here: solves whose inner solve is not the CG (which resets it per launch) still
+  // read its status word
+  if ((e = cudaMemsetAsync(m->barrier, 0, sizeof(Barrier), s))) return fail(e, "memset");
   if ((e = dalloc(m, &m->d_cg_info, 4))) return fail(e, "allocation");
+  if ((e = cudaMemsetAsync(m->d_cg_info, 0, 4 * sizeof(int), s))) return fail(e, "memset");
   if ((e = cudaMallocHost((void**)&m->h_scal, (16 + 4 * kMaxParts) * sizeof(double)))) return fail(e, "pinned allocation");
   m->solve_grid = solve_grid_size(m);
   if (m->solve_grid <= 0) {

@@ -128,3 +128,29 @@ def test_streamer_zero_steps_and_one_cell_part(dev):
         assert rel(got[:1], poisson.solve(geometry_of(tet), phi_bc_tet, fs[0], dense=True)) < 1e-9
         assert poisson.relative_residual(gc, phi_bc_cube, fs[1], got[1:]) <= 1.01e-10
     ens.free()
+
+
+def test_multigrid_solves_on_reused_device_memory(dev):
+    """A mesh uploaded into device memory that held other data (0xFF bytes) solves with the
+    multigrid inner solve in host and graph mode: no state of the solver may depend on what
+    the allocation held before (the inner solve's status words are zeroed at upload)."""
+    capi, device = dev
+    junk = torch.full((512 * 1024 * 1024,), 255, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    del junk
+    torch.cuda.empty_cache()
+    m = jittered_cube(10, seed=41)
+    from synth.workloads import StreamerCase
+    case = StreamerCase(sigma=0.15, peak=1e13)
+    dm = device.DeviceMesh(m, [case.bc_ne(), case.bc_phi()], prec="mixed")
+    ne0 = case.initial(m)[0]
+    for graph in (False, True):
+        ne, ni = dm.to_device(ne0), dm.to_device(ne0 * 1.02)
+        phi = torch.zeros(dm.n_cell, dtype=torch.float64, device="cuda")
+        sp = capi.streamer_params(mu=case.mu, A=case.A, B=case.B, De=case.De, dt=2e-9,
+                                  solve=capi.solve_opts(rtol=1e-9, inner=2, prec=capi.FVGB_FP32))
+        capi.fvgb_set_graph_mode(dm.handle, graph)
+        infos = capi.fvgb_streamer_step(dm.handle, sp, ne, ni, phi, None, 2)
+        assert all(i["rel_res"] <= 1e-9 for i in infos)
+    capi.fvgb_set_graph_mode(dm.handle, False)
+    dm.free()
