@@ -38,6 +38,18 @@ WORKLOAD = ("3D electron drift-diffusion + Poisson, FP64 plain method: unit cube
             "the previous potential)")
 
 
+def workload_text(args):
+    text = WORKLOAD
+    if args.inner > 0:
+        text = text.replace("FP64 inner CG on the two-point operator reducing its residual 5x per outer step",
+                            f"{args.inner} multigrid V-cycles per outer step")
+    if args.prec == "mixed":
+        text = text.replace("FP64 plain method", "mixed precision (FP32 transport and inner solve, "
+                                                 "FP64 refinement), autotuned launch shapes")
+        text = text.replace("FP64 inner CG", "FP32 inner CG")
+    return text
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -52,6 +64,9 @@ def parse():
     ap.add_argument("--inner", type=int, default=0,
                     help="inner solve of the headline run: 0 conjugate gradients (default), "
                          "k > 0 k multigrid V-cycles per outer step")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"],
+                    help="precision of the headline run: fp64 (the plain method, default) or mixed "
+                         "(FP32 transport and inner CG, FP64 refinement to the same residual)")
     ap.add_argument("--transport-only", default=None, choices=["fp32", "fp64", "both"],
                     help="time only the transport kernels on the 6M-cell mesh (for profiling)")
     return ap.parse_args()
@@ -352,12 +367,16 @@ def gpu_arm(args, world, rank, local):
         return
     case = StreamerCase()
     mesh = streamer_mesh(K_MESH, MESH_SEED)
-    dm = device.DeviceMesh(mesh, [case.bc_ne(), case.bc_phi()], prec="fp64")
+    mixed = args.prec == "mixed"
+    dm = device.DeviceMesh(mesh, [case.bc_ne(), case.bc_phi()], prec=args.prec)
+    if mixed:
+        capi.fvgb_autotune(dm.handle)
     N = dm.n_cell
     ne0, ni0 = case.initial(mesh)
     dt = case.dt(1.0 / K_MESH)
     sp = capi.streamer_params(mu=case.mu, A=case.A, B=case.B, De=case.De, dt=dt,
-                              solve=capi.solve_opts(rtol=RTOL, inner_rtol=INNER_RTOL, prec=capi.FVGB_FP64,
+                              solve=capi.solve_opts(rtol=RTOL, inner_rtol=INNER_RTOL,
+                                                    prec=capi.FVGB_FP32 if mixed else capi.FVGB_FP64,
                                                     inner=args.inner))
     ne, ni = dm.to_device(ne0), dm.to_device(ni0)
     phi = torch.zeros(N, dtype=torch.float64, device="cuda")
@@ -397,11 +416,12 @@ def gpu_arm(args, world, rank, local):
         total_ms = float(t.item())
     value = world * N * args.steps / (total_ms / 1e3)
 
-    # ---- roofline of the dominant kernel: the persistent FP64 CG kernel ------------------
-    # GB300 runs FP64 at ~1/69 of the FP32 rate; ncu shows this kernel bound by the FP64
+    # ---- roofline of the dominant kernel: the persistent CG kernel ------------------------
+    # GB300 runs FP64 at ~1/69 of the FP32 rate; ncu shows the FP64 kernel bound by the FP64
     # pipe with its working set in L2, so it is reported against the FP64 ALU peak
-    # (nominal 1.25 TFLOP/s = SMs x 2 FP64 FMA/clk x 2 flop x max clock).
-    w = 8
+    # (nominal 1.25 TFLOP/s = SMs x 2 FP64 FMA/clk x 2 flop x max clock). The FP32 kernel of
+    # the mixed run is reported against the measured HBM copy bandwidth.
+    w = 4 if mixed else 8
     its, launches = stats["cg_iterations"], max(stats["cg_launches"], 1)
     per_launch_its = its / launches
     flops_per_launch = N * (per_launch_its * 21 + 13)
@@ -412,21 +432,28 @@ def gpu_arm(args, world, rank, local):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     hbm = float(peaks["hbm_gbs"])
     achieved = flops_per_launch / avg_launch_s / 1e12 if avg_launch_s > 0 else None
-    kname = "k_cg<double,4>"
+    achieved_gbs = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else None
+    kname = "k_cg<float,4>" if mixed else "k_cg<double,4>"
     prof = profile_traffic(kname, source_hash("solver.cu"))
     traffic = prof["dram_bytes_per_launch"] if prof else None
     if args.inner > 0:          # no CG launches: the CG roofline does not apply
-        achieved = None
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / peak_tflops if achieved else None,
-                "traffic": traffic,
-                "peak_source": "derived FP64 peak: SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
-                "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
-                "iterations_per_launch": per_launch_its,
-                "cg_share_of_step": stats["cg_ms"] / total_ms if world == 1 else None,
-                "hbm_view": {"algorithmic_bytes_per_launch": bytes_per_launch,
-                             "achieved_GBps": bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else None,
-                             "peak_GBps": hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}}
+        achieved = achieved_gbs = None
+    common = {"kernel": kname, "traffic": traffic, "flops_per_launch": flops_per_launch,
+              "avg_launch_ms": avg_launch_s * 1e3, "iterations_per_launch": per_launch_its,
+              "cg_share_of_step": stats["cg_ms"] / total_ms if world == 1 else None}
+    if mixed:
+        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved_gbs / hbm if achieved_gbs else None,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                    "algorithmic_bytes_per_launch": bytes_per_launch, **common}
+    else:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                    "frac": achieved / peak_tflops if achieved else None,
+                    "peak_source": "derived FP64 peak: SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
+                    **common,
+                    "hbm_view": {"algorithmic_bytes_per_launch": bytes_per_launch,
+                                 "achieved_GBps": achieved_gbs, "peak_GBps": hbm,
+                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}}
 
     # ---- variants on the same workload, same steps from the same initial state, all to the
     # same rtol: graph mode, mixed precision, learned warm start, and all three together;
@@ -536,19 +563,22 @@ def gpu_arm(args, world, rank, local):
     # ---- end to end through the public API with host buffers ------------------------------
     e2e = None
     if not args.no_e2e:
-        hne = torch.from_numpy(ne0.copy()).pin_memory()
-        hni = torch.from_numpy(ni0.copy()).pin_memory()
+        rt = dm.real
+        hne = torch.from_numpy(ne0.copy()).to(rt).pin_memory()
+        hni = torch.from_numpy(ni0.copy()).to(rt).pin_memory()
         hphi = torch.zeros(N, dtype=torch.float64).pin_memory()
-        u_ne, u_ni, u_phi = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(3))
-        i_ne, i_ni, i_phi = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(3))
+        u_ne, u_ni, i_ne, i_ni = (torch.empty(N, dtype=rt, device="cuda") for _ in range(4))
+        u_phi, i_phi = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(2))
+        triples = ((hne, u_ne, i_ne), (hni, u_ni, i_ni), (hphi, u_phi, i_phi))
+        io_bytes = sum(h.numel() * h.element_size() for h, _, _ in triples)
 
         def e2e_step():
-            for h, u, i in ((hne, u_ne, i_ne), (hni, u_ni, i_ni), (hphi, u_phi, i_phi)):
+            for h, u, i in triples:
                 u.copy_(h, non_blocking=True)
-                capi.fvgb_permute(dm.handle, u, i, 1, 8, True)
+                capi.fvgb_permute(dm.handle, u, i, 1, u.element_size(), True)
             capi.fvgb_streamer_step(dm.handle, sp, i_ne, i_ni, i_phi, None, 1)
-            for h, u, i in ((hne, u_ne, i_ne), (hni, u_ni, i_ni), (hphi, u_phi, i_phi)):
-                capi.fvgb_permute(dm.handle, i, u, 1, 8, False)
+            for h, u, i in triples:
+                capi.fvgb_permute(dm.handle, i, u, 1, u.element_size(), False)
                 h.copy_(u, non_blocking=True)
 
         for _ in range(args.warmup):
@@ -568,7 +598,7 @@ def gpu_arm(args, world, rank, local):
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             e2e_ms = float(t.item())
         e2e = {"value": world * N * args.steps / (e2e_ms / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": 3 * N * 8, "d2h_bytes_per_step": 3 * N * 8}
+               "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes}
 
     ensemble = None
     if world == 1 and not args.no_ensemble:
@@ -591,10 +621,8 @@ def gpu_arm(args, world, rank, local):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.inner == 0 else WORKLOAD.replace(
-                           "FP64 inner CG on the two-point operator reducing its residual 5x per outer step",
-                           f"{args.inner} multigrid V-cycles per outer step"),
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if mixed else "f64",
+            "data": "synthetic", "config": {"workload": workload_text(args),
                        "cells": N, "faces": dm.n_face,
                        "node_neighbour_entries": dm.n_nbr, "poisson_rtol": RTOL,
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
