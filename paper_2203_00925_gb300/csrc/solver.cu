@@ -30,25 +30,24 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Grid barrier by generation count with a bounded wait. Returns false when any block
-// gave up (status set), in which case the caller leaves.
-__device__ bool grid_barrier(Barrier* bar, unsigned nblocks) {
+// Grid barrier on a monotone arrival counter with a bounded wait: the r-th barrier of a
+// launch is passed once the counter (zeroed before the launch) reaches r * nblocks, so
+// the last arrival itself releases the waiting blocks (no reset, no second word).
+// ``target`` is the caller's running count. Returns false when any block gave up
+// (status set), in which case the caller leaves.
+__device__ bool grid_barrier(Barrier* bar, unsigned nblocks, unsigned& target) {
   __shared__ int ok;
   __syncthreads();
+  target += nblocks;
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = &bar->gen;
+    volatile unsigned* vcount = &bar->count;
     volatile int* vstatus = &bar->status;
-    const unsigned g = *vgen;
     __threadfence();
-    const unsigned arrived = atomicAdd(&bar->count, 1u);
+    atomicAdd(&bar->count, 1u);
     int good = 1;
-    if (arrived == nblocks - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
+    if ((int)(*vcount - target) < 0) {
       const unsigned long long t0 = global_ns();
-      while (*vgen == g) {
+      while ((int)(*vcount - target) < 0) {
         if (*vstatus != 0) { good = 0; break; }
         if (global_ns() - t0 > kBarrierTimeoutNs) { atomicExch(&bar->status, 1); good = 0; break; }
         __nanosleep(32);
@@ -62,19 +61,29 @@ __device__ bool grid_barrier(Barrier* bar, unsigned nblocks) {
   return ok != 0;
 }
 
-// Block-wide FP64 sum in a fixed order: a shuffle tree inside each warp, then warp 0
-// sums the warp totals in warp order. Two block barriers. The result is valid in thread 0.
+// Block-wide FP64 sum in a fixed order, valid in thread 0. Every thread's value goes to
+// shared memory; four warps (one per SM sub-partition) each add a quarter of them, lane
+// by lane in index order and then by a shuffle tree, and thread 0 adds the four results.
+// GB300 issues FP64 adds at a small fraction of the FP32 rate, so the sum keeps the FP64
+// instructions on its critical path few and spread over the four sub-partitions.
+// sh holds blockDim.x doubles (blockDim.x a multiple of 128).
 __device__ __forceinline__ double block_sum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();                      // the previous call's readers are done with sh
-  if (l == 0) sh[w] = v;
+  sh[threadIdx.x] = v;
   __syncthreads();
   double t = 0.0;
-  if (threadIdx.x < 32) {
-    t = l < (int)(blockDim.x >> 5) ? sh[l] : 0.0;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int quarter = blockDim.x >> 2;
+  if (w < 4) {
+    const double* q = sh + w * quarter;
+    t = q[l];
+    for (int j = l + 32; j < quarter; j += 32) t += q[j];
     for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
   }
+  __syncthreads();                      // every quarter read before the results overwrite sh
+  if (w < 4 && l == 0) sh[w] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) t = (sh[0] + sh[1]) + (sh[2] + sh[3]);
   return t;
 }
 
@@ -159,11 +168,14 @@ struct Coef4<double> {
 // gathers of several rows are in flight together.
 template <typename T>
 __host__ __device__ constexpr int unroll_rows() { return sizeof(T) == 4 ? 4 : 2; }
+// the x/r phase holds four values a row: more rows per trip
+template <typename T>
+__host__ __device__ constexpr int unroll_rows_xr() { return sizeof(T) == 4 ? 8 : 4; }
 
 // CG phase 1 on rows [lo, hi): x += alpha p, r -= alpha q; returns the thread's sum of r^2.
 template <typename T>
 __device__ __forceinline__ T cg_phase_xr(const SolveArgs<T>& a, int64_t lo, int64_t hi, T alpha) {
-  constexpr int U = unroll_rows<T>();
+  constexpr int U = unroll_rows_xr<T>();
   T* __restrict__ X = a.cx;
   T* __restrict__ R = a.cr;
   const T* __restrict__ P = a.cp;
@@ -250,7 +262,7 @@ __device__ __forceinline__ T cg_phase_pq(const SolveArgs<T>& a, int64_t lo, int6
 // grid-barrier arrivals and partial sums, more rows in flight per thread).
 template <typename T>
 __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> a) {
-  __shared__ double sh[32];
+  __shared__ double sh[kCgThreads];
   __shared__ double stage[2][kCgThreads];
   __shared__ double tot[2 * kMaxParts];
   __shared__ double s_rr[kMaxParts], s_rr0[kMaxParts];
@@ -263,6 +275,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
   const int sc0 = a.blk_sc[blockIdx.x], sc1 = a.blk_sc[blockIdx.x + 1];
   int parity = 0;
   int total_its = 0;
+  unsigned target = 0;
   if (threadIdx.x == 0) s_status = 0;
   for (int p = threadIdx.x; p < P; p += blockDim.x) s_inner[p] = 0;
 
@@ -277,7 +290,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
       a.cx[i] = T(0);
     }
   }
-  if (!grid_barrier(a.bar, G)) goto done;
+  if (!grid_barrier(a.bar, G, target)) goto done;
   for (int sc = sc0; sc < sc1; ++sc) {
     const int p = a.sc_part[sc];
     T l0 = T(0), l1 = T(0);
@@ -292,7 +305,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
     const double t1 = block_sum((double)l1, sh);
     if (threadIdx.x == 0) { a.buf[sc] = t0; a.buf[a.n_sc + sc] = t1; }
   }
-  if (!grid_barrier(a.bar, G)) goto done;
+  if (!grid_barrier(a.bar, G, target)) goto done;
   part_totals<T, 2>(a, a.buf, tot, stage);
   if (threadIdx.x == 0) s_flag = 0;
   __syncthreads();
@@ -319,7 +332,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
       const double t = block_sum((double)l, sh);
       if (threadIdx.x == 0) buf[sc] = t;
     }
-    if (!grid_barrier(a.bar, G)) goto done;
+    if (!grid_barrier(a.bar, G, target)) goto done;
     part_totals<T, 1>(a, buf, tot, stage);
     ++total_its;
     if (threadIdx.x == 0) s_flag = 0;
@@ -345,7 +358,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
       const double t = block_sum((double)l, sh);
       if (threadIdx.x == 0) buf[sc] = t;
     }
-    if (!grid_barrier(a.bar, G)) goto done;
+    if (!grid_barrier(a.bar, G, target)) goto done;
     part_totals<T, 1>(a, buf, tot, stage);
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
       if (s_cg[p] != 0) continue;
@@ -373,7 +386,7 @@ done:
 // sub-chunks in order.
 __global__ void __launch_bounds__(kCgThreads) k_part_sumsq_partial(const double* __restrict__ v,
     const int32_t* __restrict__ blk_sc, const int64_t* __restrict__ sc_begin, double* __restrict__ buf) {
-  __shared__ double sh[32];
+  __shared__ double sh[kCgThreads];
   for (int sc = blk_sc[blockIdx.x]; sc < blk_sc[blockIdx.x + 1]; ++sc) {
     double l = 0.0;
     for (int64_t i = sc_begin[sc] + threadIdx.x; i < sc_begin[sc + 1]; i += blockDim.x) l += v[i] * v[i];
