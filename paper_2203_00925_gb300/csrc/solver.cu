@@ -117,8 +117,13 @@ struct SolveArgs {
 
 // Sum the per-sub-chunk partials of K quantities into per-part totals (shared memory
 // tot[k * P + p]), every part in sub-chunk order. Call after a grid barrier. The partials
-// are first staged in shared memory with one load per thread (one L2 round trip), then
-// each part is summed by one warp: lanes stride 32 over its sub-chunks, then a shuffle tree.
+// are first staged in shared memory with one load per thread (one L2 round trip). A part
+// of at most kSeqSubChunks sub-chunks is summed by one thread, left to right; a longer
+// one by one warp: lanes stride 32 over its sub-chunks, then a shuffle tree. (A warp-wide
+// FP64 add costs the same whatever its active lanes, so the few adds of the short parts
+// of an ensemble are cheaper in one thread than in a five-level shuffle tree.)
+constexpr int kSeqSubChunks = 8;
+
 template <typename T, int K>
 __device__ void part_totals(const SolveArgs<T>& a, const double* buf, double* tot,
                             double (*stage)[kCgThreads]) {
@@ -130,7 +135,18 @@ __device__ void part_totals(const SolveArgs<T>& a, const double* buf, double* to
       if ((int)threadIdx.x < a.n_sc) stage[k][threadIdx.x] = __ldcg(buf + (size_t)k * a.n_sc + threadIdx.x);
     __syncthreads();
   }
+  for (int p = threadIdx.x; p < a.n_part; p += blockDim.x) {
+    const int s0 = a.part_sc[p], s1 = a.part_sc[p + 1];
+    if (s1 - s0 > kSeqSubChunks) continue;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double t = 0.0;
+      for (int sc = s0; sc < s1; ++sc) t += staged ? stage[k][sc] : __ldcg(buf + (size_t)k * a.n_sc + sc);
+      tot[k * a.n_part + p] = t;
+    }
+  }
   for (int p = warp; p < a.n_part; p += nw) {
+    if (a.part_sc[p + 1] - a.part_sc[p] <= kSeqSubChunks) continue;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       double t = 0.0;
