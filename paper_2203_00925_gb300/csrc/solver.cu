@@ -344,10 +344,12 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
     double* buf = a.buf + (size_t)parity * 2 * a.n_sc;
     for (int sc = sc0; sc < sc1; ++sc) {
       const int p = a.sc_part[sc];
-      T l = T(0);
-      if (s_cg[p] == 0) l = cg_phase_xr<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], s_alpha[p]);
-      const double t = block_sum((double)l, sh);
-      if (threadIdx.x == 0) buf[sc] = t;
+      if (s_cg[p] == 0) {             // uniform in the block
+        const double t = block_sum((double)cg_phase_xr<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], s_alpha[p]), sh);
+        if (threadIdx.x == 0) buf[sc] = t;
+      } else if (threadIdx.x == 0) {
+        buf[sc] = 0.0;
+      }
     }
     if (!grid_barrier(a.bar, G, target)) goto done;
     part_totals<T, 1>(a, buf, tot, stage);
@@ -370,10 +372,12 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
     buf = a.buf + (size_t)parity * 2 * a.n_sc;
     for (int sc = sc0; sc < sc1; ++sc) {
       const int p = a.sc_part[sc];
-      T l = T(0);
-      if (s_cg[p] == 0) l = cg_phase_pq<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], s_beta[p]);
-      const double t = block_sum((double)l, sh);
-      if (threadIdx.x == 0) buf[sc] = t;
+      if (s_cg[p] == 0) {             // uniform in the block
+        const double t = block_sum((double)cg_phase_pq<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], s_beta[p]), sh);
+        if (threadIdx.x == 0) buf[sc] = t;
+      } else if (threadIdx.x == 0) {
+        buf[sc] = 0.0;
+      }
     }
     if (!grid_barrier(a.bar, G, target)) goto done;
     part_totals<T, 1>(a, buf, tot, stage);
