@@ -102,10 +102,9 @@ struct PartsDev {
 };
 
 struct Barrier {
-  unsigned int count;
-  unsigned int gen;
-  int status;      // 0 ok, 1 timeout
-  int pad;
+  unsigned int count;  // arrivals since the launch (zeroed before every launch)
+  int status;          // 0 ok, 1 timeout
+  int pad[2];
 };
 
 struct GraphState;
