@@ -497,7 +497,7 @@ def gpu_arm(args, world, rank, local):
         del pairs_p, pairs_x
         train_s = time.time() - t_train0
 
-        def run_variant(prec, graph, warm, extrap=False, inner=0):
+        def run_variant(prec, graph, warm, extrap=False, inner=0, recon=0, stages=1):
             dmv = device.DeviceMesh(mesh, [case.bc_ne(), case.bc_phi()], prec=prec)
             if prec != "fp64":
                 capi.fvgb_autotune(dmv.handle)
@@ -509,6 +509,7 @@ def gpu_arm(args, world, rank, local):
                 capi.fvgb_mpnn_set_scales(net, case.V, *scales)
             spv = capi.streamer_params(
                 mu=case.mu, A=case.A, B=case.B, De=case.De, dt=dt, warm=net, extrapolate=extrap,
+                recon=recon, stages=stages,
                 solve=capi.solve_opts(rtol=RTOL, inner_rtol=INNER_RTOL, inner=inner,
                                       prec=capi.FVGB_FP64 if prec == "fp64" else capi.FVGB_FP32))
             nev, niv = dmv.to_device(ne0), dmv.to_device(ni0)
@@ -543,7 +544,9 @@ def gpu_arm(args, world, rank, local):
                      "2 phi^{n-1} - phi^{n-2}; 'learned': the network's correction of the start (from "
                      "the previous potential, or of the extrapolation), kept per part only where it "
                      "lowers the FP64 residual; 'multigrid': 2 smoothed-aggregation V-cycles per "
-                     "outer step instead of the inner CG; networks trained on this mesh from plain runs of "
+                     "outer step instead of the inner CG; 'muscl': MUSCL reconstruction with the "
+                     "Barth-Jespersen limiter; 'rk3': three Runge-Kutta stages, a Poisson solve each; "
+                     "networks trained on this mesh from plain runs of "
                      f"{TRAIN_SEEDS} other seed positions x {TRAIN_STEPS} steps ({n_pairs[0]} / "
                      f"{n_pairs[1]} pairs, {TRAIN_EPOCHS} epochs of Adam, {train_s:.1f} s)"),
             "plain_fp64_inner_cg_its_per_step": plain_inner,
@@ -558,6 +561,10 @@ def gpu_arm(args, world, rank, local):
             "multigrid_fp64": run_variant("fp64", False, False, False, 2),
             "multigrid_mixed_graph": run_variant("mixed", True, False, False, 2),
             "multigrid_extrapolated_mixed_graph": run_variant("mixed", True, False, True, 2),
+            # other discretisations of the same step (their differences from the plain run are
+            # those of the scheme, not of the solver)
+            "muscl_multigrid_extrapolated_mixed_graph": run_variant("mixed", True, False, True, 2, recon=1),
+            "rk3_multigrid_extrapolated_mixed": run_variant("mixed", False, False, True, 2, stages=3),
         }
 
     # ---- end to end through the public API with host buffers ------------------------------
