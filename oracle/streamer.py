@@ -21,6 +21,16 @@ replace them with (SI units, lengths in metres):
   n^(j) = n^k + alpha_j dt Res(n^(j-1)), alpha = (1/2, 1/2, 1), n^{k+1} = n^(3).
 
 The ion density is written n_i here (the paper's n_p).
+
+Plasma spots (Section 4, "Streamer Branching"): Gaussian sources of electron-ion pairs,
+S_k(x) = S_0 exp(-|x - c_k|^2 / sigma^2), switched on at t_on for a given duration. The
+paper prints the exponent without its minus sign; the reading is the decaying Gaussian
+(the printed form grows without bound away from the spot). A spot adds to S_e, so it
+enters both the n_e and the n_i equations of eq. 10 (the spot is quasi-neutral and the
+charge balance is unchanged). Within a time step [t, t + dt] the spot contributes its
+average over the step, S_k(x) |[t, t + dt] n [t_on, t_on + duration]| / dt, so that steps
+of any length deposit the spot's exact total S_k(x) * duration; the three stages of eq. 6
+all use that step average.
 """
 from __future__ import annotations
 
@@ -37,6 +47,30 @@ class Params:
                  centre=(0.5, 0.5, 0.9), sigma=0.01, peak=1e16, background=1e9):
         self.V, self.mu, self.A, self.B, self.De = V, mu, A, B, De
         self.centre, self.sigma, self.peak, self.background = centre, sigma, peak, background
+
+
+class Spot:
+    """One plasma spot: source S_0 exp(-|x - centre|^2 / sigma^2) for t in
+    [t_on, t_on + duration). The defaults are the paper's values (amplitude 1e25, width
+    0.005, on at 1.26e-8 s for 0.5e-9 s)."""
+
+    def __init__(self, centre, amplitude=1e25, sigma=0.005, t_on=1.26e-8, duration=0.5e-9):
+        self.centre = np.asarray(centre, dtype=np.float64)
+        self.amplitude, self.sigma = float(amplitude), float(sigma)
+        self.t_on, self.duration = float(t_on), float(duration)
+
+
+def spot_source(geo, spots, t, dt):
+    """Per-cell source of the plasma spots averaged over the step [t, t + dt]."""
+    S = np.zeros(geo.n_cell)
+    for sp in spots:
+        lo = max(t, sp.t_on)
+        hi = min(t + dt, sp.t_on + sp.duration)
+        if hi <= lo:
+            continue
+        r2 = ((geo.cen - sp.centre) ** 2).sum(axis=1)
+        S += sp.amplitude * np.exp(-r2 / sp.sigma ** 2) * ((hi - lo) / dt)
+    return S
 
 
 def bc_phi(p):
@@ -63,19 +97,23 @@ def cell_physics(p, E, ne):
     return v, S
 
 
-def step(geo, p, ne, ni, dt, phi=None, dense=False, recon=0, alphas=(1.0,)):
-    """One step of eq. 10; returns (ne, ni, phi, E, S) of the last stage. alphas = (1,) is
-    explicit Euler, (0.5, 0.5, 1) the three stages of eq. 6 (Poisson solved per stage). A
-    given phi replaces the first stage's solve. recon = 1 takes the convective face values
-    of n_e from the MUSCL reconstruction (eq. 15)."""
+def step(geo, p, ne, ni, dt, phi=None, dense=False, recon=0, alphas=(1.0,), spots=(), t=0.0):
+    """One step of eq. 10 from time t; returns (ne, ni, phi, E, S) of the last stage.
+    alphas = (1,) is explicit Euler, (0.5, 0.5, 1) the three stages of eq. 6 (Poisson solved
+    per stage). A given phi replaces the first stage's solve. recon = 1 takes the
+    convective face values of n_e from the MUSCL reconstruction (eq. 15). spots: plasma
+    spots added to the source S (see ``spot_source``)."""
     bphi = bc_phi(p)
     ne0, ni0 = np.asarray(ne, dtype=np.float64), np.asarray(ni, dtype=np.float64)
     ne_k, ni_k = ne0, ni0
+    S_spot = spot_source(geo, spots, t, dt) if spots else None
     for j, a in enumerate(alphas):
         if j > 0 or phi is None:
             phi = poisson.solve(geo, bphi, poisson_source(ne_k, ni_k), dense=dense)
         E = -ls.ls_gradient(geo, bphi, phi)
         v, S = cell_physics(p, E, ne_k)
+        if S_spot is not None:
+            S = S + S_spot
         R = fv.residual(geo, bc_ne(), ne_k, v, p.De, src=S, recon=recon)
         ne_k, ni_k = ne0 + a * dt * R, ni0 + a * dt * S
     return ne_k, ni_k, phi, E, S

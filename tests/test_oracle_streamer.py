@@ -77,3 +77,56 @@ def test_three_stage_charge_balance():
     # the stages differ from one Euler step
     ne_e, _, _, _, _ = streamer.step(g, p, ne, ni, dt)
     assert np.abs(ne_e - ne3).max() > 1e-6 * np.abs(ne3 - ne).max()
+
+
+# ---- plasma spots (Section 4, "Streamer Branching") -------------------------------------
+
+def test_spot_gaussian_matches_its_closed_form_integral():
+    """Summed over the cells, mu_i exp(-|x_i - c|^2 / sigma^2) is the Gaussian's integral
+    pi^(3/2) sigma^3 (resolved spot well inside the cube); exp(-r^2 / (2 sigma^2)) or a
+    positive exponent would be far off."""
+    g = geometry_of(jittered_cube(16, seed=203))
+    sp = streamer.Spot((0.5, 0.5, 0.5), amplitude=3.0, sigma=0.15, t_on=0.0, duration=1.0)
+    S = streamer.spot_source(g, [sp], 0.25, 0.5)
+    total = fv.mass(g, S)
+    assert abs(total / (3.0 * np.pi ** 1.5 * 0.15 ** 3) - 1.0) < 2e-3
+
+
+def test_spot_window_deposits_its_exact_total():
+    """Without ionisation (A = 0) the ion total grows only by the spots: after a run of
+    unevenly long steps that covers both windows, by exactly sum_k S_k duration_k
+    sum_i mu_i g_k(x_i) (to round-off), and steps outside the windows add nothing."""
+    g, p, ne = _setup(5)
+    p.A = 0.0
+    spots = [streamer.Spot((0.55, 0.5, 0.8), amplitude=2e20, sigma=0.2, t_on=3e-10, duration=4e-10),
+             streamer.Spot((0.45, 0.5, 0.78), amplitude=1e20, sigma=0.25, t_on=5e-10, duration=1e-10)]
+    ni = ne.copy()
+    ni0 = ni.copy()
+    t = 0.0
+    dts = [1e-10, 2.5e-10, 0.7e-10, 3e-10, 1.3e-10, 2e-10]
+    phi = None
+    for dt in dts:
+        before = ni.copy()
+        ne, ni, phi, E, S = streamer.step(g, p, ne, ni, dt, spots=spots, t=t)
+        if t + dt <= 3e-10 or t >= 8e-10:
+            assert np.array_equal(ni, before)
+        t += dt
+    assert t > 8e-10
+    want = sum(s.amplitude * s.duration * fv.mass(g, np.exp(-((g.cen - s.centre) ** 2).sum(1) / s.sigma ** 2))
+               for s in spots)
+    got = fv.mass(g, ni) - fv.mass(g, ni0)
+    assert abs(got - want) <= 1e-12 * want
+
+
+def test_spot_keeps_charge_balance():
+    """The spot adds electron-ion pairs: n_i - n_e still changes by exactly dt times the
+    n_e outflow through the boundary."""
+    g, p, ne = _setup()
+    ni = ne * 1.01
+    dt = 1e-9
+    sp = streamer.Spot((0.5, 0.5, 0.7), amplitude=1e22, sigma=0.1, t_on=0.0, duration=1.0)
+    ne1, ni1, phi, E, S = streamer.step(g, p, ne, ni, dt, spots=[sp], t=0.0)
+    dq = fv.mass(g, ni1 - ne1) - fv.mass(g, ni - ne)
+    want = dt * streamer.boundary_outflow(g, p, ne, -p.mu * E)
+    assert abs(dq - want) <= 1e-12 * fv.mass(g, ne1)
+    assert fv.mass(g, ni1) - fv.mass(g, ni) > 0.5 * dt * 1e22 * np.pi ** 1.5 * 0.1 ** 3
