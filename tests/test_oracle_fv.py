@@ -142,3 +142,65 @@ def test_gaussian_advection_diffusion_converges():
     orders = np.log2(np.array(e[:-1]) / np.array(e[1:]))
     assert orders.min() > 0.6, (e, orders)
     assert e[2] < 0.15
+
+
+def _two_triangles():
+    """Unit square cut along its diagonal (0,0)-(1,1): cell 0 = (0,0),(1,0),(1,1) with
+    centre (2/3, 1/3), cell 1 = (0,0),(1,1),(0,1) with centre (1/3, 2/3); both have area
+    1/2. The interior face has S = (-1, 1) (length sqrt 2, pointing from cell 0 to cell 1);
+    the boundary edges have outward area vectors (0,-1) and (1,0) for cell 0, (-1,0) and
+    (0,1) for cell 1."""
+    from synth.meshgen import Mesh
+    xyz = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 1.0]])
+    cells = np.array([[0, 1, 3], [0, 3, 2]])
+    bf = np.array([[0, 1], [1, 3], [3, 2], [2, 0]])
+    tags = np.array([3, 2, 4, 1])
+    return geometry_of(Mesh(2, xyz, cells, bf, tags, 1.0))
+
+
+NEU_2D = {t: ("neumann", 0.0) for t in range(1, 5)}
+
+
+def test_face_velocity_mean_of_cells_hand_checked():
+    """V_f of eq. 4 for a cell-centred velocity (reading R8): the mean of the two cells'
+    velocities on interior faces, the interior cell's own velocity on boundary faces.
+    The residual is checked against values worked out by hand, so that V_f = V_L,
+    V_f = the upwind cell's velocity, or a zero ghost velocity all fail."""
+    g = _two_triangles()
+    inner = np.nonzero(g.face_R >= 0)[0]
+    assert inner.size == 1
+    f = inner[0]
+    assert (g.face_L[f], g.face_R[f]) == (0, 1)
+    assert np.allclose(g.S[f], [-1.0, 1.0])
+    vel = np.array([[3.0, 0.0], [0.0, 1.0]])
+    Vf = fv.face_velocity(g, vel)
+    assert np.allclose(Vf[f], [1.5, 0.5])
+    bnd = g.face_R < 0
+    assert np.array_equal(Vf[bnd], vel[g.face_L[bnd]])
+    # V_f . S = -1 on the interior face: upwind is cell 1 and F = -u_1; cell 0's boundary
+    # fluxes are 0 (y = 0) and 3 u_0 (x = 1); cell 1's are 0 (x = 0) and u_1 (y = 1).
+    # R_0 = (-F_int - 3 u_0) / (1/2) = 2 u_1 - 6 u_0, R_1 = (F_int - u_1) / (1/2) = -4 u_1.
+    u = np.array([2.0, 5.0])
+    r = fv.residual(g, NEU_2D, u, vel, 0.0)
+    assert np.allclose(r, [2 * 5.0 - 6 * 2.0, -4 * 5.0], rtol=0, atol=1e-13)
+    # the misreadings give other numbers: V_f = V_L makes F_int = -3 u_1 (R_0 = 18), V_f =
+    # V_upwind (cell 1: V . S = +1, upwind then L) makes F_int = u_0 (R_0 = -16), a zero
+    # ghost velocity halves the boundary outflow 3 u_0 (R_0 = 4)
+    assert not np.isclose(r[0], 18.0) and not np.isclose(r[0], -16.0) and not np.isclose(r[0], 4.0)
+
+
+def test_face_velocity_tie_takes_left_and_carries_no_flux():
+    """With (V_L + V_R) . S = 0 the interior face carries no convective flux (the tie
+    V_f . S >= 0 takes u_L, times zero); V_f = V_L would give -u_1 there instead."""
+    g = _two_triangles()
+    f = np.nonzero(g.face_R >= 0)[0][0]
+    vel = np.array([[1.0, 0.0], [1.0, 2.0]])
+    Vf = fv.face_velocity(g, vel)
+    assert np.dot(Vf[f], g.S[f]) == 0.0
+    u = np.array([2.0, 5.0])
+    F = fv.face_flux(g, NEU_2D, u, vel, 0.0)
+    assert F[f] == 0.0
+    # boundary: cell 0 (V = (1, 0)) has outflow 1 * u_0 at x = 1; cell 1 (V = (1, 2)) has
+    # -1 * u_1 at x = 0 and 2 * u_1 at y = 1
+    r = fv.residual(g, NEU_2D, u, vel, 0.0)
+    assert np.allclose(r, [-2.0 * 2.0, -2.0 * (2.0 * 5.0 - 5.0)], rtol=0, atol=1e-13)
