@@ -24,20 +24,62 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
+struct ScratchSlot {
+  unsigned long long ctx_id = 0;   // unique id of the context the address belongs to
+  void* addr = nullptr;
+};
+ScratchSlot g_scratch[kMaxDevices];
 
-// Device address of the scratch array on the current device, looked up once per device
-// (with that device current) and cached.
+// Driver entry points for the current context and its process-unique id, fetched through
+// the runtime (no link-time dependency on the driver library). A context id is never
+// reused, so a context that was destroyed (cudaDeviceReset) and re-created gets a new id.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+bool g_entry_looked_up = false;
+
+// id of the current context, 0 when it cannot be determined
+unsigned long long current_ctx_id() {
+  if (!g_entry_looked_up) {
+    g_entry_looked_up = true;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      g_ctx_current = (CtxGetCurrentFn)f1;
+      g_ctx_id = (CtxGetIdFn)f2;
+    }
+  }
+  if (!g_ctx_current || !g_ctx_id) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_current(&ctx) != 0 || !ctx || g_ctx_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of the scratch array in the current context. Set-up happens once per
+// device and context: the address is looked up with cudaGetSymbolAddress (with the
+// device current) and cached together with the context's id; a later call in another
+// context of the same device (after cudaDeviceReset) looks it up again. When the context
+// id cannot be read, the address is looked up on every call (a host-side table lookup
+// that allocates nothing).
 cudaError_t scratch_address(int dev, void** out) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
+  const unsigned long long id = current_ctx_id();
+  ScratchSlot& slot = g_scratch[dev];
+  if (id == 0 || slot.ctx_id != id || !slot.addr) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
+    // the lookup itself creates the context if there was none: read the id again
+    slot.ctx_id = id != 0 ? id : current_ctx_id();
+    slot.addr = p;
   }
-  *out = g_scratch_addr[dev];
+  *out = slot.addr;
   return cudaSuccess;
 }
 
@@ -87,7 +129,8 @@ extern "C" fvgb_status fvgb_fv_residual_noalloc(fvgb_mesh m, const fvgb_tcoef* t
                                                 const void* u, void* res, void* stream) {
   if (!m) { set_error("null mesh handle"); return FVGB_EINVAL; }
   if (!tc) { set_error("tcoef is null"); return FVGB_EINVAL; }
-  if (tc->recon != 0) { set_error("the allocation-free residual is first-order upwind only (recon = 0)"); return FVGB_EUNSUPPORTED; }
+  if (tc->recon != 0 && tc->recon != 1) { set_error("recon must be 0 (upwind) or 1 (MUSCL + Barth-Jespersen)"); return FVGB_EINVAL; }
+  if (tc->recon == 1) { set_error("the allocation-free residual is first-order upwind only (recon = 0)"); return FVGB_EUNSUPPORTED; }
   if (!(tc->diff >= 0.0)) { set_error("diffusivity must be >= 0"); return FVGB_EINVAL; }
   if (tc->bcset < 0 || tc->bcset >= (int32_t)m->g64.bc.size()) { set_error("bcset index out of range"); return FVGB_EINVAL; }
   if (!u || !res || u == res) { set_error("u and res must be distinct device arrays"); return FVGB_EINVAL; }
