@@ -69,16 +69,27 @@ def test_gradient_and_vertex_values(dev, name, prec):
         want = ls.ls_gradient(g, bc, u)
         assert rel(dm.to_host(gd).T, want) < tol
         assert rel(dm.vert_to_host(uvd), ls.vertex_values(g, bc, u)) < tol
-    # linear fields: exact gradient on every cell (FP64)
+    # linear fields: exact gradient on every cell (FP64). Wall and Neumann faces add no
+    # least-squares point, so any linear field is exact with them; a Dirichlet set is exact
+    # for the linear field that takes its boundary values (here: linear in z between the
+    # plates z = 0 and z = 1, whose points only slide tangentially)
     if prec == "fp64":
         b = np.arange(1, m.dim + 1) * 0.7
-        ud = dm.to_device(0.5 + g.cen @ b)
         gd = dm.empty(m.dim, dm.n_cell)
-        neu = 1 if name == "cube7" else 0
-        capi.fvgb_gradient(dm.handle, 0 if name == "square50" else neu, ud, gd)
-        torch.cuda.synchronize()
         if name == "square50":
+            capi.fvgb_gradient(dm.handle, 0, dm.to_device(0.5 + g.cen @ b), gd)
+            torch.cuda.synchronize()
             assert np.abs(dm.to_host(gd).T - b).max() < 1e-11
+        else:
+            capi.fvgb_gradient(dm.handle, 1, dm.to_device(100.0 * g.cen[:, 2]), gd)
+            torch.cuda.synchronize()
+            assert np.abs(dm.to_host(gd).T - [0.0, 0.0, 100.0]).max() < 1e-10
+            dn = device.DeviceMesh(m, [{t: ("neumann", 0.0) for t in range(1, 7)}], prec="fp64")
+            gn = dn.empty(m.dim, dn.n_cell)
+            capi.fvgb_gradient(dn.handle, 0, dn.to_device(0.5 + g.cen @ b), gn)
+            torch.cuda.synchronize()
+            assert np.abs(dn.to_host(gn).T - b).max() < 1e-11
+            dn.free()
     dm.free()
 
 
