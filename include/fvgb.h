@@ -27,6 +27,15 @@
  *   that it synchronises the stream.
  * - A mesh handle is not thread-safe: use one handle from one host thread and one
  *   stream at a time.
+ * - Asynchronous errors: a transport update (fvgb_fv_residual, fvgb_fv_step, the
+ *   transport of fvgb_streamer_step) that writes a non-finite value sets a status word on
+ *   the device instead of failing at once; the word stays set until it is reported by
+ *   fvgb_sync, by the next fvgb_poisson_solve (or the solve of the next streamer step), or
+ *   at the end of a graph-mode fvgb_streamer_step call, each of which returns
+ *   FVGB_ENONFINITE and clears it. Grid-wide waits inside the persistent CG kernel are
+ *   bounded (1 s) and give FVGB_ETIMEOUT instead of hanging; a wait of the network's
+ *   tensor-core kernels for its matrix products (also bounded, 1 s) latches a timeout
+ *   in the same status word, reported as FVGB_ETIMEOUT.
  * - Sizes are int64_t; element indices inside the library are int32 (meshes up to
  *   2^31 - 1 cells, faces and neighbour entries).
  */
@@ -212,7 +221,8 @@ fvgb_status fvgb_fv_residual(fvgb_mesh m, const fvgb_tcoef* tc, const void* u_de
  * cudaMalloc there can fail or fragment the pool) or a time-critical loop in which
  * cudaMalloc / cudaFree would add latency and implicit synchronisation. Arguments,
  * results and errors are those of fvgb_fv_residual, except that only first-order upwind
- * is offered (recon != 0 gives FVGB_EUNSUPPORTED).
+ * is offered (recon = 1 gives FVGB_EUNSUPPORTED; values other than 0 and 1 give
+ * FVGB_EINVAL, as in fvgb_fv_residual).
  *  - Scratch (the face fluxes and vertex values) lives in one fixed 8 MiB device array
  *    owned by the library, which every GPU that loads the library holds until the
  *    process exits. A mesh needs n_face + n_vert reals of it (rounded up to 256 bytes
@@ -220,8 +230,11 @@ fvgb_status fvgb_fv_residual(fvgb_mesh m, const fvgb_tcoef* tc, const void* u_de
  *    tetrahedral meshes of roughly 480,000 cells. Larger meshes get FVGB_EINVAL with a
  *    message; use fvgb_fv_residual for them.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress, with that device current) and caches it; make that first
- *    call before any stream capture.
+ *    (cudaGetSymbolAddress, with that device current) and caches it together with the
+ *    unique id of the current CUDA context; make that first call before any stream
+ *    capture. A call in a different context of the device (after cudaDeviceReset, or
+ *    once the primary context was released and re-created) looks the address up again,
+ *    so a stale address is never used.
  *  - Every call shares the one array and leaves its contents behind; each call writes
  *    the scratch it reads, so nothing needs clearing, but calls that overlap on the GPU
  *    (other streams, other meshes, other host threads) race on it: serialise them.
@@ -294,6 +307,22 @@ fvgb_status fvgb_poisson_solve(fvgb_mesh m, int32_t bcset, const double* f_dev,
                                double* phi_dev, const fvgb_solve_opts* opts,
                                fvgb_solve_info* info, void* stream);
 
+/* Plasma spot of the branching streamer (Section 4, "Streamer Branching"): a source of
+ * electron-ion pairs S(x) = amplitude exp(-|x - centre|^2 / sigma^2) (the paper prints the
+ * exponent without its minus sign; this is the decaying reading), switched on during
+ * [t_on, t_on + duration). It adds to S_e of eq. 10, i.e. to both n_e and n_i. A step
+ * [t, t + dt] takes the spot's average over its overlap with that window,
+ * S(x) |[t, t + dt] n [t_on, t_on + duration]| / dt, so steps of any length deposit the
+ * spot's exact total; the three stages of eq. 6 all use that step average. The paper's
+ * values: amplitude 1e25, sigma 0.005, t_on 1.26e-8 s, duration 0.5e-9 s. */
+typedef struct {
+  double centre[3];     /* spot centre (x, y, z; z ignored in 2D) */
+  double amplitude;     /* > 0 */
+  double sigma;         /* > 0 */
+  double t_on;
+  double duration;      /* >= 0 */
+} fvgb_spot;
+
 /* Electron drift-diffusion + Poisson step of eq. 10 with the synthetic coefficients:
  * v = -mu E, alpha = A exp(-B/|E|) (0 at |E| = 0), S = alpha |v| n_e, constant D_e,
  * Lap phi = -(e/eps0)(n_i - n_e). Per step: solve for phi (warm start from phi_dev),
@@ -326,6 +355,11 @@ typedef struct {
                             the step's solve info then sums the stages' iterations and keeps
                             their largest residual; phi and E on return are the last stage's.
                             Three-stage steps run host-driven also in graph mode. */
+  double t0;             /* time at the start of the call's first step (step n of the call
+                            starts at t0 + n dt); only the plasma spots depend on it */
+  int32_t n_spot;        /* plasma spots (0..4) added to the source, see fvgb_spot */
+  const fvgb_spot* spots;  /* host array of n_spot spots (read during the call; in graph
+                              mode copied into the captured step) */
 } fvgb_streamer_params;
 
 /* ne_dev, ni_dev: [n_cell] real; phi_dev: [n_cell] double (in: guess, out: last
@@ -369,7 +403,9 @@ fvgb_status fvgb_integral(fvgb_mesh m, const void* u_dev, double* out_host, void
  *  cg_iterations    CG iterations they ran
  *  cg_ms            summed device time of those kernels, measured with CUDA events on the
  *                   launching stream when timing was enabled (0 otherwise)
- *  solves, outer_its  Poisson solves and their outer refinement steps */
+ *  solves, outer_its  Poisson solves and their outer refinement steps
+ *  learned_starts   parts of host-driven streamer solves that evaluated a learned start
+ *  learned_kept     of those, the parts whose learned start passed the residual check */
 typedef struct {
   int64_t kernel_launches;
   int64_t cg_launches;
@@ -377,6 +413,8 @@ typedef struct {
   double cg_ms;
   int64_t solves;
   int64_t outer_its;
+  int64_t learned_starts;
+  int64_t learned_kept;
 } fvgb_stats;
 
 /* Turn CUDA-event timing of the inner CG kernels on (1) or off (0). */
@@ -388,6 +426,19 @@ fvgb_status fvgb_stats_get(fvgb_mesh m, fvgb_stats* out, int32_t reset);
 /* Forget the warm-start history (earlier charges and potentials) of this mesh: the next
  * steps start from phi alone until the history is rebuilt. */
 fvgb_status fvgb_streamer_reset(fvgb_mesh m);
+
+/* Training pair of the learned warm start (no counterpart in the paper) from the history
+ * that the last fvgb_streamer_step kept on this mesh (steps with warm start or
+ * extrapolation requested keep one). With phi^n the potential at the start of that step,
+ * phi^{n+1} = phi_dev its solution, q = n_i - n_e at step starts, dq^n = q^n - q^{n-1}:
+ *  which = 0 (a start from the previous potential): dq^n, phi^n, phi^{n+1} - phi^n;
+ *    needs two steps of history since the last reset;
+ *  which = 1 (a start from the extrapolation 2 phi^n - phi^{n-1}): dq^n - dq^{n-1}, phi^n,
+ *    phi^{n+1} - 2 phi^n + phi^{n-1}; needs three steps.
+ * All arrays [n_cell] double on the device (outputs written by the call, stream-ordered).
+ * Errors: FVGB_EINVAL for a bad argument or too short a history. */
+fvgb_status fvgb_streamer_pair(fvgb_mesh m, int32_t which, const double* phi_dev, double* dq_dev,
+                               double* phi_prev_dev, double* dphi_dev, void* stream);
 
 /* ---- Learned warm start (no counterpart in the paper) --------------------------------
  * A message-passing network predicts the potential increment of a streamer step:
@@ -425,6 +476,20 @@ fvgb_status fvgb_mpnn_loss_grad(fvgb_mpnn net, const double* dq_dev, const doubl
 fvgb_status fvgb_mpnn_train_step(fvgb_mpnn net, const double* dq_dev, const double* phi_prev_dev,
                                  const double* dphi_dev, float lr, double* loss_host,
                                  void* stream);
+
+/* Synchronise the stream and report the latched asynchronous status of the mesh (see the
+ * conventions above), then clear it: FVGB_ETIMEOUT when a tensor-core wait of the network
+ * kernels ran out, FVGB_ENONFINITE when a transport update wrote a non-finite value since
+ * the last report, FVGB_OK otherwise. */
+fvgb_status fvgb_sync(fvgb_mesh m, void* stream);
+
+/* Test hook of the bounded grid barrier of the persistent CG kernel (no counterpart in the
+ * paper; for tests of the timeout path only). skip_block >= 0 makes that block of the
+ * kernel's grid never arrive at a barrier, so that the other blocks' waits run out and the
+ * solve returns FVGB_ETIMEOUT; timeout_ms > 0 replaces the 1 s wait limit. skip_block = -1
+ * and timeout_ms = 0 restore normal operation. A captured step graph is dropped.
+ * Errors: FVGB_EINVAL for skip_block outside [-1, grid) or timeout_ms outside [0, 1000]. */
+fvgb_status fvgb_test_barrier(fvgb_mesh m, int32_t skip_block, double timeout_ms);
 
 /* Message of the last failing call in this thread ("" if none). */
 const char* fvgb_last_error(void);

@@ -35,11 +35,12 @@ EXPORTED = [
     "fvgb_permute", "fvgb_gradient", "fvgb_gradient_vertex", "fvgb_vertex_values", "fvgb_fv_residual",
     "fvgb_fv_residual_noalloc",
     "fvgb_fv_step", "fvgb_poisson_apply", "fvgb_poisson_rhs", "fvgb_poisson_solve",
-    "fvgb_streamer_step", "fvgb_streamer_reset", "fvgb_set_graph_mode",
+    "fvgb_streamer_step", "fvgb_streamer_reset", "fvgb_streamer_pair", "fvgb_set_graph_mode",
     "fvgb_mpnn_create", "fvgb_mpnn_free", "fvgb_mpnn_param_count", "fvgb_mpnn_set_params",
     "fvgb_mpnn_get_params", "fvgb_mpnn_set_scales", "fvgb_mpnn_predict", "fvgb_mpnn_loss_grad",
     "fvgb_mpnn_train_step", "fvgb_autotune", "fvgb_set_launch_shape",
-    "fvgb_integral", "fvgb_stats_enable", "fvgb_stats_get", "fvgb_last_error",
+    "fvgb_integral", "fvgb_stats_enable", "fvgb_stats_get", "fvgb_sync", "fvgb_test_barrier",
+    "fvgb_last_error",
 ]
 
 
@@ -76,17 +77,23 @@ class fvgb_solve_info(C.Structure):
                 "rel_res": self.rel_res, "bnorm": self.bnorm}
 
 
+class fvgb_spot(C.Structure):
+    _fields_ = [("centre", C.c_double * 3), ("amplitude", C.c_double), ("sigma", C.c_double),
+                ("t_on", C.c_double), ("duration", C.c_double)]
+
+
 class fvgb_streamer_params(C.Structure):
     _fields_ = [("mu", C.c_double), ("A", C.c_double), ("B", C.c_double), ("De", C.c_double),
                 ("dt", C.c_double), ("bcset_ne", C.c_int32), ("bcset_phi", C.c_int32),
                 ("solve", fvgb_solve_opts), ("warm", C.c_void_p), ("extrapolate", C.c_int32),
-                ("recon", C.c_int32), ("stages", C.c_int32)]
+                ("recon", C.c_int32), ("stages", C.c_int32), ("t0", C.c_double),
+                ("n_spot", C.c_int32), ("spots", C.POINTER(fvgb_spot))]
 
 
 class fvgb_stats(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("cg_launches", C.c_int64),
                 ("cg_iterations", C.c_int64), ("cg_ms", C.c_double), ("solves", C.c_int64),
-                ("outer_its", C.c_int64)]
+                ("outer_its", C.c_int64), ("learned_starts", C.c_int64), ("learned_kept", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -122,6 +129,9 @@ _sig = {
     "fvgb_integral": (C.c_int, [_vp, _vp, C.POINTER(_d), _vp]),
     "fvgb_set_graph_mode": (C.c_int, [_vp, _i32]),
     "fvgb_streamer_reset": (C.c_int, [_vp]),
+    "fvgb_sync": (C.c_int, [_vp, _vp]),
+    "fvgb_test_barrier": (C.c_int, [_vp, _i32, _d]),
+    "fvgb_streamer_pair": (C.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
     "fvgb_mpnn_create": (C.c_int, [_vp, _i32, C.POINTER(_vp)]),
     "fvgb_mpnn_free": (C.c_int, [_vp]),
     "fvgb_mpnn_param_count": (C.c_int64, []),
@@ -363,15 +373,43 @@ def fvgb_poisson_solve(m, bcset, f, phi, opts, stream=None, check=True):
     return st, info
 
 
+def spot(centre, amplitude=1e25, sigma=0.005, t_on=1.26e-8, duration=0.5e-9):
+    c = list(centre) + [0.0] * (3 - len(centre))
+    return fvgb_spot((C.c_double * 3)(*[float(v) for v in c]), float(amplitude), float(sigma),
+                     float(t_on), float(duration))
+
+
 def streamer_params(mu=0.0382, A=4332.0, B=2.0e5, De=0.1, dt=1e-9, bcset_ne=0, bcset_phi=1,
-                    solve=None, warm=None, extrapolate=False, recon=0, stages=1):
-    return fvgb_streamer_params(mu, A, B, De, dt, bcset_ne, bcset_phi,
-                                solve if solve is not None else solve_opts(), warm,
-                                int(bool(extrapolate)), int(recon), int(stages))
+                    solve=None, warm=None, extrapolate=False, recon=0, stages=1, t0=0.0, spots=()):
+    """fvgb_streamer_params; ``spots`` is a sequence of fvgb_spot (see ``spot``)."""
+    arr = (fvgb_spot * max(len(spots), 1))(*spots)
+    p = fvgb_streamer_params(mu, A, B, De, dt, bcset_ne, bcset_phi,
+                             solve if solve is not None else solve_opts(), warm,
+                             int(bool(extrapolate)), int(recon), int(stages), float(t0),
+                             len(spots), arr if spots else None)
+    p._keep = arr
+    return p
 
 
 def fvgb_streamer_reset(m):
     return _check(lib.fvgb_streamer_reset(m), "fvgb_streamer_reset")
+
+
+def fvgb_sync(m, stream=None):
+    """Synchronise and report the mesh's latched asynchronous status (FvgbError on error)."""
+    return _check(lib.fvgb_sync(m, stream_handle(stream)), "fvgb_sync")
+
+
+def fvgb_test_barrier(m, skip_block=-1, timeout_ms=0.0):
+    """Test hook of the CG kernel's bounded grid barrier (see include/fvgb.h)."""
+    return _check(lib.fvgb_test_barrier(m, int(skip_block), float(timeout_ms)), "fvgb_test_barrier")
+
+
+def fvgb_streamer_pair(m, which, phi, dq, phi_prev, dphi, stream=None):
+    """Training pair of the last streamer step from the mesh's warm-start history (which 0:
+    start from the previous potential, 1: from the extrapolation) into dq, phi_prev, dphi."""
+    return _check(lib.fvgb_streamer_pair(m, int(which), ptr(phi), ptr(dq), ptr(phi_prev), ptr(dphi),
+                                         stream_handle(stream)), "fvgb_streamer_pair")
 
 
 def fvgb_mpnn_create(m, bcset):

@@ -312,10 +312,29 @@ fvgb_status solve_impl(fvgb_mesh m, int bcset, const double* f, double* phi,
   double* hn = m->h_scal + 8;
   int* hact = (int*)(m->h_scal + 8 + P);
   int* hinner = hact + P;
-  int* hst = hinner + P;                    // [0] CG status, [1] CG its, [2] barrier status
+  int* hst = hinner + P;                    // [0] CG status, [1] CG its, [2] barrier status,
+                                            // [3] latched transport status
   FVGB_TRY(launch_part_sumsq(m, b, m->parts.norms, s), "norm kernel");
   FVGB_TRY(cudaMemcpyAsync(hn, m->parts.norms, P * sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+  FVGB_TRY(cudaMemcpyAsync(hst + 3, m->d_status, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+  const bool count_warm = m->warm_check_pending;
+  if (count_warm) FVGB_TRY(cudaMemcpyAsync(hact, m->warm_used, P * sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+  m->warm_check_pending = false;
   FVGB_TRY(cudaStreamSynchronize(s), "synchronize");
+  if (count_warm) {
+    m->stats.learned_starts += P;
+    for (int p = 0; p < P; ++p) m->stats.learned_kept += hact[p] ? 1 : 0;
+  }
+  if (hst[3] != 0) {
+    FVGB_TRY(cudaMemsetAsync(m->d_status, 0, sizeof(int), s), "memset");
+    if (info) *info = loc;
+    if (hst[3] & 2) {
+      set_error("a tensor-core wait of the learned start timed out (latched status)");
+      return FVGB_ETIMEOUT;
+    }
+    set_error("an earlier transport call produced a non-finite value (latched status)");
+    return FVGB_ENONFINITE;
+  }
   std::vector<double> bn2(hn, hn + P);
   double bsum = 0.0;
   bool any_zero = false;
@@ -416,6 +435,7 @@ fvgb_status warm_start(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, voi
     FVGB_TRY(dalloc(m, &m->dq, N), "allocation");
     FVGB_TRY(dalloc(m, &m->d2q, N), "allocation");
     FVGB_TRY(dalloc(m, &m->phi_old, N), "allocation");
+    FVGB_TRY(dalloc(m, &m->phi_old2, N), "allocation");
     FVGB_TRY(dalloc(m, &m->dphi_pred, N), "allocation");
     FVGB_TRY(dalloc(m, &m->phi_save, N), "allocation");
     FVGB_TRY(dalloc(m, &m->warm_norms, 2 * P), "allocation");
@@ -423,7 +443,7 @@ fvgb_status warm_start(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, voi
   }
   FVGB_TRY(launch_charge_hist(m, ne, ni, is_fp32(m), hist, m->q_prev, m->dq, m->d2q, s), "charge kernel");
   const bool extrap = p->extrapolate && hist >= 2;
-  FVGB_TRY(launch_extrapolate(m, extrap, phi, m->phi_old, s), "extrapolation kernel");
+  FVGB_TRY(launch_extrapolate(m, extrap, phi, m->phi_old, m->phi_old2, s), "extrapolation kernel");
   const bool learn = p->warm && hist >= (p->extrapolate ? 2 : 1);
   if (!learn) return FVGB_OK;
   double* f = m->w64.tmp;
@@ -439,6 +459,7 @@ fvgb_status warm_start(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, voi
   FVGB_TRY(launch_axpy_d(m->dphi_pred, 1.0, phi, N, s), "update");
   if (fvgb_status st = poisson_residual(m, p->bcset_phi, phi, b, r, s)) return st;
   FVGB_TRY(launch_part_sumsq(m, r, m->warm_norms + P, s), "norm kernel");
+  m->warm_check_pending = true;
   return cuda_status(launch_choose_start(m, m->warm_norms, m->warm_norms + P, m->phi_save, phi,
                                          m->warm_used, s), "choose kernel");
 }
@@ -460,7 +481,7 @@ fvgb_status streamer_transport_stage(fvgb_mesh m, const fvgb_streamer_params* p,
     FVGB_TRY(launch_convert(phi, w.tmp, N, s), "convert");
     FVGB_TRY(launch_gradient<float>(m, p->bcset_phi, w.tmp, w.grad, s), "gradient kernel");
     FVGB_TRY(launch_cell_physics<float>(m, w.grad, (const float*)ne, p->mu, p->A, p->B, (float*)E,
-                                        w.vel, w.src, s), "cell kernel");
+                                        w.vel, w.src, spot_args(m, p), s), "cell kernel");
     FVGB_TRY(cudaMemcpyAsync(ni, ni0, N * sizeof(float), cudaMemcpyDeviceToDevice, s), "copy");
     tc.vel_dev = w.vel;
     tc.src_dev = w.src;
@@ -469,7 +490,7 @@ fvgb_status streamer_transport_stage(fvgb_mesh m, const fvgb_streamer_params* p,
   Work<double>& w = m->w64;
   FVGB_TRY(launch_gradient<double>(m, p->bcset_phi, phi, w.grad, s), "gradient kernel");
   FVGB_TRY(launch_cell_physics<double>(m, w.grad, (const double*)ne, p->mu, p->A, p->B, (double*)E,
-                                       w.vel, w.src, s), "cell kernel");
+                                       w.vel, w.src, spot_args(m, p), s), "cell kernel");
   FVGB_TRY(cudaMemcpyAsync(ni, ni0, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
   tc.vel_dev = w.vel;
   tc.src_dev = w.src;
@@ -491,7 +512,7 @@ fvgb_status streamer_transport(fvgb_mesh m, const fvgb_streamer_params* p, void*
     FVGB_TRY(launch_convert(phi, w.tmp, N, s), "convert");
     FVGB_TRY(launch_gradient<float>(m, p->bcset_phi, w.tmp, w.grad, s), "gradient kernel");
     FVGB_TRY(launch_cell_physics<float>(m, w.grad, (const float*)ne, p->mu, p->A, p->B, (float*)E,
-                                        w.vel, w.src, s), "cell kernel");
+                                        w.vel, w.src, spot_args(m, p), s), "cell kernel");
     tc.vel_dev = w.vel;
     tc.src_dev = w.src;
     return step_T<float>(m, &tc, (float*)ne, p->dt, 1, euler, 1, (float*)ni, s);
@@ -499,7 +520,7 @@ fvgb_status streamer_transport(fvgb_mesh m, const fvgb_streamer_params* p, void*
   Work<double>& w = m->w64;
   FVGB_TRY(launch_gradient<double>(m, p->bcset_phi, phi, w.grad, s), "gradient kernel");
   FVGB_TRY(launch_cell_physics<double>(m, w.grad, (const double*)ne, p->mu, p->A, p->B,
-                                       (double*)E, w.vel, w.src, s), "cell kernel");
+                                       (double*)E, w.vel, w.src, spot_args(m, p), s), "cell kernel");
   tc.vel_dev = w.vel;
   tc.src_dev = w.src;
   return step_T<double>(m, &tc, (double*)ne, p->dt, 1, euler, 1, (double*)ni, s);
@@ -673,6 +694,10 @@ static fvgb_status upload_impl(int32_t dim, int64_t n_vert, const double* xyz, i
   if ((e = cudaMemsetAsync(m->barrier, 0, sizeof(Barrier), s))) return fail(e, "memset");
   if ((e = dalloc(m, &m->d_cg_info, 4))) return fail(e, "allocation");
   if ((e = cudaMemsetAsync(m->d_cg_info, 0, 4 * sizeof(int), s))) return fail(e, "memset");
+  if ((e = dalloc(m, &m->d_status, 1))) return fail(e, "allocation");
+  if ((e = cudaMemsetAsync(m->d_status, 0, sizeof(int), s))) return fail(e, "memset");
+  if ((e = dalloc(m, &m->d_time, 1))) return fail(e, "allocation");
+  if ((e = cudaMemsetAsync(m->d_time, 0, sizeof(double), s))) return fail(e, "memset");
   if ((e = cudaMallocHost((void**)&m->h_scal, (16 + 4 * kMaxParts) * sizeof(double)))) return fail(e, "pinned allocation");
   m->solve_grid = solve_grid_size(m);
   if (m->solve_grid <= 0) {
@@ -869,9 +894,25 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
       (p->stages != 0 && p->stages != 1 && p->stages != 3)) { set_error("bad streamer arguments"); return FVGB_EINVAL; }
   if (fvgb_status st = check_bcset(m, p->bcset_ne)) return st;
   if (fvgb_status st = check_bcset(m, p->bcset_phi)) return st;
+  if (p->n_spot < 0 || p->n_spot > kMaxSpots || (p->n_spot > 0 && !p->spots) || !std::isfinite(p->t0) ||
+      !(p->dt > 0.0)) {
+    set_error("bad streamer arguments: n_spot must be in [0, 4] with a spot array, t0 finite, dt > 0");
+    return FVGB_EINVAL;
+  }
+  for (int k = 0; k < p->n_spot; ++k) {
+    const fvgb_spot& q = p->spots[k];
+    if (!(q.amplitude > 0.0) || !std::isfinite(q.amplitude) || !(q.sigma > 0.0) || !(q.duration >= 0.0) ||
+        !std::isfinite(q.t_on) || !std::isfinite(q.duration) || !std::isfinite(q.centre[0]) ||
+        !std::isfinite(q.centre[1]) || !std::isfinite(q.centre[2])) {
+      set_error("bad plasma spot " + std::to_string(k));
+      return FVGB_EINVAL;
+    }
+  }
   const bool fp32_solve = p->solve.prec == FVGB_FP32 || p->solve.prec == FVGB_MIXED;
   if (fp32_solve && !is_fp32(m)) { set_error("FP32 inner solve needs a mesh uploaded with FVGB_FP32 or FVGB_MIXED"); return FVGB_EINVAL; }
   cudaStream_t s = (cudaStream_t)stream;
+  // the step time lives on the device (read by the spot source, advanced after each step)
+  if (p->n_spot > 0) FVGB_TRY(launch_time(m, true, p->t0, s), "time kernel");
   int n0 = 0;
   const bool warm = warm_requested(p);
   const int stages = p->stages == 3 ? 3 : 1;
@@ -888,7 +929,7 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
     if (warm) {
       fvgb_status st = warm_start(m, p, ne, ni, phi, m->warm_hist, s);
       if (st) return st;
-      m->warm_hist = std::min(2, m->warm_hist + 1);
+      m->warm_hist = std::min(3, m->warm_hist + 1);
     }
     if (stages == 1) {
       fvgb_status st = cuda_status(launch_poisson_source(m, ne, ni, fp32, f, s), "source kernel");
@@ -897,6 +938,7 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
       if (st) return st;
       st = streamer_transport(m, p, ne, ni, phi, E, s);
       if (st) return st;
+      if (p->n_spot > 0) FVGB_TRY(launch_time(m, false, p->dt, s), "time kernel");
       continue;
     }
     // three stages of eq. 6, each with its own Poisson solve (from the previous stage's phi)
@@ -922,8 +964,57 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
       st = streamer_transport_stage(m, p, m->rk_ne0, m->rk_ni0, ne, ni, phi, E, kAlpha[k], s);
       if (st) return st;
     }
+    if (p->n_spot > 0) FVGB_TRY(launch_time(m, false, p->dt, s), "time kernel");
   }
   if (n0 > 0) return streamer_graph_steps(m, p, ne, ni, phi, E, n0, info ? info + nsteps : nullptr, s);
+  return FVGB_OK;
+}
+
+fvgb_status fvgb_streamer_pair(fvgb_mesh m, int32_t which, const double* phi, double* dq_out,
+                               double* phi_prev_out, double* dphi_out, void* stream) {
+  if (fvgb_status st = check_mesh(m)) return st;
+  if ((which != 0 && which != 1) || !phi || !dq_out || !phi_prev_out || !dphi_out) {
+    set_error("bad pair arguments");
+    return FVGB_EINVAL;
+  }
+  if (!m->phi_old || m->warm_hist < 2 + which) {
+    set_error(which ? "the pair of the extrapolated start needs three streamer steps with a warm start"
+                    : "the pair needs two streamer steps with a warm start");
+    return FVGB_EINVAL;
+  }
+  return cuda_status(launch_history_pair(m, which, phi, dq_out, phi_prev_out, dphi_out, (cudaStream_t)stream),
+                     "pair kernel");
+}
+
+fvgb_status fvgb_sync(fvgb_mesh m, void* stream) {
+  if (fvgb_status st = check_mesh(m)) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  int* h = (int*)(m->h_scal + 2);
+  FVGB_TRY(cudaMemcpyAsync(h, m->d_status, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+  FVGB_TRY(cudaStreamSynchronize(s), "synchronize");
+  if (*h != 0) {
+    const int v = *h;
+    FVGB_TRY(cudaMemsetAsync(m->d_status, 0, sizeof(int), s), "memset");
+    FVGB_TRY(cudaStreamSynchronize(s), "synchronize");
+    if (v & 2) {
+      set_error("a tensor-core wait of the network kernels timed out (latched status, now cleared)");
+      return FVGB_ETIMEOUT;
+    }
+    set_error("a transport call produced a non-finite value (latched status, now cleared)");
+    return FVGB_ENONFINITE;
+  }
+  return FVGB_OK;
+}
+
+fvgb_status fvgb_test_barrier(fvgb_mesh m, int32_t skip_block, double timeout_ms) {
+  if (fvgb_status st = check_mesh(m)) return st;
+  if (skip_block < -1 || skip_block >= m->solve_grid || !(timeout_ms >= 0.0) || timeout_ms > 1000.0) {
+    set_error("skip_block must be in [-1, grid) and timeout_ms in [0, 1000]");
+    return FVGB_EINVAL;
+  }
+  m->test_skip_block = skip_block;
+  m->test_barrier_ns = (unsigned long long)(timeout_ms * 1e6);
+  graph_invalidate(m);
   return FVGB_OK;
 }
 

@@ -10,6 +10,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "internal.h"
 
@@ -33,6 +34,7 @@ struct GraphState {
   double* phi = nullptr;
   void* E = nullptr;
   fvgb_streamer_params params{};
+  std::vector<fvgb_spot> spots;   // copy of the captured step's plasma spots
   // device state
   double* bn2 = nullptr;        // [P]
   double* rel = nullptr;        // [P]
@@ -115,7 +117,20 @@ __global__ void k_zero_parts(const double* __restrict__ bn2, const int32_t* __re
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) phi[i] = 0.0;
 }
 
-// field by field (padding bytes of a caller's struct may hold anything)
+bool same_spots(const std::vector<fvgb_spot>& a, const fvgb_streamer_params& b) {
+  if ((int)a.size() != b.n_spot) return false;
+  for (int k = 0; k < b.n_spot; ++k) {
+    const fvgb_spot& x = a[k];
+    const fvgb_spot& y = b.spots[k];
+    if (x.centre[0] != y.centre[0] || x.centre[1] != y.centre[1] || x.centre[2] != y.centre[2] ||
+        x.amplitude != y.amplitude || x.sigma != y.sigma || x.t_on != y.t_on || x.duration != y.duration)
+      return false;
+  }
+  return true;
+}
+
+// field by field (padding bytes of a caller's struct may hold anything); the start time t0
+// is not part of the graph (the step time lives on the device)
 bool same_params(const fvgb_streamer_params& a, const fvgb_streamer_params& b) {
   return a.mu == b.mu && a.A == b.A && a.B == b.B && a.De == b.De && a.dt == b.dt &&
          a.bcset_ne == b.bcset_ne && a.bcset_phi == b.bcset_phi && a.solve.rtol == b.solve.rtol &&
@@ -154,6 +169,7 @@ fvgb_status build_graph(fvgb_mesh m, GraphState& g, const fvgb_streamer_params* 
   };
   // ---- before the loop
   if (warm_requested(p) && (st = warm_start(m, p, ne, ni, phi, 2, g.cs))) return bail(st);
+  m->warm_check_pending = false;   // captured, not run: graph steps are not counted
   if ((st = cuda_status(launch_poisson_source(m, ne, ni, is_fp32(m), f, g.cs), "source kernel"))) return bail(st);
   if ((st = poisson_rhs_impl(m, p->bcset_phi, f, b, g.cs))) return bail(st);
   if ((st = cuda_status(launch_part_sumsq(m, b, g.bn2, g.cs), "norm kernel"))) return bail(st);
@@ -189,6 +205,7 @@ fvgb_status build_graph(fvgb_mesh m, GraphState& g, const fvgb_streamer_params* 
                         "capture dependencies"))) return bail(st);
   // ---- after the loop: field, cell physics, transport
   if ((st = streamer_transport(m, p, ne, ni, phi, E, g.cs))) return bail(st);
+  if (p->n_spot > 0 && (st = cuda_status(launch_time(m, false, p->dt, g.cs), "time kernel"))) return bail(st);
   const long long k2 = g_kernel_launches.load();
   cudaGraph_t out = nullptr;
   if ((st = cuda_status(cudaStreamEndCapture(g.cs, &out), "end capture"))) { cudaGraphDestroy(graph); return st; }
@@ -229,6 +246,8 @@ fvgb_status build_graph(fvgb_mesh m, GraphState& g, const fvgb_streamer_params* 
   if (g.exec) cudaGraphExecDestroy(g.exec);
   g.exec = exec;
   g.ne = ne; g.ni = ni; g.phi = phi; g.E = E; g.params = *p;
+  g.spots.assign(p->spots, p->spots + p->n_spot);
+  g.params.spots = nullptr;
   g.k_pre = k1 - k0;
   g.k_post = k2 - k1;
   g.k_body = k3 - k2;
@@ -279,7 +298,7 @@ fvgb_status streamer_graph_steps(fvgb_mesh m, const fvgb_streamer_params* p, voi
     g->ctl = (int*)c;
   }
   GraphState& g = *m->graph;
-  if (!g.exec || g.ne != ne || g.ni != ni || g.phi != phi || g.E != E || !same_params(g.params, *p)) {
+  if (!g.exec || g.ne != ne || g.ni != ni || g.phi != phi || g.E != E || !same_params(g.params, *p) || !same_spots(g.spots, *p)) {
     FVGB_TRY(cudaStreamSynchronize(s), "synchronize");
     if (fvgb_status st = build_graph(m, g, p, ne, ni, phi, E)) return st;
   }
@@ -294,6 +313,8 @@ fvgb_status streamer_graph_steps(fvgb_mesh m, const fvgb_streamer_params* p, voi
     FVGB_TRY(cudaGraphLaunch(g.exec, s), "graph launch");
     FVGB_TRY(cudaMemcpyAsync(g.h_info + n, g.info, sizeof(StepInfoDev), cudaMemcpyDeviceToHost, s), "copy");
   }
+  // a captured step updates the warm-start history like a host-driven one
+  if (warm_requested(p)) m->warm_hist = std::min(3, m->warm_hist + nsteps);
   // per-part results of the last solve, for fvgb_solve_parts
   m->last_rel.assign(P, 0.0);
   m->last_outer.assign(P, 0);
@@ -301,6 +322,8 @@ fvgb_status streamer_graph_steps(fvgb_mesh m, const fvgb_streamer_params* p, voi
   FVGB_TRY(cudaMemcpyAsync(m->last_rel.data(), g.rel, P * sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
   FVGB_TRY(cudaMemcpyAsync(m->last_outer.data(), g.outer, P * sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
   FVGB_TRY(cudaMemcpyAsync(m->last_inner.data(), g.inner, P * sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+  int* hlatch = (int*)(m->h_scal + 3);
+  FVGB_TRY(cudaMemcpyAsync(hlatch, m->d_status, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
   FVGB_TRY(cudaStreamSynchronize(s), "synchronize");
   fvgb_status first = FVGB_OK;
   for (int n = 0; n < nsteps; ++n) {
@@ -315,6 +338,11 @@ fvgb_status streamer_graph_steps(fvgb_mesh m, const fvgb_streamer_params* p, voi
       first = d.status == 5 ? FVGB_ENOCONV : d.status == 7 ? FVGB_ETIMEOUT : FVGB_ENONFINITE;
       set_error("streamer step " + std::to_string(n) + ": Poisson solve failed (status " + std::to_string(d.status) + ")");
     }
+  }
+  if (first == FVGB_OK && *hlatch != 0) {
+    FVGB_TRY(cudaMemsetAsync(m->d_status, 0, sizeof(int), s), "memset");
+    set_error("a transport update of a graph step produced a non-finite value (latched status)");
+    first = FVGB_ENONFINITE;
   }
   return first;
 }

@@ -137,6 +137,12 @@ struct fvgb_mesh_s {
   double* dzero = nullptr;              // [N] zeros
   fvgb::Barrier* barrier = nullptr;
   int* d_cg_info = nullptr;             // [4] iterations, status
+  int* d_status = nullptr;              // latched asynchronous errors, cleared when reported:
+                                        // bit 0 (1) non-finite transport output, bit 1 (2) a
+                                        // tensor-core wait of the network kernels timed out
+  double* d_time = nullptr;             // start time of the current streamer step
+  int test_skip_block = -1;             // test hook of the CG barrier (fvgb_test_barrier)
+  unsigned long long test_barrier_ns = 0;  // barrier wait limit (0: the default 1 s)
   int solve_grid = 0;                   // cooperative grid of the Poisson kernel
   fvgb::PartsDev parts;
   std::vector<int64_t> part_cell_begin; // [P+1] internal cell range of each part
@@ -152,12 +158,14 @@ struct fvgb_mesh_s {
   double* q_prev = nullptr;             // [N] n_i - n_e of the previous step
   double* dq = nullptr;                 // [N] latest change of n_i - n_e
   double* d2q = nullptr;                // [N] its change since the step before
-  double* phi_old = nullptr;            // [N] potential of the step before the last
+  double* phi_old = nullptr;            // [N] potential at the start of the last step
+  double* phi_old2 = nullptr;           // [N] potential at the start of the step before
   double* dphi_pred = nullptr;          // [N] learned correction
   double* phi_save = nullptr;           // [N] start without the learned correction
   double* warm_norms = nullptr;         // [2][P] residual norms of the two starts
   int* warm_used = nullptr;             // [P] 1 where the learned start was kept
-  int warm_hist = 0;                    // streamer steps recorded in the history (capped at 2)
+  bool warm_check_pending = false;      // warm_used of a host-driven step not yet counted
+  int warm_hist = 0;                    // streamer steps recorded in the history (capped at 3)
   fvgb::GraphState* graph = nullptr;    // captured step graph (graph.cu)
   fvgb::AmgState* amg = nullptr;        // multigrid hierarchies per boundary set (amg.cu)
   void* rk_ne0 = nullptr;               // [N] n_e, n_i at the start of a three-stage streamer step
@@ -212,16 +220,32 @@ enum UpdateMode { kResidual = 0, kStep = 1, kPoissonApply = 2, kPoissonResidual 
 template <typename T>
 cudaError_t launch_update(fvgb_mesh_s* m, int mode, const T* flux, const T* src, const T* base,
                           double adt, const T* aux, T* out, T* out2, cudaStream_t s);
+// Plasma spots of a streamer step (fvgb_spot), passed to the cell-physics kernel by value;
+// the step's start time is read from the device (m->d_time).
+constexpr int kMaxSpots = 4;
+struct SpotArgs {
+  int n = 0;
+  double cx[kMaxSpots], cy[kMaxSpots], cz[kMaxSpots];
+  double amp[kMaxSpots], s2[kMaxSpots], t_on[kMaxSpots], t_off[kMaxSpots];
+  double dt = 0.0;
+  const double* t = nullptr;
+};
+SpotArgs spot_args(fvgb_mesh_s* m, const fvgb_streamer_params* p);
 template <typename T>
 cudaError_t launch_cell_physics(fvgb_mesh_s* m, const T* grad, const T* ne, double mu, double A,
-                                double B, T* E, T* vel, T* src, cudaStream_t s);
+                                double B, T* E, T* vel, T* src, const SpotArgs& sp, cudaStream_t s);
+// device time of the streamer steps: set, or advanced by dt
+cudaError_t launch_time(fvgb_mesh_s* m, bool set, double v, cudaStream_t s);
 cudaError_t launch_poisson_source(fvgb_mesh_s* m, const void* ne, const void* ni, bool fp32,
                                   double* f, cudaStream_t s);
 cudaError_t launch_sumsq(fvgb_mesh_s* m, const double* x, int64_t n, double* out, cudaStream_t s);
 cudaError_t launch_integral(fvgb_mesh_s* m, const void* u, bool fp32, double* out, cudaStream_t s);
 cudaError_t launch_charge_hist(fvgb_mesh_s* m, const void* ne, const void* ni, bool fp32, int hist,
                                double* q_prev, double* dq, double* d2q, cudaStream_t s);
-cudaError_t launch_extrapolate(fvgb_mesh_s* m, bool extrap, double* phi, double* phi_old, cudaStream_t s);
+cudaError_t launch_extrapolate(fvgb_mesh_s* m, bool extrap, double* phi, double* phi_old, double* phi_old2,
+                               cudaStream_t s);
+cudaError_t launch_history_pair(fvgb_mesh_s* m, int which, const double* phi, double* q_out, double* p_out,
+                                double* d_out, cudaStream_t s);
 cudaError_t launch_choose_start(fvgb_mesh_s* m, const double* na, const double* nb, const double* saved,
                                 double* phi, int* used, cudaStream_t s);
 cudaError_t launch_axpy_d(const double* x, double a, double* y, int64_t n, cudaStream_t s);

@@ -7,10 +7,13 @@
 //         z   = W_l [h ; m] + b_l,   h = h + relu(z)
 //   out   = w_dec . h + b_dec,  predicted potential increment V s2 out
 //
-// The layer products [h ; m] W_l^T (16 cells x 128 inputs x 64 outputs per warp tile)
-// and their backward dz W_l run on the tensor cores with mma.sync m16n8k16 (BF16
-// operands, FP32 accumulation); hidden states, messages and pre-activations are kept in
-// FP32. Weight gradients are FP32 outer-product sums per block, reduced over blocks in
+// The layer products [h ; m] W_l^T (128 cells x 128 inputs x 64 outputs per tile) and
+// their backward dz W_l (128 cells x 64 x 128) run on the fifth-generation tensor cores:
+// the block gathers a tile of BF16 operands into shared memory (canonical K-major layout
+// without swizzle), one thread issues tcgen05.mma (kind::f16, FP32 accumulators in tensor
+// memory), completion is signalled through an mbarrier, and every thread reads its
+// cell's row of the accumulator with tcgen05.ld for the fused epilogue (bias, ReLU,
+// residual). Hidden states, messages and pre-activations are kept in FP32. Weight gradients are FP32 outer-product sums per block, reduced over blocks in
 // FP64 in a fixed order (deterministic). Adam updates FP32 master weights and refreshes
 // their BF16 copies.
 #include <cuda_bf16.h>
@@ -31,10 +34,13 @@ constexpr int kOffWenc = 0, kOffBenc = 128, kOffLayer0 = 192, kLayerSize = kHid 
 constexpr int kOffWdec = kOffLayer0 + kLayers * kLayerSize;   // 24960
 constexpr int kOffBdec = kOffWdec + kHid;                       // 25024
 constexpr int kNParams = kOffBdec + 1;                          // 25025
-constexpr int kApad = kIn + 8;         // padded bf16 row of an A tile / W row
-constexpr int kTpad = kHid + 8;        // padded bf16 row of a transposed W / dz tile
-constexpr int kWarps = 4;              // warps per block of the tensor-core kernels
+constexpr int kTile = 128;             // cells per tensor-core tile (the MMA's M), one thread each
 constexpr int kGradBlocks = 304;       // blocks of the gradient reductions
+// dynamic shared memory of the layer kernels: forward A = [h ; m] (128 x 128 BF16, 32 KB)
+// and W (64 x 128, 16 KB); backward A = dz (128 x 64, 16 KB) and W^T (128 x 64, 16 KB),
+// padded to 72 KB so that at most three blocks share an SM (3 x 128 tensor-memory columns)
+constexpr uint32_t kFwdB = 32768, kFwdSmem = 49152;
+constexpr uint32_t kBwdB = 16384, kBwdSmem = 72 * 1024;
 
 }  // namespace fvgb
 
@@ -74,23 +80,116 @@ using MpnnNet = ::fvgb_mpnn_s;
 
 namespace {
 
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+// ---- tcgen05 helpers -------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Byte offset of element (r, k) of a K-major tile with K elements a row, without swizzle:
+// 8 x 8 core matrices of 16-byte rows; core matrices adjacent in K are 128 bytes apart,
+// groups of 8 rows are K / 8 x 128 bytes apart.
+__device__ __forceinline__ uint32_t kmaj_off(int r, int k, int K) {
+  return (uint32_t)((r >> 3) * (K >> 3) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Shared-memory matrix descriptor of tcgen05.mma for such a tile: start address, leading
+// byte offset (K-adjacent core matrices), stride byte offset (8-row groups), version 1,
+// no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B (both K-major), FP32 accumulator, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// make the block's st.shared of an operand tile visible to the tensor cores
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {   // one warp
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)), "r"(ncols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {      // the same warp
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+// D (tensor memory) = A B^T (+ D when accumulate), one thread issues
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       int accumulate) {
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+// arrive on the mbarrier once every MMA issued so far by this thread has completed
+__device__ __forceinline__ void tc_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+               : "memory");
 }
 
-__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p) {
-  return *reinterpret_cast<const uint32_t*>(p);
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-__device__ __forceinline__ void st_pair(__nv_bfloat16* p, float a, float b) {
+__device__ __forceinline__ unsigned long long mp_global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase ``parity`` of the mbarrier, for at most one second; false on timeout.
+constexpr unsigned long long kMbarTimeoutNs = 1000000000ull;
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+  const uint32_t a = smem_u32(mbar);
+  const unsigned long long t0 = mp_global_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done) : "r"(a), "r"(parity) : "memory");
+    if (done) return true;
+    if (mp_global_ns() - t0 > kMbarTimeoutNs) return false;
+  }
+}
+
+// 32 consecutive FP32 accumulator columns of this thread's lane (its warp's 32 lanes)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void load8(const float* p, float (&v)[8]) {
+  const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void store8(float* p, const float (&v)[8]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  *reinterpret_cast<float4*>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
+}
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 v;
   v.x = __float2bfloat16_rn(a);
   v.y = __float2bfloat16_rn(b);
-  *reinterpret_cast<__nv_bfloat162*>(p) = v;
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+// eight values as BF16 into one 16-byte row of a core matrix
+__device__ __forceinline__ void st_bf16x8(unsigned char* p, const float (&v)[8]) {
+  *reinterpret_cast<uint4*>(p) = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]),
+                                            pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
 }
 
 // ---- features and message weights ---------------------------------------------------------
@@ -141,77 +240,115 @@ __global__ void k_encode(int64_t N, const float* __restrict__ F, const float* __
 }
 
 // ---- one message-passing layer, forward (tensor cores) ---------------------------------------
-// Warp w of a block handles tiles of 16 cells: A = [h ; m] (16 x 128, BF16 in shared
-// memory), Z = A W^T + b by 8 n-tiles x 8 k-steps of m16n8k16, H_out = H + relu(Z).
-__global__ void __launch_bounds__(32 * kWarps)
+// Persistent over tiles of 128 cells, thread t owning cell tile * 128 + t: the thread gathers
+// its cell's row A_t = [h ; m] (m = sum_j w_j (h_j - h), four neighbours, in chunks of eight
+// features) into the BF16 tile, thread 0 issues Z = A W^T as 8 tcgen05.mma of K = 16 into
+// 64 tensor-memory columns, and after the mbarrier signals completion every thread reads its
+// row, adds the bias and writes H_out = H + relu(Z) (and, when training, M and Z). A wait
+// that runs out sets bit 2 of *err and the block leaves.
+__global__ void __launch_bounds__(kTile)
 k_layer_fwd(int64_t N, const float* __restrict__ H, const int4* __restrict__ nbr, const float4* __restrict__ wn,
             const __nv_bfloat16* __restrict__ Wg, const float* __restrict__ bias, float* __restrict__ Mout,
-            float* __restrict__ Zout, float* __restrict__ Hout) {
-  __shared__ __align__(16) __nv_bfloat16 Ws[kHid * kApad];
-  __shared__ __align__(16) __nv_bfloat16 As[kWarps][16 * kApad];
+            float* __restrict__ Zout, float* __restrict__ Hout, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
   __shared__ float bs[kHid];
-  for (int k = threadIdx.x; k < kHid * kIn; k += blockDim.x) Ws[(k / kIn) * kApad + (k % kIn)] = Wg[k];
-  for (int k = threadIdx.x; k < kHid; k += blockDim.x) bs[k] = bias[k];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, t4 = lane & 3;
-  __nv_bfloat16* A = As[warp];
-  const int64_t ntiles = (N + 15) / 16;
-  for (int64_t tile = blockIdx.x * (int64_t)kWarps + warp; tile < ntiles; tile += (int64_t)gridDim.x * kWarps) {
-    const int64_t c0 = tile * 16;
-    for (int r = 0; r < 16; ++r) {
-      const int64_t c = c0 + r;
-      float hx = 0.0f, hy = 0.0f, mx = 0.0f, my = 0.0f;
-      if (c < N) {
-        const float2 h = *reinterpret_cast<const float2*>(H + c * kHid + 2 * lane);
-        hx = h.x; hy = h.y;
-        const int4 nb = nbr[c];
-        const float4 w = wn[c];
-        const int ns[4] = {nb.x, nb.y, nb.z, nb.w};
-        const float ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          const float2 hn = *reinterpret_cast<const float2*>(H + (int64_t)ns[s] * kHid + 2 * lane);
-          mx += ws[s] * (hn.x - hx);
-          my += ws[s] * (hn.y - hy);
-        }
-        if (Mout) *reinterpret_cast<float2*>(Mout + c * kHid + 2 * lane) = make_float2(mx, my);
-      }
-      st_pair(A + r * kApad + 2 * lane, hx, hy);
-      st_pair(A + r * kApad + kHid + 2 * lane, mx, my);
-    }
-    __syncwarp();
-    float acc[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
-#pragma unroll
-    for (int kk = 0; kk < kIn / 16; ++kk) {
-      uint32_t a[4];
-      a[0] = ld_pair(A + g * kApad + kk * 16 + 2 * t4);
-      a[1] = ld_pair(A + (g + 8) * kApad + kk * 16 + 2 * t4);
-      a[2] = ld_pair(A + g * kApad + kk * 16 + 8 + 2 * t4);
-      a[3] = ld_pair(A + (g + 8) * kApad + kk * 16 + 8 + 2 * t4);
-#pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
-        const __nv_bfloat16* Bc = Ws + (nt * 8 + g) * kApad + kk * 16 + 2 * t4;
-        mma16816(acc[nt], a, ld_pair(Bc), ld_pair(Bc + 8));
-      }
-    }
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const int col = nt * 8 + 2 * t4;
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const int64_t c = c0 + g + 8 * half;
-        if (c >= N) continue;
-        const float z0 = acc[nt][2 * half] + bs[col], z1 = acc[nt][2 * half + 1] + bs[col + 1];
-        if (Zout) *reinterpret_cast<float2*>(Zout + c * kHid + col) = make_float2(z0, z1);
-        const float2 h = *reinterpret_cast<const float2*>(H + c * kHid + col);
-        *reinterpret_cast<float2*>(Hout + c * kHid + col) = make_float2(h.x + fmaxf(z0, 0.0f), h.y + fmaxf(z1, 0.0f));
-      }
-    }
-    __syncwarp();
+  __shared__ int s_fail;
+  const int t = threadIdx.x, warp = t >> 5;
+  unsigned char* As = smem;
+  unsigned char* Bs = smem + kFwdB;
+  // W (the B operand: 64 outputs x 128 inputs, K-major) and the bias, once per block
+  for (int e = t; e < kHid * (kIn / 8); e += kTile) {
+    const int r = e / (kIn / 8), kc = e % (kIn / 8);
+    *reinterpret_cast<uint4*>(Bs + kmaj_off(r, kc * 8, kIn)) =
+        *reinterpret_cast<const uint4*>(Wg + r * kIn + kc * 8);
   }
+  if (t < kHid) bs[t] = bias[t];
+  if (t == 0) {
+    s_fail = 0;
+    mbar_init(&mbar, 1);
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, kHid);
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's 32 lanes
+  const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+  const int64_t ntiles = (N + kTile - 1) / kTile;
+  uint32_t phase = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t c = tile * kTile + t;
+    const bool live = c < N;
+    const int4 nb = live ? nbr[c] : make_int4(0, 0, 0, 0);
+    const float4 w4 = live ? wn[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int ns[4] = {nb.x, nb.y, nb.z, nb.w};
+    const float ws[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll 1
+    for (int kc = 0; kc < kHid / 8; ++kc) {
+      float h[8], m[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) h[j] = m[j] = 0.0f;
+      if (live) {
+        load8(H + c * kHid + kc * 8, h);
+        float g[4][8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) load8(H + (int64_t)ns[q] * kHid + kc * 8, g[q]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) m[j] += ws[q] * (g[q][j] - h[j]);
+        if (Mout) store8(Mout + c * kHid + kc * 8, m);
+      }
+      st_bf16x8(As + kmaj_off(t, kc * 8, kIn), h);
+      st_bf16x8(As + kmaj_off(t, kHid + kc * 8, kIn), m);
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < kIn / 16; ++kk)
+        tc_mma(tmem, smem_desc(a0 + kk * 256, 128, (kIn / 8) * 128), smem_desc(b0 + kk * 256, 128, (kIn / 8) * 128),
+               idesc_bf16(kTile, kHid), kk > 0);
+      tc_commit(&mbar);
+    }
+    if (!mbar_wait(&mbar, phase)) s_fail = 1;
+    phase ^= 1;
+    __syncthreads();
+    if (s_fail) break;
+    tc_fence_after();
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      float z[32];
+      tmem_ld32(trow + half * 32, z);
+      if (live) {
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          const int col = half * 32 + j;
+          const float4 zz = make_float4(z[j] + bs[col], z[j + 1] + bs[col + 1], z[j + 2] + bs[col + 2],
+                                        z[j + 3] + bs[col + 3]);
+          if (Zout) *reinterpret_cast<float4*>(Zout + c * kHid + col) = zz;
+          const float4 hv = *reinterpret_cast<const float4*>(H + c * kHid + col);
+          *reinterpret_cast<float4*>(Hout + c * kHid + col) =
+              make_float4(hv.x + fmaxf(zz.x, 0.0f), hv.y + fmaxf(zz.y, 0.0f), hv.z + fmaxf(zz.z, 0.0f),
+                          hv.w + fmaxf(zz.w, 0.0f));
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();      // accumulator read and A tile consumed before the next tile
+  }
+  if (s_fail) {
+    if (t == 0) atomicOr(err, 2);
+    mbar_wait(&mbar, phase ^ 1);       // the tensor cores may still be writing: wait once more
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, kHid);
 }
 
 // ---- decoder: out = w_dec . h + b_dec ----------------------------------------------------------
@@ -295,73 +432,101 @@ __global__ void k_decode_grad(int64_t N, const float* __restrict__ Ha, const flo
 }
 
 // ---- one layer, backward (tensor cores) --------------------------------------------------------
-// dz = dH_next * (z > 0);  [g_h ; g_m] = dz W_l  (16 cells x 64 x 128 per warp tile);
-// dH = dH_next + g_h;  G = g_m (its message is added by k_msg_add);  dZ = dz (FP32, for the
-// weight gradients).
-__global__ void __launch_bounds__(32 * kWarps)
+// dz = dH_next * (z > 0);  [g_h ; g_m] = dz W_l (128 cells x 64 x 128 per tile, tcgen05.mma
+// into 128 tensor-memory columns);  dH = dH_next + g_h;  G = g_m (its message is added by
+// k_msg_add);  dZ = dz (FP32, for the weight gradients). Structure as k_layer_fwd.
+__global__ void __launch_bounds__(kTile)
 k_layer_bwd(int64_t N, const float* __restrict__ dHn, const float* __restrict__ Z,
             const __nv_bfloat16* __restrict__ Wg, float* __restrict__ dZ, float* __restrict__ dH,
-            float* __restrict__ G) {
-  __shared__ __align__(16) __nv_bfloat16 WT[kIn * kTpad];   // W^T: [in][out]
-  __shared__ __align__(16) __nv_bfloat16 Ds[kWarps][16 * kTpad];
-  for (int k = threadIdx.x; k < kHid * kIn; k += blockDim.x) {
-    const int o = k / kIn, i = k % kIn;
-    WT[i * kTpad + o] = Wg[k];
+            float* __restrict__ G, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  const int t = threadIdx.x, warp = t >> 5;
+  unsigned char* As = smem;
+  unsigned char* Bs = smem + kBwdB;
+  // W^T (the B operand: 128 inputs x 64 outputs, K-major): element (n, k) = W[k][n]
+  for (int e = t; e < kHid * kIn; e += kTile) {
+    const int k = e / kIn, n = e % kIn;
+    *reinterpret_cast<__nv_bfloat16*>(Bs + kmaj_off(n, k, kHid)) = Wg[e];
   }
+  if (t == 0) {
+    s_fail = 0;
+    mbar_init(&mbar, 1);
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, kIn);
+  fence_async_smem();
+  tc_fence_before();
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, t4 = lane & 3;
-  __nv_bfloat16* D = Ds[warp];
-  const int64_t ntiles = (N + 15) / 16;
-  for (int64_t tile = blockIdx.x * (int64_t)kWarps + warp; tile < ntiles; tile += (int64_t)gridDim.x * kWarps) {
-    const int64_t c0 = tile * 16;
-    for (int r = 0; r < 16; ++r) {
-      const int64_t c = c0 + r;
-      float dx = 0.0f, dy = 0.0f;
-      if (c < N) {
-        const float2 d = *reinterpret_cast<const float2*>(dHn + c * kHid + 2 * lane);
-        const float2 z = *reinterpret_cast<const float2*>(Z + c * kHid + 2 * lane);
-        dx = z.x > 0.0f ? d.x : 0.0f;
-        dy = z.y > 0.0f ? d.y : 0.0f;
-        *reinterpret_cast<float2*>(dZ + c * kHid + 2 * lane) = make_float2(dx, dy);
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+  const int64_t ntiles = (N + kTile - 1) / kTile;
+  uint32_t phase = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t c = tile * kTile + t;
+    const bool live = c < N;
+#pragma unroll 1
+    for (int kc = 0; kc < kHid / 8; ++kc) {
+      float d[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) d[j] = 0.0f;
+      if (live) {
+        float z[8];
+        load8(dHn + c * kHid + kc * 8, d);
+        load8(Z + c * kHid + kc * 8, z);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) d[j] = z[j] > 0.0f ? d[j] : 0.0f;
+        store8(dZ + c * kHid + kc * 8, d);
       }
-      st_pair(D + r * kTpad + 2 * lane, dx, dy);
+      st_bf16x8(As + kmaj_off(t, kc * 8, kHid), d);
     }
-    __syncwarp();
-    float acc[16][4];
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
 #pragma unroll
-    for (int nt = 0; nt < 16; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
-#pragma unroll
-    for (int kk = 0; kk < kHid / 16; ++kk) {
-      uint32_t a[4];
-      a[0] = ld_pair(D + g * kTpad + kk * 16 + 2 * t4);
-      a[1] = ld_pair(D + (g + 8) * kTpad + kk * 16 + 2 * t4);
-      a[2] = ld_pair(D + g * kTpad + kk * 16 + 8 + 2 * t4);
-      a[3] = ld_pair(D + (g + 8) * kTpad + kk * 16 + 8 + 2 * t4);
-#pragma unroll
-      for (int nt = 0; nt < 16; ++nt) {
-        const __nv_bfloat16* Bc = WT + (nt * 8 + g) * kTpad + kk * 16 + 2 * t4;
-        mma16816(acc[nt], a, ld_pair(Bc), ld_pair(Bc + 8));
-      }
+      for (int kk = 0; kk < kHid / 16; ++kk)
+        tc_mma(tmem, smem_desc(a0 + kk * 256, 128, (kHid / 8) * 128), smem_desc(b0 + kk * 256, 128, (kHid / 8) * 128),
+               idesc_bf16(kTile, kIn), kk > 0);
+      tc_commit(&mbar);
     }
+    if (!mbar_wait(&mbar, phase)) s_fail = 1;
+    phase ^= 1;
+    __syncthreads();
+    if (s_fail) break;
+    tc_fence_after();
 #pragma unroll
-    for (int nt = 0; nt < 16; ++nt) {
-      const int col = nt * 8 + 2 * t4;
+    for (int q = 0; q < 4; ++q) {
+      float v[32];
+      tmem_ld32(trow + q * 32, v);
+      if (live) {
 #pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const int64_t c = c0 + g + 8 * half;
-        if (c >= N) continue;
-        const float v0 = acc[nt][2 * half], v1 = acc[nt][2 * half + 1];
-        if (col < kHid) {
-          const float2 d = *reinterpret_cast<const float2*>(dHn + c * kHid + col);
-          *reinterpret_cast<float2*>(dH + c * kHid + col) = make_float2(d.x + v0, d.y + v1);
-        } else {
-          *reinterpret_cast<float2*>(G + c * kHid + col - kHid) = make_float2(v0, v1);
+        for (int j = 0; j < 32; j += 4) {
+          const int col = q * 32 + j;
+          if (col < kHid) {
+            const float4 dv = *reinterpret_cast<const float4*>(dHn + c * kHid + col);
+            *reinterpret_cast<float4*>(dH + c * kHid + col) =
+                make_float4(dv.x + v[j], dv.y + v[j + 1], dv.z + v[j + 2], dv.w + v[j + 3]);
+          } else {
+            *reinterpret_cast<float4*>(G + c * kHid + col - kHid) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+          }
         }
       }
     }
-    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
   }
+  if (s_fail) {
+    if (t == 0) atomicOr(err, 2);
+    mbar_wait(&mbar, phase ^ 1);
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, kIn);
 }
 
 // dH_i += sum_j w_ij (G_j - G_i): the adjoint of the (symmetric) message operator
@@ -533,8 +698,19 @@ cudaError_t alloc_train(MpnnNet* n) {
   return cudaSuccess;
 }
 
-unsigned layer_grid(MpnnNet* n) {
-  return (unsigned)std::min<int64_t>((n->N + 16 * kWarps - 1) / (16 * kWarps), (int64_t)n->m->num_sms * 16);
+// grids of the tensor-core layer kernels: persistent over 128-cell tiles, as many blocks as
+// fit on the SMs (forward: 48 KB shared memory and 64 tensor-memory columns a block, up to
+// four an SM; backward: 72 KB and 128 columns, up to three an SM)
+unsigned layer_grid(MpnnNet* n, int per_sm) {
+  return (unsigned)std::min<int64_t>((n->N + kTile - 1) / kTile, (int64_t)n->m->num_sms * per_sm);
+}
+
+// dynamic shared memory above 48 KB must be enabled per kernel (current device)
+cudaError_t layer_kernels_setup() {
+  cudaError_t e = cudaFuncSetAttribute(k_layer_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_layer_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
+  return e;
 }
 
 // One evaluation of the network. train: activation set ``set`` keeps every layer;
@@ -554,10 +730,10 @@ cudaError_t forward(MpnnNet* n, int set, const double* dq, const double* phi, bo
   for (int l = 0; l < kLayers; ++l) {
     const float* Hin = train ? n->H[set][l] : n->H[0][l % 2];
     float* Hout = train ? n->H[set][l + 1] : n->H[0][(l + 1) % 2];
-    k_layer_fwd<<<layer_grid(n), 32 * kWarps, 0, s>>>(N, Hin, nbr, wn, n->wbf + (size_t)l * kHid * kIn,
-                                                      n->theta + kOffLayer0 + l * kLayerSize + kHid * kIn,
-                                                      train ? n->M[set][l] : nullptr,
-                                                      train ? n->Z[set][l] : nullptr, Hout);
+    k_layer_fwd<<<layer_grid(n, 4), kTile, kFwdSmem, s>>>(N, Hin, nbr, wn, n->wbf + (size_t)l * kHid * kIn,
+                                                          n->theta + kOffLayer0 + l * kLayerSize + kHid * kIn,
+                                                          train ? n->M[set][l] : nullptr,
+                                                          train ? n->Z[set][l] : nullptr, Hout, n->m->d_status);
     count_launch();
   }
   return cudaGetLastError();
@@ -589,8 +765,8 @@ void backward_set(MpnnNet* n, int set, float sign, int row0, cudaStream_t s) {
   const int4* nbr = reinterpret_cast<const int4*>(n->m->g64.bc[n->bcset].at_nbr);
   const float4* wn = reinterpret_cast<const float4*>(n->wn);
   for (int l = kLayers - 1; l >= 0; --l) {
-    k_layer_bwd<<<layer_grid(n), 32 * kWarps, 0, s>>>(N, dHn, n->Z[set][l], n->wbf + (size_t)l * kHid * kIn,
-                                                      n->dZ, dHo, n->G);
+    k_layer_bwd<<<layer_grid(n, 3), kTile, kBwdSmem, s>>>(N, dHn, n->Z[set][l], n->wbf + (size_t)l * kHid * kIn,
+                                                          n->dZ, dHo, n->G, n->m->d_status);
     k_msg_add<<<grid_n(N * 32), 256, 0, s>>>(N, n->G, nbr, wn, dHo);
     k_layer_wgrad<<<G, 256, 0, s>>>(N, n->dZ, n->H[set][l], n->M[set][l], kOffLayer0 + l * kLayerSize, part);
     count_launch(3);
@@ -643,6 +819,7 @@ fvgb_status fvgb_mpnn_create(fvgb_mesh m, int32_t bcset, fvgb_mpnn* out) {
     net_release(n);
     return st;
   };
+  if ((e = layer_kernels_setup())) return fail("tensor-core kernel attributes");
   if ((e = nalloc(n, &n->theta, kNParams))) return fail("allocation");
   if ((e = nalloc(n, &n->adam_m, kNParams))) return fail("allocation");
   if ((e = nalloc(n, &n->adam_v, kNParams))) return fail("allocation");

@@ -516,7 +516,7 @@ template <typename T, int NV, int MODE>
 __global__ void __launch_bounds__(1024)
 k_update(int64_t N, const int32_t* __restrict__ cell_face, const T* __restrict__ flux,
          const T* __restrict__ inv_vol, const T* __restrict__ vol, const T* __restrict__ src,
-         const T* base, T adt, const T* __restrict__ aux, T* out, T* out2) {
+         const T* base, T adt, const T* __restrict__ aux, T* out, T* out2, int* __restrict__ status) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     T acc = T(0);  // sum over faces entering i minus faces leaving i
@@ -526,12 +526,20 @@ k_update(int64_t N, const int32_t* __restrict__ cell_face, const T* __restrict__
       acc += e >= 0 ? -flux[e] : flux[~e];
     }
     if constexpr (MODE == kResidual) {
-      out[i] = acc * inv_vol[i] + (src ? src[i] : T(0));
+      const T r = acc * inv_vol[i] + (src ? src[i] : T(0));
+      out[i] = r;
+      if (!isfinite(r)) atomicOr(status, 1);     // latched for fvgb_sync
     } else if constexpr (MODE == kStep) {
       const T s = src ? src[i] : T(0);
       const T r = acc * inv_vol[i] + s;
-      out[i] = base[i] + adt * r;
-      if (out2) out2[i] += adt * s;
+      const T v = base[i] + adt * r;
+      out[i] = v;
+      if (out2) {
+        const T w = out2[i] + adt * s;
+        out2[i] = w;
+        if (!isfinite(w)) atomicOr(status, 1);
+      }
+      if (!isfinite(v)) atomicOr(status, 1);
     } else if constexpr (MODE == kPoissonApply) {
       out[i] = acc;                       // A x = -mu Lap_h x
     } else if constexpr (MODE == kPoissonResidual) {
@@ -543,10 +551,36 @@ k_update(int64_t N, const int32_t* __restrict__ cell_face, const T* __restrict__
 }
 
 // ---- streamer cell physics (eq. 10 with v = -mu E, alpha = A exp(-B/|E|)) --------------------
+// Plasma spots (Section 4, "Streamer Branching"): the source of the spots averaged over
+// the step [t, t + dt], sum_k S_k exp(-|x - c_k|^2 / sigma_k^2) |[t, t + dt] n window_k| / dt,
+// in FP64 at the cell centre (FP32 meshes: high + low parts of the centre).
+template <typename T, int D>
+__device__ __forceinline__ double spot_term(const SpotArgs& sp, const T* __restrict__ cen,
+                                            const T* __restrict__ cen_lo, int64_t N, int64_t i) {
+  const double t = *sp.t;
+  double add = 0.0;
+  for (int k = 0; k < sp.n; ++k) {
+    const double lo = fmax(t, sp.t_on[k]);
+    const double hi = fmin(t + sp.dt, sp.t_off[k]);
+    if (!(hi > lo)) continue;
+    const double c[3] = {sp.cx[k], sp.cy[k], sp.cz[k]};
+    double r2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const double x = (double)cen[a * N + i] + (cen_lo ? (double)cen_lo[a * N + i] : 0.0);
+      const double d = x - c[a];
+      r2 += d * d;
+    }
+    add += sp.amp[k] * exp(-r2 / sp.s2[k]) * ((hi - lo) / sp.dt);
+  }
+  return add;
+}
+
 template <typename T, int D>
 __global__ void __launch_bounds__(kThreads)
 k_cell_physics(int64_t N, const T* __restrict__ grad, const T* __restrict__ ne, T mu, T A, T B,
-               T* __restrict__ E, T* __restrict__ vel, T* __restrict__ src) {
+               T* __restrict__ E, T* __restrict__ vel, T* __restrict__ src, const T* __restrict__ cen,
+               const T* __restrict__ cen_lo, const SpotArgs sp) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   T e[3], en2 = T(0);
@@ -559,7 +593,13 @@ k_cell_physics(int64_t N, const T* __restrict__ grad, const T* __restrict__ ne, 
     vel[a * N + i] = -mu * e[a];
     if (E) E[a * N + i] = e[a];
   }
-  src[i] = alpha * mu * en * ne[i];
+  T S = alpha * mu * en * ne[i];
+  if (sp.n > 0) S += (T)spot_term<T, D>(sp, cen, cen_lo, N, i);
+  src[i] = S;
+}
+
+__global__ void k_time(double* __restrict__ t, int set, double v) {
+  if (threadIdx.x == 0) t[0] = set ? v : t[0] + v;
 }
 
 template <typename T>
@@ -799,7 +839,7 @@ cudaError_t launch_update(fvgb_mesh_s* m, int mode, const T* flux, const T* src,
   const int tb = m->tune[kTuneUpdate].threads;
 #define FVGB_UPD(NV, MD)                                                                 \
   k_update<T, NV, MD><<<gr, tb, 0, s>>>(t.N, t.cell_face, flux, g.inv_vol, g.vol, src, \
-                                              base, (T)adt, aux, out, out2)
+                                              base, (T)adt, aux, out, out2, m->d_status)
 #define FVGB_UPD_MODES(NV)                                       \
   switch (mode) {                                                \
     case kResidual: FVGB_UPD(NV, kResidual); break;              \
@@ -817,12 +857,37 @@ cudaError_t launch_update(fvgb_mesh_s* m, int mode, const T* flux, const T* src,
 
 template <typename T>
 cudaError_t launch_cell_physics(fvgb_mesh_s* m, const T* grad, const T* ne, double mu, double A,
-                                double B, T* E, T* vel, T* src, cudaStream_t s) {
+                                double B, T* E, T* vel, T* src, const SpotArgs& sp, cudaStream_t s) {
   const TopoDev& t = m->topo;
+  const GeoDev<T>& g = geo_of<T>(m);
   if (t.dim == 3)
-    k_cell_physics<T, 3><<<grid_for(t.N), kThreads, 0, s>>>(t.N, grad, ne, (T)mu, (T)A, (T)B, E, vel, src);
+    k_cell_physics<T, 3><<<grid_for(t.N), kThreads, 0, s>>>(t.N, grad, ne, (T)mu, (T)A, (T)B, E, vel, src,
+                                                            g.cen, g.cen_lo, sp);
   else
-    k_cell_physics<T, 2><<<grid_for(t.N), kThreads, 0, s>>>(t.N, grad, ne, (T)mu, (T)A, (T)B, E, vel, src);
+    k_cell_physics<T, 2><<<grid_for(t.N), kThreads, 0, s>>>(t.N, grad, ne, (T)mu, (T)A, (T)B, E, vel, src,
+                                                            g.cen, g.cen_lo, sp);
+  count_launch();
+  return cudaGetLastError();
+}
+
+SpotArgs spot_args(fvgb_mesh_s* m, const fvgb_streamer_params* p) {
+  SpotArgs a;
+  a.n = p->n_spot;
+  for (int k = 0; k < p->n_spot; ++k) {
+    const fvgb_spot& q = p->spots[k];
+    a.cx[k] = q.centre[0]; a.cy[k] = q.centre[1]; a.cz[k] = q.centre[2];
+    a.amp[k] = q.amplitude;
+    a.s2[k] = q.sigma * q.sigma;
+    a.t_on[k] = q.t_on;
+    a.t_off[k] = q.t_on + q.duration;
+  }
+  a.dt = p->dt;
+  a.t = m->d_time;
+  return a;
+}
+
+cudaError_t launch_time(fvgb_mesh_s* m, bool set, double v, cudaStream_t s) {
+  k_time<<<1, 32, 0, s>>>(m->d_time, set ? 1 : 0, v);
   count_launch();
   return cudaGetLastError();
 }
@@ -879,18 +944,46 @@ cudaError_t launch_charge_hist(fvgb_mesh_s* m, const void* ne, const void* ni, b
   return cudaGetLastError();
 }
 
-// phi_old <- phi and, when extrapolating, phi <- 2 phi - phi_old (linear in time)
-__global__ void k_extrapolate(int64_t N, int extrap, double* __restrict__ phi, double* __restrict__ phi_old) {
+// phi_old2 <- phi_old, phi_old <- phi and, when extrapolating, phi <- 2 phi - phi_old
+// (linear in time)
+__global__ void k_extrapolate(int64_t N, int extrap, double* __restrict__ phi, double* __restrict__ phi_old,
+                              double* __restrict__ phi_old2) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const double o = phi[i];
-    if (extrap) phi[i] = 2.0 * o - phi_old[i];
+    const double po = phi_old[i];
+    if (extrap) phi[i] = 2.0 * o - po;
+    phi_old2[i] = po;
     phi_old[i] = o;
   }
 }
 
-cudaError_t launch_extrapolate(fvgb_mesh_s* m, bool extrap, double* phi, double* phi_old, cudaStream_t s) {
+cudaError_t launch_extrapolate(fvgb_mesh_s* m, bool extrap, double* phi, double* phi_old, double* phi_old2,
+                               cudaStream_t s) {
   const int64_t N = m->topo.N;
-  k_extrapolate<<<grid_for(N), kThreads, 0, s>>>(N, extrap ? 1 : 0, phi, phi_old);
+  k_extrapolate<<<grid_for(N), kThreads, 0, s>>>(N, extrap ? 1 : 0, phi, phi_old, phi_old2);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Training pair of the last streamer step from the warm-start history: which = 0 gives
+// (dq, phi^n, phi^{n+1} - phi^n), which = 1 gives (d2q, phi^n, phi^{n+1} - 2 phi^n + phi^{n-1}).
+__global__ void k_history_pair(int64_t N, int which, const double* __restrict__ phi,
+                               const double* __restrict__ phi_old, const double* __restrict__ phi_old2,
+                               const double* __restrict__ dq, const double* __restrict__ d2q,
+                               double* __restrict__ q_out, double* __restrict__ p_out, double* __restrict__ d_out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double po = phi_old[i];
+    q_out[i] = which ? d2q[i] : dq[i];
+    p_out[i] = po;
+    d_out[i] = which ? (phi[i] - po) - (po - phi_old2[i]) : phi[i] - po;
+  }
+}
+
+cudaError_t launch_history_pair(fvgb_mesh_s* m, int which, const double* phi, double* q_out, double* p_out,
+                                double* d_out, cudaStream_t s) {
+  const int64_t N = m->topo.N;
+  k_history_pair<<<grid_for(N), kThreads, 0, s>>>(N, which, phi, m->phi_old, m->phi_old2, m->dq, m->d2q,
+                                                  q_out, p_out, d_out);
   count_launch();
   return cudaGetLastError();
 }
@@ -969,7 +1062,8 @@ cudaError_t launch_nonfinite_check(const double* x, int64_t n, int* flag, cudaSt
   template cudaError_t launch_update<T>(fvgb_mesh_s*, int, const T*, const T*, const T*,      \
                                         double, const T*, T*, T*, cudaStream_t);              \
   template cudaError_t launch_cell_physics<T>(fvgb_mesh_s*, const T*, const T*, double,       \
-                                              double, double, T*, T*, T*, cudaStream_t);
+                                              double, double, T*, T*, T*, const SpotArgs&,    \
+                                              cudaStream_t);
 FVGB_INST(double)
 FVGB_INST(float)
 #undef FVGB_INST

@@ -13,8 +13,9 @@
 // blocks take the same decisions and results are bitwise reproducible for a given grid.
 // The same decomposition gives the per-part norms of the outer loop (k_part_sumsq).
 //
-// Grid-wide barriers are bounded: a wait longer than one second sets a status word and
-// every block leaves; the host reports FVGB_ETIMEOUT.
+// Grid-wide barriers are bounded: a wait longer than one second (or the limit set by the
+// test hook fvgb_test_barrier) sets a status word and every block leaves; the host
+// reports FVGB_ETIMEOUT.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -22,7 +23,7 @@
 namespace fvgb {
 namespace {
 
-constexpr unsigned long long kBarrierTimeoutNs = 1000000000ull;
+constexpr unsigned long long kBarrierTimeoutNs = 1000000000ull;   // default wait limit
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -34,8 +35,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // launch is passed once the counter (zeroed before the launch) reaches r * nblocks, so
 // the last arrival itself releases the waiting blocks (no reset, no second word).
 // ``target`` is the caller's running count. Returns false when any block gave up
-// (status set), in which case the caller leaves.
-__device__ bool grid_barrier(Barrier* bar, unsigned nblocks, unsigned& target) {
+// (status set), in which case the caller leaves. ``skip`` (test hook only) leaves out this
+// block's arrival, so that the other blocks' waits run out.
+__device__ bool grid_barrier(Barrier* bar, unsigned nblocks, unsigned& target, bool skip,
+                             unsigned long long limit_ns) {
   __shared__ int ok;
   __syncthreads();
   target += nblocks;
@@ -43,13 +46,13 @@ __device__ bool grid_barrier(Barrier* bar, unsigned nblocks, unsigned& target) {
     volatile unsigned* vcount = &bar->count;
     volatile int* vstatus = &bar->status;
     __threadfence();
-    atomicAdd(&bar->count, 1u);
+    if (!skip) atomicAdd(&bar->count, 1u);
     int good = 1;
     if ((int)(*vcount - target) < 0) {
       const unsigned long long t0 = global_ns();
       while ((int)(*vcount - target) < 0) {
         if (*vstatus != 0) { good = 0; break; }
-        if (global_ns() - t0 > kBarrierTimeoutNs) { atomicExch(&bar->status, 1); good = 0; break; }
+        if (global_ns() - t0 > limit_ns) { atomicExch(&bar->status, 1); good = 0; break; }
         __nanosleep(32);
       }
     }
@@ -113,6 +116,8 @@ struct SolveArgs {
   int maxit_inner;
   int* out_inner;           // [P] iterations per part
   int* out_status;          // [0]: 0 ok, 6 non-finite / breakdown; [1]: iterations run
+  int skip_block;           // test hook: this block never arrives at a barrier (-1: none)
+  unsigned long long barrier_ns;  // limit of a barrier wait
 };
 
 // Sum the per-sub-chunk partials of K quantities into per-part totals (shared memory
@@ -307,7 +312,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
       a.cx[i] = T(0);
     }
   }
-  if (!grid_barrier(a.bar, G, target)) goto done;
+  if (!grid_barrier(a.bar, G, target, a.skip_block == (int)blockIdx.x, a.barrier_ns)) goto done;
   for (int sc = sc0; sc < sc1; ++sc) {
     const int p = a.sc_part[sc];
     T l0 = T(0), l1 = T(0);
@@ -322,7 +327,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
     const double t1 = block_sum((double)l1, sh);
     if (threadIdx.x == 0) { a.buf[sc] = t0; a.buf[a.n_sc + sc] = t1; }
   }
-  if (!grid_barrier(a.bar, G, target)) goto done;
+  if (!grid_barrier(a.bar, G, target, a.skip_block == (int)blockIdx.x, a.barrier_ns)) goto done;
   part_totals<T, 2>(a, a.buf, tot, stage);
   if (threadIdx.x == 0) s_flag = 0;
   __syncthreads();
@@ -351,7 +356,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
         buf[sc] = 0.0;
       }
     }
-    if (!grid_barrier(a.bar, G, target)) goto done;
+    if (!grid_barrier(a.bar, G, target, a.skip_block == (int)blockIdx.x, a.barrier_ns)) goto done;
     part_totals<T, 1>(a, buf, tot, stage);
     ++total_its;
     if (threadIdx.x == 0) s_flag = 0;
@@ -379,7 +384,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
         buf[sc] = 0.0;
       }
     }
-    if (!grid_barrier(a.bar, G, target)) goto done;
+    if (!grid_barrier(a.bar, G, target, a.skip_block == (int)blockIdx.x, a.barrier_ns)) goto done;
     part_totals<T, 1>(a, buf, tot, stage);
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
       if (s_cg[p] != 0) continue;
@@ -467,6 +472,8 @@ cudaError_t launch_cg(fvgb_mesh_s* m, int bcset, const double* r, double inner_r
   a.maxit_inner = maxit;
   a.out_inner = pd.out_inner;
   a.out_status = m->d_cg_info;
+  a.skip_block = m->test_skip_block;
+  a.barrier_ns = m->test_barrier_ns > 0 ? m->test_barrier_ns : kBarrierTimeoutNs;
   cudaError_t e = cudaMemsetAsync(m->barrier, 0, sizeof(Barrier), s);
   if (e != cudaSuccess) return e;
   void* args[] = {&a};
