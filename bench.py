@@ -1,7 +1,11 @@
 """Benchmark of the GPU finite-volume hot path: one streamer step = one Poisson solve to
 relative residual 1e-8 + least-squares field + upwind/diamond transport update of n_e
-and n_i, on the 3D electron drift-diffusion + Poisson workload (unit cube, 50^3
-jittered hexes x 6 Kuhn tetrahedra = 750,000 cells, FP64 plain method).
+and n_i, on the 3D electron drift-diffusion + Poisson workload of the learned-warm-start
+configuration (unit cube, 100^3 jittered hexes x 6 Kuhn tetrahedra = 6,000,000 cells),
+timed in the FP64 plain method (CG from the previous potential); beside it, on the same
+mesh from the same state to the same residual, mixed precision, the learned warm start
+(network trained on 2,000 solver-generated pairs from 20 seed positions) and the other
+variants, with their errors against the FP64 run.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -18,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -25,17 +30,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-updates/s per FV step + Poisson, learned vs plain CG at rel. residual 1e-8"
 UNIT = "cell-updates/s"
-K_MESH = 50                 # 6 * 50^3 = 750,000 cells
-MESH_SEED = 201
+K_MESH = 100                # 6 * 100^3 = 6,000,000 cells
+MESH_SEED = 301
+K_SMALL, SMALL_SEED = 50, 201   # the 750,000-cell FP64 workload, run as a labelled variant
 RTOL = 1e-8
 INNER_RTOL = 0.2            # inner CG reduction per outer step (measured fastest of 0.03-0.5)
 ORACLE_SAMPLE_K = 12        # 10,368 cells, same recipe
-TRAIN_SEEDS, TRAIN_STEPS, TRAIN_EPOCHS = 8, 50, 5   # learned warm start training set
-WORKLOAD = ("3D electron drift-diffusion + Poisson, FP64 plain method: unit cube, 50^3 "
-            "jittered hexes x 6 Kuhn tets (750,000 cells), seed at (0.5,0.5,0.9), V = 12.5 kV, "
-            "Poisson to rel. residual 1e-8 each step (FP64 defect correction + FP64 inner CG "
-            "on the two-point operator reducing its residual 5x per outer step, warm start from "
-            "the previous potential)")
+N_SEEDS, N_HELD_OUT, TRAIN_STEPS = 20, 2, 100   # 20 x 100 = 2,000 (charge, phi) pairs
+HELD_OUT_STEPS = 40
+WORKLOAD = ("3D electron drift-diffusion + Poisson, FP64 plain method, on the 6M-cell mesh of the "
+            "learned-warm-start workload: unit cube, 100^3 jittered hexes x 6 Kuhn tets (6,000,000 "
+            "cells, mesh seed 301), seed at (0.5,0.5,0.9), V = 12.5 kV, Poisson to rel. residual 1e-8 "
+            "each step (FP64 defect correction + FP64 inner CG on the two-point operator reducing its "
+            "residual 5x per outer step, warm start from the previous potential)")
 
 
 def workload_text(args):
@@ -53,7 +60,7 @@ def workload_text(args):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
@@ -61,6 +68,11 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-transport", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip training the learned warm start (and its variants)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="time the headline step only (no variants, e2e, ensemble, transport or "
+                         "CPU baseline); for profiling")
     ap.add_argument("--inner", type=int, default=0,
                     help="inner solve of the headline run: 0 conjugate gradients (default), "
                          "k > 0 k multigrid V-cycles per outer step")
@@ -132,7 +144,8 @@ def reference_arm(args, world, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
         "config": {"workload": WORKLOAD, "sample_cells": res["cells"]},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+                         "kind": "oracle",
                          "sample": oracle_sample_text(ORACLE_SAMPLE_K, args.steps, res["cells"])},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -150,11 +163,11 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="fvgb_clocks_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}",
                                           f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
@@ -169,6 +182,7 @@ class ClockSampler:
         self.proc.wait()
         self.fh.close()
         rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
@@ -208,10 +222,11 @@ TRANSPORT_K = 100          # 6 * 100^3 = 6,000,000 cells: every array well above
 TRANSPORT_SEED = 301
 
 
-def transport_kernels(capi, device, torch, stream, flush, precs, reps=10, warm=3):
+def transport_kernels(capi, device, torch, stream, flush, precs, meshes=None, reps=10, warm=3):
     """The transport operators on the 6M-cell mesh, each timed alone between CUDA events
     with L2 flushed before every repetition; achieved GB/s from the algorithmic bytes
-    (each array element counted once, gathered neighbour values as cache hits)."""
+    (each array element counted once, gathered neighbour values as cache hits).
+    ``meshes`` ({"fp32": ..., "fp64": ...}) reuses uploaded meshes of that mesh."""
     import numpy as np
     from synth.workloads import StreamerCase, streamer_mesh
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -221,8 +236,10 @@ def transport_kernels(capi, device, torch, stream, flush, precs, reps=10, warm=3
     out = {"mesh": f"unit cube, {TRANSPORT_K}^3 x 6 Kuhn tets, seed {TRANSPORT_SEED}",
            "peak_GBps": hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
            "l2": "flushed before each repetition (256 MiB write, untimed)"}
+    meshes = meshes or {}
     for prec in precs:
-        dm = device.DeviceMesh(mesh, [case.bc_ne(), case.bc_phi()], prec=prec)
+        own = prec not in meshes
+        dm = device.DeviceMesh(mesh, [case.bc_ne(), case.bc_phi()], prec=prec) if own else meshes[prec]
         N, F, V, NN = dm.n_cell, dm.n_face, dm.n_vert, dm.n_nbr
         w = 8 if prec == "fp64" else 4
         rng = np.random.default_rng(1)
@@ -278,7 +295,8 @@ def transport_kernels(capi, device, torch, stream, flush, precs, reps=10, warm=3
             r[name] = {"ms": med, "algorithmic_bytes": nbytes, "GBps": nbytes / med / 1e6,
                        "frac_of_measured_hbm": nbytes / med / 1e6 / hbm}
         out[prec] = r
-        dm.free()
+        if own:
+            dm.free()
     return out
 
 
@@ -365,12 +383,27 @@ def gpu_arm(args, world, rank, local):
         print(json.dumps(transport_kernels(capi, device, torch, torch.cuda.current_stream(),
                                            flush, precs)), flush=True)
         return
+    t_start = time.time()
+
+    def log(msg):
+        print(f"[bench {time.time() - t_start:7.1f} s] {msg}", file=sys.stderr, flush=True)
+
     case = StreamerCase()
     mesh = streamer_mesh(K_MESH, MESH_SEED)
     mixed = args.prec == "mixed"
-    dm = device.DeviceMesh(mesh, [case.bc_ne(), case.bc_phi()], prec=args.prec)
-    if mixed:
-        capi.fvgb_autotune(dm.handle)
+    bcs = [case.bc_ne(), case.bc_phi()]
+    meshes = {}
+
+    def mesh_for(prec):
+        """The workload mesh uploaded once per precision ("fp64" or "mixed")."""
+        if prec not in meshes:
+            meshes[prec] = device.DeviceMesh(mesh, bcs, prec=prec)
+            if prec != "fp64":
+                capi.fvgb_autotune(meshes[prec].handle)
+            log(f"uploaded the {prec} mesh")
+        return meshes[prec]
+
+    dm = mesh_for("mixed" if mixed else "fp64")
     N = dm.n_cell
     ne0, ni0 = case.initial(mesh)
     dt = case.dt(1.0 / K_MESH)
@@ -389,6 +422,7 @@ def gpu_arm(args, world, rank, local):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    capi.fvgb_streamer_reset(dm.handle)
     for _ in range(args.warmup):
         capi.fvgb_streamer_step(dm.handle, sp, ne, ni, phi, None, 1)
     capi.fvgb_stats_enable(dm.handle, True)
@@ -408,19 +442,23 @@ def gpu_arm(args, world, rank, local):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     stats = capi.fvgb_stats_get(dm.handle, reset=True)
-    # the CG launches do not include the L2 flush: the library syncs inside the step
+    capi.fvgb_stats_enable(dm.handle, False)
     total_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
     value = world * N * args.steps / (total_ms / 1e3)
+    log(f"headline {total_ms / args.steps:.2f} ms/step")
 
     # ---- roofline of the dominant kernel: the persistent CG kernel ------------------------
-    # GB300 runs FP64 at ~1/69 of the FP32 rate; ncu shows the FP64 kernel bound by the FP64
-    # pipe with its working set in L2, so it is reported against the FP64 ALU peak
-    # (nominal 1.25 TFLOP/s = SMs x 2 FP64 FMA/clk x 2 flop x max clock). The FP32 kernel of
-    # the mixed run is reported against the measured HBM copy bandwidth.
+    # Per CG iteration and cell: operator (ELL-4 indices 16 B, 4 coefficients, diagonal, r and
+    # its 4 neighbours as cache hits, p, q read and written) and the x/r phase (x, p, r, q
+    # read, x, r written): 16 w + 16 bytes; flops 9 (operator) + 12 (four updates, two dots).
+    # Per launch add the initial pass (r = rhs, zeroed p, q, x) and the first operator apply.
+    # At 6M cells the iteration's working set (~860 MB FP64) is far above L2, so both the HBM
+    # and the FP64-pipe views apply; the line reports the one with the larger fraction as the
+    # bound and the other beside it.
     w = 4 if mixed else 8
     its, launches = stats["cg_iterations"], max(stats["cg_launches"], 1)
     per_launch_its = its / launches
@@ -431,89 +469,106 @@ def gpu_arm(args, world, rank, local):
     peak_tflops = props.multi_processor_count * 2 * 2 * 2.070e9 / 1e12
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     hbm = float(peaks["hbm_gbs"])
-    achieved = flops_per_launch / avg_launch_s / 1e12 if avg_launch_s > 0 else None
-    achieved_gbs = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else None
+    ok = avg_launch_s > 0 and args.inner == 0          # multigrid runs launch no CG kernel
+    achieved_tf = flops_per_launch / avg_launch_s / 1e12 if ok else None
+    achieved_gbs = bytes_per_launch / avg_launch_s / 1e9 if ok else None
     kname = "k_cg<float,4>" if mixed else "k_cg<double,4>"
     prof = profile_traffic(kname, source_hash("solver.cu"))
     traffic = prof["dram_bytes_per_launch"] if prof else None
-    if args.inner > 0:          # no CG launches: the CG roofline does not apply
-        achieved = achieved_gbs = None
-    common = {"kernel": kname, "traffic": traffic, "flops_per_launch": flops_per_launch,
+    common = {"kernel": kname, "traffic": traffic,
+              "traffic_source": prof.get("source") if prof else None,
               "avg_launch_ms": avg_launch_s * 1e3, "iterations_per_launch": per_launch_its,
-              "cg_share_of_step": stats["cg_ms"] / total_ms if world == 1 else None}
-    if mixed:
-        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved_gbs / hbm if achieved_gbs else None,
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-                    "algorithmic_bytes_per_launch": bytes_per_launch, **common}
+              "cg_share_of_step": stats["cg_ms"] / total_ms if world == 1 else None,
+              "timing": "CUDA events on the launching stream around every CG launch of the timed steps"}
+    hbm_view = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": achieved_gbs / hbm if ok else None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                "algorithmic_bytes_per_launch": bytes_per_launch}
+    alu_view = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved_tf / peak_tflops if ok else None,
+                "peak_source": "derived FP64 peak: SMs x 2 FMA/clk x 2 flop x 2.07 GHz (nominal rate; "
+                               "MEASURED_PEAKS.json has no FP64 figure)",
+                "flops_per_launch": flops_per_launch}
+    if mixed or not ok or hbm_view["frac"] >= alu_view["frac"]:
+        roofline = {**hbm_view, **common, "alu_view": None if mixed else alu_view}
     else:
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                    "frac": achieved / peak_tflops if achieved else None,
-                    "peak_source": "derived FP64 peak: SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
-                    **common,
-                    "hbm_view": {"algorithmic_bytes_per_launch": bytes_per_launch,
-                                 "achieved_GBps": achieved_gbs, "peak_GBps": hbm,
-                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}}
+        roofline = {**alu_view, **common, "hbm_view": hbm_view}
+
+    headline_only = args.headline_only
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    # ---- learned warm start (config: 2,000 (charge, phi) pairs from 20 seeded streamer
+    # runs of the plain solver on this mesh; 18 seed positions train, 2 are held out) -------
+    nets, learned_info = None, None
+    want_learned = world == 1 and not args.no_variants and not args.no_learned and not headline_only
+    if want_learned:
+        from paper_2203_00925_gb300 import learned
+        t_train0 = time.time()
+        rng = np.random.default_rng(4000)
+        seeds = [StreamerCase(centre=(rng.uniform(0.3, 0.7), rng.uniform(0.3, 0.7), rng.uniform(0.8, 0.95)))
+                 for _ in range(N_SEEDS)]
+        train_cases, held_out = seeds[:N_SEEDS - N_HELD_OUT], seeds[N_SEEDS - N_HELD_OUT:]
+        dmx = mesh_for("mixed")
+        gen = capi.solve_opts(rtol=RTOL, inner_rtol=INNER_RTOL, prec=capi.FVGB_FP32, inner=2)
+        nets, learned_info = learned.train_streaming(
+            dmx, mesh, train_cases, dt, TRAIN_STEPS, gen, case.V, log=log)
+        learned_info["pairs_generated"] = N_SEEDS * TRAIN_STEPS
+        learned_info["seed_positions"] = {"train": len(train_cases), "held_out": len(held_out),
+                                          "stream": "numpy default_rng(4000), uniform [0.3,0.7]^2 x [0.8,0.95]"}
+        learned_info["train_s"] = time.time() - t_train0
+        log(f"trained the networks in {learned_info['train_s']:.1f} s")
+        # held-out seed positions: the solves started from the learned guess against the same
+        # starts without it (mixed precision, host-driven steps, every solve to 1e-8)
+        ho = {}
+        for name, kw in (("previous_phi", {}), ("learned", {"net": nets[False]}),
+                         ("extrapolated", {"extrapolate": True}),
+                         ("learned_extrapolated", {"net": nets[True], "extrapolate": True})):
+            tot = {"inner": 0, "outer": 0, "ms": 0.0, "max_rel_res": 0.0, "accepted_steps": 0, "steps": 0}
+            for c in held_out:
+                r = learned.held_out_run(dmx, mesh, c, dt, HELD_OUT_STEPS, capi.solve_opts(
+                    rtol=RTOL, inner_rtol=INNER_RTOL, prec=capi.FVGB_FP32), V=case.V, **kw)
+                for key in ("inner", "outer", "ms", "accepted_steps", "steps"):
+                    tot[key] += r[key]
+                tot["max_rel_res"] = max(tot["max_rel_res"], r["max_rel_res"])
+            ho[name] = tot
+        ho["inner_ratio_learned_vs_previous_phi"] = ho["learned"]["inner"] / max(ho["previous_phi"]["inner"], 1)
+        ho["inner_ratio_learned_extrapolated_vs_extrapolated"] = (
+            ho["learned_extrapolated"]["inner"] / max(ho["extrapolated"]["inner"], 1))
+        ho["note"] = (f"{len(held_out)} held-out seed positions x {HELD_OUT_STEPS} steps (steps 3.. counted), "
+                      "mixed precision, host-driven; inner = CG iterations of the inner solves; "
+                      "accepted_steps = steps whose learned start passed the residual check")
+        learned_info["held_out"] = ho
+        log("held-out evaluation done")
 
     # ---- variants on the same workload, same steps from the same initial state, all to the
-    # same rtol: graph mode, mixed precision, learned warm start, and all three together;
-    # errors against the plain FP64 run -----------------------------------------------------
+    # same rtol; errors against the plain FP64 run -----------------------------------------
     variants = None
-    if world == 1 and not args.no_variants:
-        from paper_2203_00925_gb300 import learned
+    if world == 1 and not args.no_variants and not headline_only:
         ref_ne = dm.to_host(ne)
         ref_phi = dm.to_host(phi)
         ref_ne_total = capi.fvgb_integral(dm.handle, ne)
         ref_q = capi.fvgb_integral(dm.handle, ni) - ref_ne_total
-        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
         plain_inner = sum(i["inner_its_total"] for i in infos) / len(infos)
 
-        # learned warm start: trained on this mesh from plain runs of other seed positions
-        # (TRAIN_SEEDS x TRAIN_STEPS), not the benchmark's own seed
-        t_train0 = time.time()
-        rng = np.random.default_rng(4000)
-        tcases = [StreamerCase(centre=(rng.uniform(0.3, 0.7), rng.uniform(0.3, 0.7), rng.uniform(0.8, 0.95)))
-                  for _ in range(TRAIN_SEEDS)]
-        pairs_p, pairs_x = [], []
-        for c in tcases:
-            _, pp, px = learned.streamer_run(dm, c, mesh, dt, TRAIN_STEPS, capi.solve_opts(rtol=RTOL, inner_rtol=INNER_RTOL),
-                                             record=True)
-            pairs_p += pp
-            pairs_x += px
-
-        def fit(pairs):
-            net_tr = capi.fvgb_mpnn_create(dm.handle, 1)
-            capi.fvgb_mpnn_set_params(net_tr, learned.init_params(0))
-            sc = learned.scales_for(pairs, case.V, dm.n_cell)
-            capi.fvgb_mpnn_set_scales(net_tr, case.V, *sc)
-            for ep in range(TRAIN_EPOCHS):
-                learned.train(net_tr, pairs, epochs=1, lr=1e-3 if ep < TRAIN_EPOCHS - 1 else 3e-4, seed=ep)
-            th = capi.fvgb_mpnn_get_params(net_tr)
-            capi.fvgb_mpnn_free(net_tr)
-            return th, sc
-
-        nets = {False: fit(pairs_p), True: fit(pairs_x)}
-        n_pairs = (len(pairs_p), len(pairs_x))
-        del pairs_p, pairs_x
-        train_s = time.time() - t_train0
-
-        def run_variant(prec, graph, warm, extrap=False, inner=0, recon=0, stages=1):
-            dmv = device.DeviceMesh(mesh, [case.bc_ne(), case.bc_phi()], prec=prec)
-            if prec != "fp64":
-                capi.fvgb_autotune(dmv.handle)
+        def run_variant(prec, graph, warm=None, extrap=False, inner=0, recon=0, stages=1,
+                        dmv=None, meshv=None, casev=None, dtv=None):
+            dmv = dmv or mesh_for(prec)
+            meshv, casev, dtv = meshv or mesh, casev or case, dtv or dt
             net = None
-            if warm:
+            if warm is not None:
                 theta, scales = nets[extrap]
                 net = capi.fvgb_mpnn_create(dmv.handle, 1)
                 capi.fvgb_mpnn_set_params(net, theta)
-                capi.fvgb_mpnn_set_scales(net, case.V, *scales)
+                capi.fvgb_mpnn_set_scales(net, casev.V, *scales)
             spv = capi.streamer_params(
-                mu=case.mu, A=case.A, B=case.B, De=case.De, dt=dt, warm=net, extrapolate=extrap,
+                mu=casev.mu, A=casev.A, B=casev.B, De=casev.De, dt=dtv, warm=net, extrapolate=extrap,
                 recon=recon, stages=stages,
                 solve=capi.solve_opts(rtol=RTOL, inner_rtol=INNER_RTOL, inner=inner,
                                       prec=capi.FVGB_FP64 if prec == "fp64" else capi.FVGB_FP32))
-            nev, niv = dmv.to_device(ne0), dmv.to_device(ni0)
-            phiv = torch.zeros(N, dtype=torch.float64, device="cuda")
+            a0, b0 = casev.initial(meshv)
+            nev, niv = dmv.to_device(a0), dmv.to_device(b0)
+            phiv = torch.zeros(dmv.n_cell, dtype=torch.float64, device="cuda")
+            capi.fvgb_streamer_reset(dmv.handle)
             capi.fvgb_set_graph_mode(dmv.handle, graph)
             capi.fvgb_streamer_step(dmv.handle, spv, nev, niv, phiv, None, args.warmup)
             barrier()
@@ -523,53 +578,62 @@ def gpu_arm(args, world, rank, local):
             e1.record(stream)
             barrier()
             ms = e0.elapsed_time(e1)
-            q = capi.fvgb_integral(dmv.handle, niv) - capi.fvgb_integral(dmv.handle, nev)
-            out = {"ms_per_step": ms / args.steps, "value": N * args.steps / (ms / 1e3),
-                   "speedup_vs_plain_fp64": total_ms / ms,
+            capi.fvgb_set_graph_mode(dmv.handle, False)
+            out = {"ms_per_step": ms / args.steps, "value": dmv.n_cell * args.steps / (ms / 1e3),
                    "max_rel_res": max(i["rel_res"] for i in infv),
                    "outer_its_per_step": sum(i["outer_its"] for i in infv) / len(infv),
-                   "inner_cg_its_per_step": sum(i["inner_its_total"] for i in infv) / len(infv),
-                   "rel_err_vs_plain_fp64": {"n_e": rel(dmv.to_host(nev), ref_ne),
-                                             "phi": rel(dmv.to_host(phiv), ref_phi),
-                                             "total_charge_over_total_electrons": abs(q - ref_q) / abs(ref_ne_total)}}
+                   "inner_its_per_step": sum(i["inner_its_total"] for i in infv) / len(infv)}
+            if meshv is mesh:
+                q = capi.fvgb_integral(dmv.handle, niv) - capi.fvgb_integral(dmv.handle, nev)
+                out["speedup_vs_plain_fp64"] = total_ms / ms
+                out["rel_err_vs_plain_fp64"] = {
+                    "n_e": rel(dmv.to_host(nev), ref_ne), "phi": rel(dmv.to_host(phiv), ref_phi),
+                    "total_charge_over_total_electrons": abs(q - ref_q) / abs(ref_ne_total)}
             if net:
                 capi.fvgb_mpnn_free(net)
-            dmv.free()
+            log(f"variant {prec} graph={graph} warm={warm is not None} extrap={extrap} inner={inner}: "
+                f"{out['ms_per_step']:.2f} ms/step")
             return out
 
         variants = {
             "note": ("same initial state and step count as the headline run, every Poisson solve to "
                      "rel. residual 1e-8; each variant times all its steps in one call between CUDA "
-                     "events (no L2 flush between steps); 'extrapolated': the solve starts from "
-                     "2 phi^{n-1} - phi^{n-2}; 'learned': the network's correction of the start (from "
-                     "the previous potential, or of the extrapolation), kept per part only where it "
-                     "lowers the FP64 residual; 'multigrid': 2 smoothed-aggregation V-cycles per "
-                     "outer step instead of the inner CG; 'muscl': MUSCL reconstruction with the "
-                     "Barth-Jespersen limiter; 'rk3': three Runge-Kutta stages, a Poisson solve each; "
-                     "networks trained on this mesh from plain runs of "
-                     f"{TRAIN_SEEDS} other seed positions x {TRAIN_STEPS} steps ({n_pairs[0]} / "
-                     f"{n_pairs[1]} pairs, {TRAIN_EPOCHS} epochs of Adam, {train_s:.1f} s)"),
+                     "events (no L2 flush between steps; the 6M-cell arrays are far above L2); "
+                     "'mixed': FP32 transport and inner CG, FP64 refinement; 'graph': each step one "
+                     "CUDA graph; 'extrapolated': the solve starts from 2 phi^{n-1} - phi^{n-2}; "
+                     "'learned': the network's correction of the start (from the previous potential, "
+                     "or of the extrapolation), kept per part only where it lowers the FP64 residual; "
+                     "'multigrid': 2 smoothed-aggregation V-cycles per outer step instead of the inner "
+                     "CG; 'muscl': MUSCL reconstruction with the Barth-Jespersen limiter; 'rk3': three "
+                     "Runge-Kutta stages, a Poisson solve each"),
             "plain_fp64_inner_cg_its_per_step": plain_inner,
-            "graph_fp64": run_variant("fp64", True, False),
-            "mixed": run_variant("mixed", False, False),
-            "learned_fp64": run_variant("fp64", False, True),
-            "learned_mixed_graph": run_variant("mixed", True, True),
-            "extrapolated_fp64": run_variant("fp64", False, False, True),
-            "learned_extrapolated_fp64": run_variant("fp64", False, True, True),
-            "extrapolated_mixed_graph": run_variant("mixed", True, False, True),
-            "learned_extrapolated_mixed_graph": run_variant("mixed", True, True, True),
-            "multigrid_fp64": run_variant("fp64", False, False, False, 2),
-            "multigrid_mixed_graph": run_variant("mixed", True, False, False, 2),
-            "multigrid_extrapolated_mixed_graph": run_variant("mixed", True, False, True, 2),
-            # other discretisations of the same step (their differences from the plain run are
-            # those of the scheme, not of the solver)
-            "muscl_multigrid_extrapolated_mixed_graph": run_variant("mixed", True, False, True, 2, recon=1),
-            "rk3_multigrid_extrapolated_mixed": run_variant("mixed", False, False, True, 2, stages=3),
+            "mixed": run_variant("mixed", False),
+            "mixed_graph": run_variant("mixed", True),
+            "extrapolated_fp64": run_variant("fp64", False, extrap=True),
+            "extrapolated_mixed_graph": run_variant("mixed", True, extrap=True),
+            "multigrid_extrapolated_mixed_graph": run_variant("mixed", True, extrap=True, inner=2),
+            "muscl_multigrid_extrapolated_mixed_graph": run_variant("mixed", True, extrap=True, inner=2, recon=1),
+            "rk3_multigrid_extrapolated_mixed": run_variant("mixed", False, extrap=True, inner=2, stages=3),
         }
+        if nets is not None:
+            variants.update({
+                "learned_fp64": run_variant("fp64", False, warm=True),
+                "learned_mixed_graph": run_variant("mixed", True, warm=True),
+                "learned_extrapolated_fp64": run_variant("fp64", False, warm=True, extrap=True),
+                "learned_extrapolated_mixed_graph": run_variant("mixed", True, warm=True, extrap=True),
+            })
+        # the 750,000-cell FP64 workload (the small 3D configuration; its arrays fit in L2)
+        small = streamer_mesh(K_SMALL, SMALL_SEED)
+        dms = device.DeviceMesh(small, bcs, prec="fp64")
+        variants["plain_fp64_750k"] = run_variant("fp64", False, dmv=dms, meshv=small,
+                                                  dtv=case.dt(1.0 / K_SMALL))
+        variants["plain_fp64_750k"]["mesh"] = (f"unit cube, {K_SMALL}^3 x 6 Kuhn tets (750,000 cells), "
+                                               f"seed {SMALL_SEED}; its working set fits in L2")
+        dms.free()
 
     # ---- end to end through the public API with host buffers ------------------------------
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not headline_only:
         rt = dm.real
         hne = torch.from_numpy(ne0.copy()).to(rt).pin_memory()
         hni = torch.from_numpy(ni0.copy()).to(rt).pin_memory()
@@ -588,6 +652,7 @@ def gpu_arm(args, world, rank, local):
                 capi.fvgb_permute(dm.handle, i, u, 1, u.element_size(), False)
                 h.copy_(u, non_blocking=True)
 
+        capi.fvgb_streamer_reset(dm.handle)
         for _ in range(args.warmup):
             e2e_step()
         barrier()
@@ -606,23 +671,28 @@ def gpu_arm(args, world, rank, local):
             e2e_ms = float(t.item())
         e2e = {"value": world * N * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes}
+        log("e2e done")
 
     ensemble = None
-    if world == 1 and not args.no_ensemble:
+    if world == 1 and not args.no_ensemble and not headline_only:
         ensemble = ensemble_block(capi, device, torch, stream, args.warmup,
                                   nets if variants is not None else None)
+        log("ensemble done")
 
     transport = None
-    if world == 1 and not args.no_transport:
-        transport = transport_kernels(capi, device, torch, stream, flush, ["fp32", "fp64"])
+    if world == 1 and not args.no_transport and not headline_only:
+        transport = transport_kernels(capi, device, torch, stream, flush, ["fp32", "fp64"],
+                                      meshes={"fp32": mesh_for("mixed"), "fp64": mesh_for("fp64")})
+        log("transport kernels done")
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not headline_only:
         steps_cpu = 5
         res = run_oracle(ORACLE_SAMPLE_K, steps_cpu, 0)
         v = res["cells"] * len(res["times"]) / sum(res["times"])
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
                "sample": oracle_sample_text(ORACLE_SAMPLE_K, steps_cpu, res["cells"])}
+        log("CPU baseline done")
 
     if rank == 0:
         line = {
@@ -632,7 +702,8 @@ def gpu_arm(args, world, rank, local):
             "data": "synthetic", "config": {"workload": workload_text(args),
                        "cells": N, "faces": dm.n_face,
                        "node_neighbour_entries": dm.n_nbr, "poisson_rtol": RTOL,
-                       "l2": "flushed between timed steps (256 MiB write, untimed)",
+                       "l2": "flushed between timed steps (256 MiB write, untimed); the 6M-cell arrays "
+                             "are far above L2",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "outer_its_per_step": sum(i["outer_its"] for i in infos) / len(infos),
                        "inner_cg_its_per_step": sum(i["inner_its_total"] for i in infos) / len(infos),
@@ -640,6 +711,7 @@ def gpu_arm(args, world, rank, local):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "learned": learned_info,
             "variants": variants,
             "ensemble": ensemble,
             "transport_kernels": transport,
@@ -647,7 +719,8 @@ def gpu_arm(args, world, rank, local):
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
-    dm.free()
+    for d in meshes.values():
+        d.free()
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -339,9 +339,12 @@ typedef struct {
                             step after the first on this mesh predicts the increment of
                             phi from the change of n_i - n_e since the previous step and
                             phi, and starts the Poisson solve of every part from
-                            phi + prediction where that start has the smaller FP64
-                            residual ||b - A phi||, from phi elsewhere (the solve still
-                            converges to rtol either way) */
+                            phi + s prediction: s = 1 where that start has the smaller
+                            FP64 residual ||b - A phi||, elsewhere s = <r0, A pred> /
+                            ||A pred||^2 (r0 = b - A phi), the scale that minimises the
+                            residual along the prediction; so the start's residual is not
+                            larger than without the network (s = 0 where the prediction
+                            is 0); the solve still converges to rtol either way */
   int32_t extrapolate;   /* 1: start each solve from the linear extrapolation in time
                             2 phi^{n-1} - phi^{n-2} (after two steps on this mesh); with
                             a network, the network then predicts the extrapolation's
@@ -405,7 +408,8 @@ fvgb_status fvgb_integral(fvgb_mesh m, const void* u_dev, double* out_host, void
  *                   launching stream when timing was enabled (0 otherwise)
  *  solves, outer_its  Poisson solves and their outer refinement steps
  *  learned_starts   parts of host-driven streamer solves that evaluated a learned start
- *  learned_kept     of those, the parts whose learned start passed the residual check */
+ *  learned_kept     of those, the parts whose learned correction entered the start with a
+ *                   positive scale */
 typedef struct {
   int64_t kernel_launches;
   int64_t cg_launches;

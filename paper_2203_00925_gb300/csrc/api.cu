@@ -68,6 +68,43 @@ void build_sell(const std::vector<int32_t>& ptr, const std::vector<int32_t>& idx
   }
 }
 
+// Halo lists of the shared-memory gradient (see TopoDev): per tile of kGradTile rows, its
+// own rows, then every other cell met in the rows' padded node-neighbour lists (sorted);
+// lidx[pos] is the position of sidx[pos] in its row's tile list. Returns the longest list.
+int build_grad_tiles(int64_t N, const std::vector<int64_t>& sptr, const std::vector<int32_t>& sidx,
+                     std::vector<int32_t>& tptr, std::vector<int32_t>& tidx, std::vector<int16_t>& lidx) {
+  const int64_t ntile = (N + kGradTile - 1) / kGradTile;
+  std::vector<std::vector<int32_t>> lists(ntile);
+  lidx.assign(sidx.size(), 0);
+  int max_len = 0;
+#pragma omp parallel reduction(max : max_len)
+  {
+    std::vector<int32_t> stamp(N, -1), pos(N, 0);
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t t = 0; t < ntile; ++t) {
+      const int64_t r0 = t * kGradTile, r1 = std::min<int64_t>(N, r0 + kGradTile);
+      std::vector<int32_t>& L = lists[t];
+      for (int64_t r = r0; r < r1; ++r) { stamp[r] = (int32_t)t; L.push_back((int32_t)r); }
+      const int64_t s0 = r0 / 32, s1 = (r1 + 31) / 32;
+      const size_t own = L.size();
+      for (int64_t q = sptr[s0]; q < sptr[s1]; ++q) {
+        const int32_t j = sidx[q];
+        if (stamp[j] != (int32_t)t) { stamp[j] = (int32_t)t; L.push_back(j); }
+      }
+      std::sort(L.begin() + own, L.end());
+      for (size_t k = 0; k < L.size(); ++k) pos[L[k]] = (int32_t)k;
+      if (L.size() <= 32767)
+        for (int64_t q = sptr[s0]; q < sptr[s1]; ++q) lidx[q] = (int16_t)pos[sidx[q]];
+      max_len = std::max(max_len, (int)L.size());
+    }
+  }
+  tptr.assign(ntile + 1, 0);
+  for (int64_t t = 0; t < ntile; ++t) tptr[t + 1] = tptr[t] + (int32_t)lists[t].size();
+  tidx.resize(tptr[ntile]);
+  for (int64_t t = 0; t < ntile; ++t) std::copy(lists[t].begin(), lists[t].end(), tidx.begin() + tptr[t]);
+  return max_len;
+}
+
 template <typename T>
 cudaError_t upload_geo(fvgb_mesh_s* m, const HostMesh& h, const std::vector<double>& sw,
                        GeoDev<T>& g, cudaStream_t s) {
@@ -423,9 +460,12 @@ bool warm_requested(const fvgb_streamer_params* p) { return p->warm || p->extrap
 //  - charge history: dq = change of n_i - n_e since the previous step, d2q its change;
 //  - base start: phi (the previous potential), or with extrapolation and two earlier
 //    steps 2 phi - phi_old (linear in time);
-//  - learned correction (when p->warm): the network's increment from dq (base = phi) or
-//    from d2q (base = extrapolation, whose error is the increment's change), added on
-//    the parts where that start has the smaller FP64 residual ||b - A phi||.
+//  - learned correction (when p->warm): the network's increment pred from dq (base = phi)
+//    or from d2q (base = extrapolation, whose error is the increment's change), added per
+//    part in full where phi + pred has the smaller FP64 residual (r1 = b - A (phi + pred)
+//    against r0 = b - A phi), elsewhere scaled by s = <r0, A pred> / ||A pred||^2 (with
+//    A pred = r0 - r1), the scale that minimises ||b - A (phi + s pred)||. Either way the
+//    start's residual is not larger than without the network.
 fvgb_status warm_start(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, void* ni, double* phi,
                        int hist, cudaStream_t s) {
   const int64_t N = m->topo.N;
@@ -438,8 +478,9 @@ fvgb_status warm_start(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, voi
     FVGB_TRY(dalloc(m, &m->phi_old2, N), "allocation");
     FVGB_TRY(dalloc(m, &m->dphi_pred, N), "allocation");
     FVGB_TRY(dalloc(m, &m->phi_save, N), "allocation");
-    FVGB_TRY(dalloc(m, &m->warm_norms, 2 * P), "allocation");
+    FVGB_TRY(dalloc(m, &m->warm_norms, 4 * P), "allocation");
     FVGB_TRY(dalloc(m, &m->warm_used, P), "allocation");
+    FVGB_TRY(dalloc(m, &m->warm_scale, P), "allocation");
   }
   FVGB_TRY(launch_charge_hist(m, ne, ni, is_fp32(m), hist, m->q_prev, m->dq, m->d2q, s), "charge kernel");
   const bool extrap = p->extrapolate && hist >= 2;
@@ -448,20 +489,21 @@ fvgb_status warm_start(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, voi
   if (!learn) return FVGB_OK;
   double* f = m->w64.tmp;
   double* b = m->dphi_tmp2;
-  double* r = m->dphi_tmp;
+  double* r0 = m->dphi_tmp;
   FVGB_TRY(launch_poisson_source(m, ne, ni, is_fp32(m), f, s), "source kernel");
   if (fvgb_status st = poisson_rhs_impl(m, p->bcset_phi, f, b, s)) return st;
+  double* r1 = f;                      // the source is no longer needed once b is formed
   FVGB_TRY(cudaMemcpyAsync(m->phi_save, phi, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
-  if (fvgb_status st = poisson_residual(m, p->bcset_phi, phi, b, r, s)) return st;
-  FVGB_TRY(launch_part_sumsq(m, r, m->warm_norms, s), "norm kernel");
+  if (fvgb_status st = poisson_residual(m, p->bcset_phi, phi, b, r0, s)) return st;
   if (fvgb_status st = fvgb_mpnn_predict(p->warm, p->extrapolate ? m->d2q : m->dq, m->phi_old,
                                          m->dphi_pred, s)) return st;
   FVGB_TRY(launch_axpy_d(m->dphi_pred, 1.0, phi, N, s), "update");
-  if (fvgb_status st = poisson_residual(m, p->bcset_phi, phi, b, r, s)) return st;
-  FVGB_TRY(launch_part_sumsq(m, r, m->warm_norms + P, s), "norm kernel");
+  if (fvgb_status st = poisson_residual(m, p->bcset_phi, phi, b, r1, s)) return st;
+  // r0 - r1 = A pred: the residual-minimising scale of the correction, per part
+  FVGB_TRY(launch_part_dots(m, r0, r1, m->warm_norms, s), "dot kernel");
   m->warm_check_pending = true;
-  return cuda_status(launch_choose_start(m, m->warm_norms, m->warm_norms + P, m->phi_save, phi,
-                                         m->warm_used, s), "choose kernel");
+  return cuda_status(launch_scale_start(m, m->warm_norms, m->phi_save, m->dphi_pred, phi, m->warm_used,
+                                        m->warm_scale, s), "start kernel");
 }
 
 // Field, cell physics and one transport stage of eq. 6 (after the stage's solve):
@@ -673,6 +715,18 @@ static fvgb_status upload_impl(int32_t dim, int64_t n_vert, const double* xyz, i
   build_sell(h.nptr, h.nidx, nullptr, h.N, true, sptr, sidx, nullptr);
   if ((e = dupload(m, &t.nsell.ptr, sptr, s))) return fail(e, "upload");
   if ((e = dupload(m, &t.nsell.idx, sidx, s))) return fail(e, "upload");
+  if (prec != FVGB_FP64 && h.dim == 3 && h.N >= kGradTile &&
+      (int64_t)h.nptr[h.N] < (int64_t)INT32_MAX / 2) {   // the FP32 shared-memory gradient
+    std::vector<int32_t> tptr, tidx;
+    std::vector<int16_t> lidx;
+    const int mx = build_grad_tiles(h.N, sptr, sidx, tptr, tidx, lidx);
+    if (mx <= kGradTileMaxHalo) {
+      t.tile_max = mx;
+      if ((e = dupload(m, &t.tile_ptr, tptr, s))) return fail(e, "upload");
+      if ((e = dupload(m, &t.tile_idx, tidx, s))) return fail(e, "upload");
+      if ((e = dupload(m, &t.tile_lidx, lidx, s))) return fail(e, "upload");
+    }
+  }
   std::vector<double> sw;
   build_sell(h.vptr, h.vcell, &h.valpha, h.V, false, sptr, sidx, &sw);
   if ((e = dupload(m, &t.vsell.ptr, sptr, s))) return fail(e, "upload");

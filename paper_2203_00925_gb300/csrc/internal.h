@@ -65,7 +65,17 @@ struct TopoDev {
   int32_t* vcount = nullptr;     // [V] cells around each vertex
   Sell nsell;                    // node neighbours of each cell (padded with the cell)
   Sell vsell;                    // cells around each vertex (padded, weight 0)
+  // Tiles of kGradTile consecutive cells for the shared-memory gradient: per tile its
+  // halo list (the tile's own cells in order, then the other node neighbours of its cells,
+  // sorted) and, aligned with nsell.idx, each entry's position in its tile's list.
+  int32_t* tile_ptr = nullptr;   // [n_tile + 1]
+  int32_t* tile_idx = nullptr;   // halo lists
+  int16_t* tile_lidx = nullptr;  // [size of nsell.idx]
+  int tile_max = 0;              // longest halo list (0: tiles not built)
 };
+
+constexpr int kGradTile = 128;      // cells per tile of the shared-memory gradient
+constexpr int kGradTileMaxHalo = 3072;  // longest halo list the FP32 tiled kernel stages (48 KB)
 
 // Scratch of one precision.
 template <typename T>
@@ -162,8 +172,9 @@ struct fvgb_mesh_s {
   double* phi_old2 = nullptr;           // [N] potential at the start of the step before
   double* dphi_pred = nullptr;          // [N] learned correction
   double* phi_save = nullptr;           // [N] start without the learned correction
-  double* warm_norms = nullptr;         // [2][P] residual norms of the two starts
-  int* warm_used = nullptr;             // [P] 1 where the learned start was kept
+  double* warm_norms = nullptr;         // [4][P] per part <r0, A pred>, ||A pred||^2, ||r0||^2, ||r1||^2
+  int* warm_used = nullptr;             // [P] 1 where the learned correction was used (scale > 0)
+  double* warm_scale = nullptr;         // [P] scale of the learned correction in the start
   bool warm_check_pending = false;      // warm_used of a host-driven step not yet counted
   int warm_hist = 0;                    // streamer steps recorded in the history (capped at 3)
   fvgb::GraphState* graph = nullptr;    // captured step graph (graph.cu)
@@ -246,8 +257,8 @@ cudaError_t launch_extrapolate(fvgb_mesh_s* m, bool extrap, double* phi, double*
                                cudaStream_t s);
 cudaError_t launch_history_pair(fvgb_mesh_s* m, int which, const double* phi, double* q_out, double* p_out,
                                 double* d_out, cudaStream_t s);
-cudaError_t launch_choose_start(fvgb_mesh_s* m, const double* na, const double* nb, const double* saved,
-                                double* phi, int* used, cudaStream_t s);
+cudaError_t launch_scale_start(fvgb_mesh_s* m, const double* dots, const double* saved, const double* pred,
+                               double* phi, int* used, double* scale, cudaStream_t s);
 cudaError_t launch_axpy_d(const double* x, double a, double* y, int64_t n, cudaStream_t s);
 cudaError_t launch_add_to_double(const void* x, bool fp32, double* y, int64_t n, cudaStream_t s);
 cudaError_t launch_convert(const double* x, float* y, int64_t n, cudaStream_t s);
@@ -329,5 +340,7 @@ cudaError_t launch_inner(fvgb_mesh_s* m, int bcset, const double* r, const fvgb_
 }
 
 cudaError_t launch_part_sumsq(fvgb_mesh_s* m, const double* v, double* out, cudaStream_t s);
+// per part <r0, r0 - r1>, ||r0 - r1||^2, ||r0||^2, ||r1||^2 into out[k P, (k + 1) P), k = 0..3
+cudaError_t launch_part_dots(fvgb_mesh_s* m, const double* r0, const double* r1, double* out, cudaStream_t s);
 
 }  // namespace fvgb

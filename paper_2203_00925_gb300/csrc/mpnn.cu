@@ -203,17 +203,20 @@ __global__ void k_features(int64_t N, const double* __restrict__ dq, const doubl
   }
 }
 
-__global__ void k_max_coef(int64_t n, const double* __restrict__ coef, double* __restrict__ out) {
+// maximum of n coefficients: per-block maxima into part[blockIdx.x], then (nblocks = 1,
+// n = grid of the first pass) the maximum of those
+__global__ void k_max_coef(int64_t n, const double* __restrict__ coef, double* __restrict__ part) {
   __shared__ double sh[256];
   double mx = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, coef[i]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    mx = fmax(mx, coef[i]);
   sh[threadIdx.x] = mx;
   __syncthreads();
   for (int s = 128; s > 0; s >>= 1) {
     if (threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[0] = sh[0];
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
 __global__ void k_msg_weights(int64_t n, const double* __restrict__ coef, const double* __restrict__ cmax,
@@ -255,7 +258,7 @@ k_layer_fwd(int64_t N, const float* __restrict__ H, const int4* __restrict__ nbr
   __shared__ uint32_t tmem_base;
   __shared__ float bs[kHid];
   __shared__ int s_fail;
-  const int t = threadIdx.x, warp = t >> 5;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   unsigned char* As = smem;
   unsigned char* Bs = smem + kFwdB;
   // W (the B operand: 64 outputs x 128 inputs, K-major) and the bias, once per block
@@ -282,17 +285,21 @@ k_layer_fwd(int64_t N, const float* __restrict__ H, const int4* __restrict__ nbr
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t c = tile * kTile + t;
     const bool live = c < N;
-    const int4 nb = live ? nbr[c] : make_int4(0, 0, 0, 0);
-    const float4 w4 = live ? wn[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int ns[4] = {nb.x, nb.y, nb.z, nb.w};
-    const float ws[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll 1
-    for (int kc = 0; kc < kHid / 8; ++kc) {
+    // gather: warp w builds rows [32 w, 32 w + 32) of A, a step covering 8 rows x 4 chunks
+    // of 8 features (whole 128-byte lines per load, conflict-free shared-memory stores)
+#pragma unroll 2
+    for (int st = 0; st < 8; ++st) {
+      const int r = 32 * warp + 8 * (st >> 1) + (lane & 7), kc = 4 * (st & 1) + (lane >> 3);
+      const int64_t cr = tile * kTile + r;
       float h[8], m[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) h[j] = m[j] = 0.0f;
-      if (live) {
-        load8(H + c * kHid + kc * 8, h);
+      if (cr < N) {
+        const int4 nb = nbr[cr];
+        const float4 w4 = wn[cr];
+        const int ns[4] = {nb.x, nb.y, nb.z, nb.w};
+        const float ws[4] = {w4.x, w4.y, w4.z, w4.w};
+        load8(H + cr * kHid + kc * 8, h);
         float g[4][8];
 #pragma unroll
         for (int q = 0; q < 4; ++q) load8(H + (int64_t)ns[q] * kHid + kc * 8, g[q]);
@@ -300,10 +307,10 @@ k_layer_fwd(int64_t N, const float* __restrict__ H, const int4* __restrict__ nbr
         for (int q = 0; q < 4; ++q)
 #pragma unroll
           for (int j = 0; j < 8; ++j) m[j] += ws[q] * (g[q][j] - h[j]);
-        if (Mout) store8(Mout + c * kHid + kc * 8, m);
+        if (Mout) store8(Mout + cr * kHid + kc * 8, m);
       }
-      st_bf16x8(As + kmaj_off(t, kc * 8, kIn), h);
-      st_bf16x8(As + kmaj_off(t, kHid + kc * 8, kIn), m);
+      st_bf16x8(As + kmaj_off(r, kc * 8, kIn), h);
+      st_bf16x8(As + kmaj_off(r, kHid + kc * 8, kIn), m);
     }
     fence_async_smem();
     tc_fence_before();
@@ -416,16 +423,30 @@ __global__ void k_head_dh(int64_t N, const float* __restrict__ dout, const float
     dH[e] = sign * dout[e / kHid] * theta[kOffWdec + (int)(e % kHid)];
 }
 
+// Per-block sums over the block's cell range for the gradient partials: kRowGroups groups of
+// 64 threads (one feature each) take every kRowGroups-th cell, then the group sums are
+// added in group order.
+constexpr int kRowGroups = 8;
+
 // decoder gradient partials: part[b][w_dec] = sum dout (h_a - h_b); part[b][b_dec] = 0
-__global__ void k_decode_grad(int64_t N, const float* __restrict__ Ha, const float* __restrict__ Hb,
-                              const float* __restrict__ dout, float* __restrict__ part) {
+__global__ void __launch_bounds__(kRowGroups * kHid)
+k_decode_grad(int64_t N, const float* __restrict__ Ha, const float* __restrict__ Hb,
+              const float* __restrict__ dout, float* __restrict__ part) {
+  __shared__ float red[kRowGroups][kHid];
   const int64_t per = (N + gridDim.x - 1) / gridDim.x;
   const int64_t lo = blockIdx.x * per, hi = lo + per < N ? lo + per : N;
+  const int g = threadIdx.x / kHid, o = threadIdx.x % kHid;
+  float acc = 0.0f;
+#pragma unroll 4
+  for (int64_t i = lo + g; i < hi; i += kRowGroups) acc += dout[i] * (Ha[i * kHid + o] - Hb[i * kHid + o]);
+  red[g][o] = acc;
+  __syncthreads();
   float* p = part + (size_t)blockIdx.x * kNParams;
   if (threadIdx.x < kHid) {
-    float acc = 0.0f;
-    for (int64_t i = lo; i < hi; ++i) acc += dout[i] * (Ha[i * kHid + threadIdx.x] - Hb[i * kHid + threadIdx.x]);
-    p[kOffWdec + threadIdx.x] = acc;
+    float t = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kRowGroups; ++q) t += red[q][o];
+    p[kOffWdec + o] = t;
   } else if (threadIdx.x == kHid) {
     p[kOffBdec] = 0.0f;
   }
@@ -443,7 +464,7 @@ k_layer_bwd(int64_t N, const float* __restrict__ dHn, const float* __restrict__ 
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
-  const int t = threadIdx.x, warp = t >> 5;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   unsigned char* As = smem;
   unsigned char* Bs = smem + kBwdB;
   // W^T (the B operand: 128 inputs x 64 outputs, K-major): element (n, k) = W[k][n]
@@ -468,20 +489,23 @@ k_layer_bwd(int64_t N, const float* __restrict__ dHn, const float* __restrict__ 
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t c = tile * kTile + t;
     const bool live = c < N;
-#pragma unroll 1
-    for (int kc = 0; kc < kHid / 8; ++kc) {
+    // dz tile: warp w builds rows [32 w, 32 w + 32), a step covering 8 rows x 4 chunks
+#pragma unroll 2
+    for (int st = 0; st < 8; ++st) {
+      const int r = 32 * warp + 8 * (st >> 1) + (lane & 7), kc = 4 * (st & 1) + (lane >> 3);
+      const int64_t cr = tile * kTile + r;
       float d[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) d[j] = 0.0f;
-      if (live) {
+      if (cr < N) {
         float z[8];
-        load8(dHn + c * kHid + kc * 8, d);
-        load8(Z + c * kHid + kc * 8, z);
+        load8(dHn + cr * kHid + kc * 8, d);
+        load8(Z + cr * kHid + kc * 8, z);
 #pragma unroll
         for (int j = 0; j < 8; ++j) d[j] = z[j] > 0.0f ? d[j] : 0.0f;
-        store8(dZ + c * kHid + kc * 8, d);
+        store8(dZ + cr * kHid + kc * 8, d);
       }
-      st_bf16x8(As + kmaj_off(t, kc * 8, kHid), d);
+      st_bf16x8(As + kmaj_off(r, kc * 8, kHid), d);
     }
     fence_async_smem();
     tc_fence_before();
@@ -592,23 +616,35 @@ __global__ void __launch_bounds__(256) k_layer_wgrad(int64_t N, const float* __r
 }
 
 // encoder gradients: dz0 = dH0 * (z0 > 0); part[b][W_enc] = sum dz0 (x) f, part[b][b_enc] = sum dz0
-__global__ void k_encode_grad(int64_t N, const float* __restrict__ dH, const float* __restrict__ Z0,
-                              const float* __restrict__ F, float* __restrict__ part) {
-  const int o = threadIdx.x;
-  if (o >= kHid) return;
+__global__ void __launch_bounds__(kRowGroups * kHid)
+k_encode_grad(int64_t N, const float* __restrict__ dH, const float* __restrict__ Z0,
+              const float* __restrict__ F, float* __restrict__ part) {
+  __shared__ float red[3][kRowGroups][kHid];
   const int64_t per = (N + gridDim.x - 1) / gridDim.x;
   const int64_t lo = blockIdx.x * per, hi = lo + per < N ? lo + per : N;
+  const int g = threadIdx.x / kHid, o = threadIdx.x % kHid;
   float a0 = 0.0f, a1 = 0.0f, ab = 0.0f;
-  for (int64_t c = lo; c < hi; ++c) {
+#pragma unroll 4
+  for (int64_t c = lo + g; c < hi; c += kRowGroups) {
     const float d = Z0[c * kHid + o] > 0.0f ? dH[c * kHid + o] : 0.0f;
-    a0 += d * F[2 * c];
-    a1 += d * F[2 * c + 1];
+    const float2 f = *reinterpret_cast<const float2*>(F + 2 * c);
+    a0 += d * f.x;
+    a1 += d * f.y;
     ab += d;
   }
-  float* p = part + (size_t)blockIdx.x * kNParams;
-  p[kOffWenc + 2 * o] = a0;
-  p[kOffWenc + 2 * o + 1] = a1;
-  p[kOffBenc + o] = ab;
+  red[0][g][o] = a0;
+  red[1][g][o] = a1;
+  red[2][g][o] = ab;
+  __syncthreads();
+  if (threadIdx.x < kHid) {
+    float t0 = 0.0f, t1 = 0.0f, tb = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kRowGroups; ++q) { t0 += red[0][q][o]; t1 += red[1][q][o]; tb += red[2][q][o]; }
+    float* p = part + (size_t)blockIdx.x * kNParams;
+    p[kOffWenc + 2 * o] = t0;
+    p[kOffWenc + 2 * o + 1] = t1;
+    p[kOffBenc + o] = tb;
+  }
 }
 
 // grad[k] = sum over blocks of part[b][k] in block order (FP64 accumulation)
@@ -693,7 +729,6 @@ cudaError_t alloc_train(MpnnNet* n) {
   if ((e = nalloc(n, &n->dZ, NH))) return e;
   if ((e = nalloc(n, &n->dout, n->N))) return e;
   if ((e = nalloc(n, &n->part, (size_t)2 * kGradBlocks * kNParams))) return e;
-  if ((e = nalloc(n, &n->dpart, kGradBlocks))) return e;
   n->train_buffers = true;
   return cudaSuccess;
 }
@@ -772,7 +807,7 @@ void backward_set(MpnnNet* n, int set, float sign, int row0, cudaStream_t s) {
     count_launch(3);
     std::swap(dHn, dHo);
   }
-  k_encode_grad<<<G, kHid, 0, s>>>(N, dHn, n->Z0[set], n->F[set], part);
+  k_encode_grad<<<G, kRowGroups * kHid, 0, s>>>(N, dHn, n->Z0[set], n->F[set], part);
   count_launch();
 }
 
@@ -788,7 +823,7 @@ cudaError_t loss_grad(MpnnNet* n, const double* dq, const double* phi, const dou
   k_head_train<<<G, 256, 0, s>>>(N, n->H[0][kLayers], n->H[1][kLayers], n->theta, n->V * n->s2, target,
                                  n->dout, n->dpart);
   k_reduce_loss<<<1, 32, 0, s>>>(G, n->dpart, n->dloss);
-  k_decode_grad<<<G, 96, 0, s>>>(N, n->H[0][kLayers], n->H[1][kLayers], n->dout, n->part);
+  k_decode_grad<<<G, kRowGroups * kHid, 0, s>>>(N, n->H[0][kLayers], n->H[1][kLayers], n->dout, n->part);
   count_launch(3);
   backward_set(n, 0, 1.0f, 0, s);
   backward_set(n, 1, -1.0f, G, s);
@@ -837,9 +872,11 @@ fvgb_status fvgb_mpnn_create(fvgb_mesh m, int32_t bcset, fvgb_mpnn* out) {
   if ((e = cudaMemset(n->wbf, 0, (size_t)kLayers * kHid * kIn * sizeof(__nv_bfloat16)))) return fail("memset");
   // message weights: c1 of the interior faces (two-point coefficients of bcset), / max
   const double* coef = m->g64.bc[bcset].at_coef;
-  k_max_coef<<<1, 256>>>(4 * n->N, coef, n->dloss + 1);
+  if ((e = nalloc(n, &n->dpart, kGradBlocks))) return fail("allocation");
+  k_max_coef<<<kGradBlocks, 256>>>(4 * n->N, coef, n->dpart);
+  k_max_coef<<<1, 256>>>(kGradBlocks, n->dpart, n->dloss + 1);
   k_msg_weights<<<grid_n(4 * n->N), 256>>>(4 * n->N, coef, n->dloss + 1, n->wn);
-  count_launch(2);
+  count_launch(3);
   if ((e = cudaDeviceSynchronize())) return fail("message weights");
   *out = n;
   return FVGB_OK;

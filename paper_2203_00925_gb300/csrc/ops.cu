@@ -179,6 +179,75 @@ k_gradient(int64_t N, int64_t F, int64_t Fi, const int64_t* __restrict__ sptr,
   }
 }
 
+// FP32, 3D, shared-memory form of k_gradient: one block per tile of kGradTile consecutive
+// cells. The block first stages its tile's halo list (own cells, then their other node
+// neighbours) as 16-byte records {u, x - o, y - o, z - o} with coordinates relative to the
+// tile's first centre o (high + low parts combined there, so the small differences keep
+// FP32 accuracy); each neighbour entry is then one shared-memory read at its int16 local
+// position instead of a 32-byte gather from L1/L2. Same sum order as k_gradient.
+__global__ void __launch_bounds__(kGradTile)
+k_gradient_tiled(int64_t N, int64_t F, int64_t Fi, const int64_t* __restrict__ sptr,
+                 const int16_t* __restrict__ lidx, const int32_t* __restrict__ tptr,
+                 const int32_t* __restrict__ tidx, const float* __restrict__ rec,
+                 const float* __restrict__ cen, const float* __restrict__ cen_lo, const float* __restrict__ xf,
+                 const float* __restrict__ xf_lo, const float* __restrict__ minv,
+                 const int32_t* __restrict__ gptr, const int32_t* __restrict__ gface,
+                 const float* __restrict__ bval, float* __restrict__ grad) {
+  extern __shared__ float4 hrec[];
+  const int64_t tile = blockIdx.x;
+  const int64_t r0 = tile * kGradTile;
+  const int32_t h0 = tptr[tile], nh = tptr[tile + 1] - h0;
+  const float4* R = reinterpret_cast<const float4*>(rec);
+  const float4 oa = __ldg(R + 2 * r0), ob = __ldg(R + 2 * r0 + 1);   // origin: the first own centre
+  for (int k = threadIdx.x; k < nh; k += blockDim.x) {
+    const int32_t j = __ldg(tidx + h0 + k);
+    const float4 a = __ldg(R + 2 * (int64_t)j), b = __ldg(R + 2 * (int64_t)j + 1);
+    hrec[k] = make_float4(a.x, (a.y - oa.y) + (b.x - ob.x), (a.z - oa.z) + (b.y - ob.y), (a.w - oa.w) + (b.z - ob.z));
+  }
+  __syncthreads();
+  const int64_t i = r0 + threadIdx.x;
+  if (i >= N) return;
+  const int64_t sl = i >> 5;
+  const int lane = (int)(i & 31);
+  const int64_t b0 = sptr[sl];
+  const int width = (int)((sptr[sl + 1] - b0) >> 5);
+  const int16_t* col = lidx + b0 + lane;
+  const float4 me = hrec[threadIdx.x];
+  float J[3] = {0.0f, 0.0f, 0.0f};
+  int c = 0;
+  for (; c + 4 <= width; c += 4) {
+    const float4 n0 = hrec[__ldg(col + 32 * c)], n1 = hrec[__ldg(col + 32 * (c + 1))],
+                 n2 = hrec[__ldg(col + 32 * (c + 2))], n3 = hrec[__ldg(col + 32 * (c + 3))];
+    const float4 nn[4] = {n0, n1, n2, n3};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float du = nn[q].x - me.x;
+      J[0] += (nn[q].y - me.y) * du;
+      J[1] += (nn[q].z - me.z) * du;
+      J[2] += (nn[q].w - me.w) * du;
+    }
+  }
+  for (; c < width; ++c) {
+    const float4 nq = hrec[__ldg(col + 32 * c)];
+    const float du = nq.x - me.x;
+    J[0] += (nq.y - me.y) * du;
+    J[1] += (nq.z - me.z) * du;
+    J[2] += (nq.w - me.w) * du;
+  }
+  const float ui = me.x;
+  for (int32_t t = gptr[i]; t < gptr[i + 1]; ++t) {
+    const int32_t f = gface[t];
+    const float du = bval[f - Fi] - ui;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) J[a] += cdiff(xf + a * F, xf_lo + a * F, f, cen + a * N, cen_lo + a * N, i) * du;
+  }
+  const float m0 = minv[i], m1 = minv[N + i], m2 = minv[2 * N + i], m3 = minv[3 * N + i], m4 = minv[4 * N + i],
+              m5 = minv[5 * N + i];
+  grad[i] = m0 * J[0] + m1 * J[1] + m2 * J[2];
+  grad[N + i] = m1 * J[0] + m3 * J[1] + m4 * J[2];
+  grad[2 * N + i] = m2 * J[0] + m4 * J[1] + m5 * J[2];
+}
+
 // ---- multiplicity-weighted least-squares gradient (vertex-factorised variant) ---------------
 // grad u_i = Mv_i^{-1} J_i, J_i = sum over the vertices A of T_i, over the cells c around A,
 // of (x_c - x_i)(u_c - u_i), plus each Dirichlet ghost point once per shared vertex. Per
@@ -709,6 +778,17 @@ cudaError_t launch_gradient(fvgb_mesh_s* m, int bcset, const T* u, T* grad, cuda
   const int tg = m->tune[kTuneGrad].threads;
   if (t.dim == 3) {
     k_grad_pack<3><<<gp, kThreads, 0, s>>>(t.N, g.cen, g.cen_lo, u, rec);
+    if constexpr (sizeof(T) == 4) {
+      if (t.tile_max > 0) {      // FP32: the shared-memory form
+        const int64_t ntile = (t.N + kGradTile - 1) / kGradTile;
+        k_gradient_tiled<<<(unsigned)ntile, kGradTile, t.tile_max * sizeof(float4), s>>>(
+            t.N, t.F, t.Fi, t.nsell.ptr, t.tile_lidx, t.tile_ptr, t.tile_idx, (const float*)rec,
+            (const float*)g.cen, (const float*)g.cen_lo, (const float*)g.xf, (const float*)g.xf_lo,
+            (const float*)b.minv, b.gptr, b.gface, (const float*)b.bval, (float*)grad);
+        count_launch(2);
+        return cudaGetLastError();
+      }
+    }
     k_gradient<T, 3><<<gg, tg, 0, s>>>(t.N, t.F, t.Fi, t.nsell.ptr, t.nsell.idx, rec, g.cen,
         g.cen_lo, g.xf, g.xf_lo, u, b.minv, b.gptr, b.gface, b.bval, grad);
   } else {
@@ -988,22 +1068,30 @@ cudaError_t launch_history_pair(fvgb_mesh_s* m, int which, const double* phi, do
   return cudaGetLastError();
 }
 
-// per part: keep the learned start only where its residual is smaller (block p = part p)
-__global__ void k_choose_start(const double* __restrict__ na, const double* __restrict__ nb,
-                               const int32_t* __restrict__ part_sc, const int64_t* __restrict__ sc_begin,
-                               const double* __restrict__ saved, double* __restrict__ phi,
-                               int* __restrict__ used) {
+// per part p (block p): phi = saved + s pred. dots: per part <r0, A pred>, ||A pred||^2,
+// ||r0||^2, ||r1||^2 (r1 the residual of saved + pred). s = 1 where ||r1|| < ||r0||, else
+// s = <r0, A pred> / ||A pred||^2, the scale that minimises the FP64 residual
+// ||r0 - s A pred|| along the prediction; s = 0 where that is undefined. used[p] = (s > 0).
+__global__ void k_scale_start(const double* __restrict__ dots, int P, const int32_t* __restrict__ part_sc,
+                              const int64_t* __restrict__ sc_begin, const double* __restrict__ saved,
+                              const double* __restrict__ pred, double* __restrict__ phi, int* __restrict__ used,
+                              double* __restrict__ scale) {
   const int p = blockIdx.x;
-  const bool keep = nb[p] < na[p];   // false for NaN as well
-  if (threadIdx.x == 0) used[p] = keep ? 1 : 0;
-  if (keep) return;
+  const double num = dots[p], den = dots[P + p], n0 = dots[2 * P + p], n1 = dots[3 * P + p];
+  double sc = n1 < n0 ? 1.0 : (den > 0.0 ? num / den : 0.0);
+  if (!isfinite(sc)) sc = 0.0;
+  if (threadIdx.x == 0) {
+    used[p] = sc > 0.0 ? 1 : 0;
+    scale[p] = sc;
+  }
   const int64_t lo = sc_begin[part_sc[p]], hi = sc_begin[part_sc[p + 1]];
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) phi[i] = saved[i];
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) phi[i] = saved[i] + sc * pred[i];
 }
 
-cudaError_t launch_choose_start(fvgb_mesh_s* m, const double* na, const double* nb, const double* saved,
-                                double* phi, int* used, cudaStream_t s) {
-  k_choose_start<<<m->parts.n_part, 256, 0, s>>>(na, nb, m->parts.part_sc, m->parts.sc_begin, saved, phi, used);
+cudaError_t launch_scale_start(fvgb_mesh_s* m, const double* dots, const double* saved, const double* pred,
+                               double* phi, int* used, double* scale, cudaStream_t s) {
+  k_scale_start<<<m->parts.n_part, 256, 0, s>>>(dots, m->parts.n_part, m->parts.part_sc, m->parts.sc_begin,
+                                                saved, pred, phi, used, scale);
   count_launch();
   return cudaGetLastError();
 }

@@ -90,6 +90,29 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
+// Block-wide FP64 sum in a fixed order for launches over many parts: a shuffle tree inside
+// each warp, then warp 0 sums the warp totals in warp order. Valid in thread 0. Measured
+// faster than block_sum on the 64-mesh ensemble, whose short inner solves leave most
+// blocks summing finished or tiny sub-chunks; block_sum is faster on a single mesh.
+__device__ __forceinline__ double block_sum_tree(double v, double* sh) {
+  __syncthreads();                      // the previous call's readers are done with sh
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = l < (int)(blockDim.x >> 5) ? sh[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  }
+  return t;
+}
+
+// the block sum of the CG kernel: by part count (uniform over the grid)
+__device__ __forceinline__ double cg_block_sum(double v, double* sh, bool many_parts) {
+  return many_parts ? block_sum_tree(v, sh) : block_sum(v, sh);
+}
+
 template <typename T>
 struct SolveArgs {
   int64_t N;
@@ -294,6 +317,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
   __shared__ int s_flag, s_status;
   const unsigned G = gridDim.x;
   const int P = a.n_part;
+  const bool many = P > 1;
   const int sc0 = a.blk_sc[blockIdx.x], sc1 = a.blk_sc[blockIdx.x + 1];
   int parity = 0;
   int total_its = 0;
@@ -323,8 +347,8 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
       }
       l1 = cg_phase_pq<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], T(0));
     }
-    const double t0 = block_sum((double)l0, sh);
-    const double t1 = block_sum((double)l1, sh);
+    const double t0 = cg_block_sum((double)l0, sh, many);
+    const double t1 = cg_block_sum((double)l1, sh, many);
     if (threadIdx.x == 0) { a.buf[sc] = t0; a.buf[a.n_sc + sc] = t1; }
   }
   if (!grid_barrier(a.bar, G, target, a.skip_block == (int)blockIdx.x, a.barrier_ns)) goto done;
@@ -350,7 +374,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
     for (int sc = sc0; sc < sc1; ++sc) {
       const int p = a.sc_part[sc];
       if (s_cg[p] == 0) {             // uniform in the block
-        const double t = block_sum((double)cg_phase_xr<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], s_alpha[p]), sh);
+        const double t = cg_block_sum((double)cg_phase_xr<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], s_alpha[p]), sh, many);
         if (threadIdx.x == 0) buf[sc] = t;
       } else if (threadIdx.x == 0) {
         buf[sc] = 0.0;
@@ -378,7 +402,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
     for (int sc = sc0; sc < sc1; ++sc) {
       const int p = a.sc_part[sc];
       if (s_cg[p] == 0) {             // uniform in the block
-        const double t = block_sum((double)cg_phase_pq<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], s_beta[p]), sh);
+        const double t = cg_block_sum((double)cg_phase_pq<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], s_beta[p]), sh, many);
         if (threadIdx.x == 0) buf[sc] = t;
       } else if (threadIdx.x == 0) {
         buf[sc] = 0.0;
@@ -432,6 +456,36 @@ __global__ void __launch_bounds__(kCgThreads) k_part_sumsq_final(const double* _
   }
 }
 
+// Per-part sums of r0 (r0 - r1), (r0 - r1)^2, r0^2 and r1^2 over the same sub-chunks, for
+// the scale of a correction whose operator image is r0 - r1 (partials per sub-chunk: four
+// block sums, in buf[k * n_sc + sc]).
+__global__ void __launch_bounds__(kCgThreads) k_part_dots_partial(const double* __restrict__ r0,
+    const double* __restrict__ r1, const int32_t* __restrict__ blk_sc, const int64_t* __restrict__ sc_begin,
+    int n_sc, double* __restrict__ buf) {
+  __shared__ double sh[kCgThreads];
+  for (int sc = blk_sc[blockIdx.x]; sc < blk_sc[blockIdx.x + 1]; ++sc) {
+    double a = 0.0, b = 0.0, c0 = 0.0, c1 = 0.0;
+    for (int64_t i = sc_begin[sc] + threadIdx.x; i < sc_begin[sc + 1]; i += blockDim.x) {
+      const double x = r0[i], y = r1[i];
+      const double d = x - y;
+      a += x * d;
+      b += d * d;
+      c0 += x * x;
+      c1 += y * y;
+    }
+    a = block_sum(a, sh);
+    b = block_sum(b, sh);
+    c0 = block_sum(c0, sh);
+    c1 = block_sum(c1, sh);
+    if (threadIdx.x == 0) {
+      buf[sc] = a;
+      buf[n_sc + sc] = b;
+      buf[2 * n_sc + sc] = c0;
+      buf[3 * n_sc + sc] = c1;
+    }
+  }
+}
+
 }  // namespace
 
 int solve_grid_size(fvgb_mesh_s* m) {
@@ -450,6 +504,15 @@ cudaError_t launch_part_sumsq(fvgb_mesh_s* m, const double* v, double* out, cuda
   k_part_sumsq_partial<<<m->solve_grid, kCgThreads, 0, s>>>(v, pd.blk_sc, pd.sc_begin, pd.buf);
   k_part_sumsq_final<<<1, kCgThreads, 0, s>>>(pd.buf, pd.part_sc, pd.n_part, out);
   count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_part_dots(fvgb_mesh_s* m, const double* r0, const double* r1, double* out, cudaStream_t s) {
+  const PartsDev& pd = m->parts;
+  k_part_dots_partial<<<m->solve_grid, kCgThreads, 0, s>>>(r0, r1, pd.blk_sc, pd.sc_begin, pd.n_sc, pd.buf);
+  for (int k = 0; k < 4; ++k)
+    k_part_sumsq_final<<<1, kCgThreads, 0, s>>>(pd.buf + k * pd.n_sc, pd.part_sc, pd.n_part, out + k * pd.n_part);
+  count_launch(5);
   return cudaGetLastError();
 }
 

@@ -38,37 +38,43 @@ def init_params(seed):
 
 
 def streamer_run(dm, case, mesh, dt, steps, solve, warm=None, extrapolate=False, record=False,
-                 graph=False):
+                 graph=False, on_pair=None):
     """Run ``steps`` streamer steps of one case from its initial state (phi from 0).
 
     Returns per-step solve infos and, when ``record``, two lists of training pairs as FP64
-    device tensors: (dq, phi_prev, dphi) for a start from the previous potential (steps
-    1..) and (d2q, phi_prev, dphi - dphi_prev) for a start from the linear extrapolation in
-    time (steps 2..), where dq is the change of n_i - n_e between step starts and d2q the
-    change of dq."""
+    device tensors, built by the library from its warm-start history
+    (fvgb_streamer_pair): (dq, phi_prev, dphi) for a start from the previous potential
+    (steps 1..) and (d2q, phi_prev, dphi - dphi_prev) for a start from the linear
+    extrapolation in time (steps 2..). With ``on_pair`` each pair is handed to
+    on_pair(which, dq, phi_prev, dphi) instead, in buffers reused for the next pair.
+    Recording keeps a warm-start history, so a recording run starts its solves from the
+    extrapolation (the pairs are those of the converged trajectory either way)."""
     ne0, ni0 = case.initial(mesh)
     ne, ni = dm.to_device(ne0), dm.to_device(ni0)
     phi = torch.zeros(dm.n_cell, dtype=torch.float64, device=dm.device)
+    keep = record or on_pair is not None
     sp = capi.streamer_params(mu=case.mu, A=case.A, B=case.B, De=case.De, dt=dt, solve=solve,
-                              warm=warm, extrapolate=extrapolate)
+                              warm=warm, extrapolate=extrapolate or (keep and warm is None))
     capi.fvgb_streamer_reset(dm.handle)
     capi.fvgb_set_graph_mode(dm.handle, graph)
-    infos, plain_pairs, extrap_pairs = [], [], []
-    qh, ph = [], []          # charges at the last step starts, potentials of the last steps
+    infos, pairs = [], ([], [])
+    bufs = [tuple(torch.empty_like(phi) for _ in range(3)) for _ in range(2)]
     for s in range(steps):
-        if record:
-            qh = (qh + [ni.double() - ne.double()])[-3:]
         infos += capi.fvgb_streamer_step(dm.handle, sp, ne, ni, phi, None, 1)
-        if record:
-            ph = (ph + [phi.clone()])[-3:]
-            if len(qh) >= 2:
-                plain_pairs.append((qh[-1] - qh[-2], ph[-2], ph[-1] - ph[-2]))
-            if len(qh) >= 3:
-                extrap_pairs.append(((qh[-1] - qh[-2]) - (qh[-2] - qh[-3]), ph[-2],
-                                     ph[-1] - 2.0 * ph[-2] + ph[-3]))
+        if not keep:
+            continue
+        for which in (0, 1):
+            if s < 1 + which:
+                continue
+            out = bufs[which] if on_pair is not None else tuple(torch.empty_like(phi) for _ in range(3))
+            capi.fvgb_streamer_pair(dm.handle, which, phi, *out)
+            if on_pair is not None:
+                on_pair(which, *out)
+            else:
+                pairs[which].append(out)
     capi.fvgb_set_graph_mode(dm.handle, False)
     if record:
-        return infos, plain_pairs, extrap_pairs
+        return infos, pairs[0], pairs[1]
     return infos, []
 
 
@@ -99,3 +105,94 @@ def train(net, pairs, epochs=2, lr=1e-3, seed=0, log_every=0):
 
 def mean_loss(net, pairs):
     return float(np.mean([capi.fvgb_mpnn_loss_grad(net, *p, want_grad=False)[0] for p in pairs]))
+
+
+def _rms_scales(sums, count, V, n_cell):
+    """Scales of fvgb_mpnn_set_scales from mean squares of dq, phi_prev, dphi."""
+    h2 = (1.0 / n_cell) ** (2.0 / 3.0)
+    rq, rp, rd = (float(torch.sqrt(x / count)) for x in sums)
+    return max(E_OVER_EPS0 * rq * h2 / V, 1e-30), max(rp / V, 1e-30), max(rd / V, 1e-30)
+
+
+def train_streaming(dm, mesh, cases, dt, steps, solve, V, lr=1e-3, lr_final=3e-4, seed=0,
+                    log_every=25, log=None):
+    """Train the two networks of the learned start (start from the previous potential, and
+    correction of the extrapolation) while the solver generates their pairs: one Adam step
+    per pair, as each streamer step of each case produces it, so that no pair is stored.
+    The normalisation scales come from a first run of cases[0]. The cases run in a seeded
+    random order; the last third of them with the smaller learning rate.
+
+    Returns ({False: (theta, scales), True: (theta, scales)}, info)."""
+    nets = {}
+    sums = {w: [torch.zeros((), dtype=torch.float64, device=dm.device) for _ in range(3)] for w in (0, 1)}
+    count = {0: 0, 1: 0}
+
+    def acc(which, dq, pp, dp):
+        for k, x in enumerate((dq, pp, dp)):
+            sums[which][k] += torch.mean(x * x)
+        count[which] += 1
+
+    streamer_run(dm, cases[0], mesh, dt, steps, solve, on_pair=acc)
+    scales = {w: _rms_scales(sums[w], count[w], V, dm.n_cell) for w in (0, 1)}
+    for w in (0, 1):
+        nets[w] = capi.fvgb_mpnn_create(dm.handle, 1)
+        capi.fvgb_mpnn_set_params(nets[w], init_params(w))
+        capi.fvgb_mpnn_set_scales(nets[w], V, *scales[w])
+    order = np.random.default_rng(seed).permutation(len(cases))
+    hist = {0: [], 1: []}
+    n_pairs = {0: 0, 1: 0}
+    for rank, ci in enumerate(order):
+        rate = lr if rank < (2 * len(cases)) // 3 else lr_final
+
+        def step(which, dq, pp, dp):
+            want = n_pairs[which] % log_every == 0
+            loss = capi.fvgb_mpnn_train_step(nets[which], dq, pp, dp, rate, want_loss=want)
+            if want:
+                hist[which].append(loss)
+            n_pairs[which] += 1
+
+        streamer_run(dm, cases[ci], mesh, dt, steps, solve, on_pair=step)
+        if log:
+            log(f"trained on case {rank + 1}/{len(cases)}")
+    out = {}
+    for w in (0, 1):
+        out[bool(w)] = (capi.fvgb_mpnn_get_params(nets[w]), scales[w])
+        capi.fvgb_mpnn_free(nets[w])
+    info = {"pairs_trained": {"previous_phi": n_pairs[0], "extrapolated": n_pairs[1]},
+            "loss_first_last": {"previous_phi": [hist[0][0], hist[0][-1]] if hist[0] else None,
+                                "extrapolated": [hist[1][0], hist[1][-1]] if hist[1] else None},
+            "loss_history_every": log_every,
+            "scales": {"previous_phi": scales[0], "extrapolated": scales[1]},
+            "learning_rates": [lr, lr_final]}
+    return out, info
+
+
+def held_out_run(dm, mesh, case, dt, steps, solve, V, net=None, extrapolate=False, skip=2):
+    """Steps of a held-out case with the learned start ``net`` = (theta, scales) or without
+    it; returns inner / outer iterations and device time summed over steps skip.., the
+    largest relative residual and how many learned starts passed the residual check."""
+    handle = None
+    if net is not None:
+        handle = capi.fvgb_mpnn_create(dm.handle, 1)
+        capi.fvgb_mpnn_set_params(handle, net[0])
+        capi.fvgb_mpnn_set_scales(handle, V, *net[1])
+    ne0, ni0 = case.initial(mesh)
+    ne, ni = dm.to_device(ne0), dm.to_device(ni0)
+    phi = torch.zeros(dm.n_cell, dtype=torch.float64, device=dm.device)
+    sp = capi.streamer_params(mu=case.mu, A=case.A, B=case.B, De=case.De, dt=dt, solve=solve,
+                              warm=handle, extrapolate=extrapolate)
+    capi.fvgb_streamer_reset(dm.handle)
+    capi.fvgb_set_graph_mode(dm.handle, False)
+    capi.fvgb_streamer_step(dm.handle, sp, ne, ni, phi, None, skip)
+    capi.fvgb_stats_get(dm.handle, reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    infos = capi.fvgb_streamer_step(dm.handle, sp, ne, ni, phi, None, steps - skip)
+    e1.record()
+    torch.cuda.synchronize()
+    st = capi.fvgb_stats_get(dm.handle, reset=True)
+    if handle is not None:
+        capi.fvgb_mpnn_free(handle)
+    return {"inner": sum(i["inner_its_total"] for i in infos), "outer": sum(i["outer_its"] for i in infos),
+            "ms": e0.elapsed_time(e1), "max_rel_res": max(i["rel_res"] for i in infos),
+            "accepted_steps": st["learned_kept"], "steps": len(infos)}
