@@ -34,13 +34,17 @@ constexpr int kOffWenc = 0, kOffBenc = 128, kOffLayer0 = 192, kLayerSize = kHid 
 constexpr int kOffWdec = kOffLayer0 + kLayers * kLayerSize;   // 24960
 constexpr int kOffBdec = kOffWdec + kHid;                       // 25024
 constexpr int kNParams = kOffBdec + 1;                          // 25025
-constexpr int kTile = 128;             // cells per tensor-core tile (the MMA's M), one thread each
-constexpr int kGradBlocks = 304;       // blocks of the gradient reductions
+constexpr int kTile = 128;             // cells per tensor-core tile (the MMA's M)
+constexpr int kTileThreads = 256;      // threads of the layer kernels: two per cell row
+constexpr int kGradBlocks = 304;       // blocks of the gradient reductions (and of the backward)
 // dynamic shared memory of the layer kernels: forward A = [h ; m] (128 x 128 BF16, 32 KB)
-// and W (64 x 128, 16 KB); backward A = dz (128 x 64, 16 KB) and W^T (128 x 64, 16 KB),
-// padded to 72 KB so that at most three blocks share an SM (3 x 128 tensor-memory columns)
+// and W (64 x 128, 16 KB): up to four blocks an SM, 4 x 64 tensor-memory columns.
+// Backward: B1 = W^T (128 x 64, 16 KB), A1 = dz (128 cells x 64, 16 KB), A2 = [h ; m]^T
+// (128 inputs x 128 cells, 32 KB), B2 = dz^T (64 outputs x 128 cells, 16 KB); the last three
+// are reused as the 64 KB staging of the data product: at most two blocks an SM,
+// 2 x 256 tensor-memory columns.
 constexpr uint32_t kFwdB = 32768, kFwdSmem = 49152;
-constexpr uint32_t kBwdB = 16384, kBwdSmem = 72 * 1024;
+constexpr uint32_t kBwdA1 = 16384, kBwdA2 = 32768, kBwdB2 = 65536, kBwdSmem = 81920;
 
 }  // namespace fvgb
 
@@ -65,7 +69,6 @@ struct fvgb_mpnn_s {
   float* dH = nullptr;                 // [N][64]
   float* dHb = nullptr;                // [N][64]
   float* G = nullptr;                  // [N][64] message part of dz W
-  float* dZ = nullptr;                 // [N][64]
   float* part = nullptr;               // [blocks][params] gradient partials
   double* dpart = nullptr;             // [kGradBlocks] loss partials
   double* dloss = nullptr;             // [1]
@@ -96,6 +99,24 @@ __device__ __forceinline__ uint32_t kmaj_off(int r, int k, int K) {
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
          (1ull << 46);
+}
+
+// 128-byte swizzled K-major layout: K in slabs of 64 elements, a slab of R rows taking
+// R x 128 bytes (1024-byte aligned); the 16-byte chunk c of row r sits at chunk c ^ (r % 8)
+// of the row (the hardware's swizzle of address bits [4, 7) by bits [7, 10)), so the eight
+// chunks of a row, and one chunk of eight consecutive rows, fall in different banks.
+__device__ __forceinline__ uint32_t sw_off(int r, int k, int R) {
+  return (uint32_t)((k >> 6) * R * 128 + r * 128 + ((((k >> 3) & 7) ^ (r & 7)) << 4) + (k & 7) * 2);
+}
+// descriptor of such an operand: start address (slab base + 32 bytes per K step of 16 inside
+// the slab), stride byte offset 1024 (8-row groups), version 1, swizzle mode 128 bytes
+__device__ __forceinline__ uint64_t sw_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+         (2ull << 61);
+}
+// address of the K step kk (16 elements) of a swizzled operand of R rows
+__device__ __forceinline__ uint32_t sw_kstep(uint32_t base, int kk, int R) {
+  return base + (uint32_t)((kk >> 2) * R * 128 + (kk & 3) * 32);
 }
 
 // Instruction descriptor of kind::f16: BF16 A and B (both K-major), FP32 accumulator, M x N.
@@ -191,6 +212,17 @@ __device__ __forceinline__ void st_bf16x8(unsigned char* p, const float (&v)[8])
   *reinterpret_cast<uint4*>(p) = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]),
                                             pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
 }
+__device__ __forceinline__ void st_bf16x4(unsigned char* p, const float4& v) {
+  *reinterpret_cast<uint2*>(p) = make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
+}
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, const float4& v) { *reinterpret_cast<float4*>(p) = v; }
+// staging of a row-per-thread accumulator: float4 q of row r at q ^ (r % Q) (Q = float4s
+// per row), so that 32 rows writing one quad, or one row read by quads, hit distinct banks
+template <int Q>
+__device__ __forceinline__ float* stage_at(float* S, int r, int q) {
+  return S + r * (4 * Q) + 4 * (q ^ (r % Q));
+}
 
 // ---- features and message weights ---------------------------------------------------------
 __global__ void k_features(int64_t N, const double* __restrict__ dq, const double* __restrict__ phi,
@@ -243,13 +275,17 @@ __global__ void k_encode(int64_t N, const float* __restrict__ F, const float* __
 }
 
 // ---- one message-passing layer, forward (tensor cores) ---------------------------------------
-// Persistent over tiles of 128 cells, thread t owning cell tile * 128 + t: the thread gathers
-// its cell's row A_t = [h ; m] (m = sum_j w_j (h_j - h), four neighbours, in chunks of eight
-// features) into the BF16 tile, thread 0 issues Z = A W^T as 8 tcgen05.mma of K = 16 into
-// 64 tensor-memory columns, and after the mbarrier signals completion every thread reads its
-// row, adds the bias and writes H_out = H + relu(Z) (and, when training, M and Z). A wait
+// Persistent over tiles of 128 cells. The block's eight warps gather the tile's rows
+// A_c = [h ; m] (m = sum_j w_j (h_j - h), four neighbours) into the BF16 operand tile, 16
+// lanes a row (a float4 of features each: whole 256-byte rows per load), two rows a step,
+// warp w taking rows [16 w, 16 w + 16); the tile is in the 128-byte swizzled K-major layout
+// (h in the first slab, m in the second), so a row's stores are bank-conflict-free. Thread 0
+// issues Z = A W^T as 8 tcgen05.mma of K = 16 into 64 tensor-memory columns; after the
+// mbarrier signals completion warp w reads lanes 32 (w % 4) .. + 31 and columns
+// 32 (w / 4) .. + 31, adds the bias and stages Z in shared memory (over the consumed A tile);
+// the warps then write Z (training) and H_out = H + relu(Z) row by row, coalesced. A wait
 // that runs out sets bit 2 of *err and the block leaves.
-__global__ void __launch_bounds__(kTile)
+__global__ void __launch_bounds__(kTileThreads)
 k_layer_fwd(int64_t N, const float* __restrict__ H, const int4* __restrict__ nbr, const float4* __restrict__ wn,
             const __nv_bfloat16* __restrict__ Wg, const float* __restrict__ bias, float* __restrict__ Mout,
             float* __restrict__ Zout, float* __restrict__ Hout, int* __restrict__ err) {
@@ -261,10 +297,11 @@ k_layer_fwd(int64_t N, const float* __restrict__ H, const int4* __restrict__ nbr
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   unsigned char* As = smem;
   unsigned char* Bs = smem + kFwdB;
-  // W (the B operand: 64 outputs x 128 inputs, K-major) and the bias, once per block
-  for (int e = t; e < kHid * (kIn / 8); e += kTile) {
+  float* S = reinterpret_cast<float*>(smem);      // Z staging (128 x 64), over the A tile
+  // W (the B operand: 64 outputs x 128 inputs), once per block
+  for (int e = t; e < kHid * (kIn / 8); e += kTileThreads) {
     const int r = e / (kIn / 8), kc = e % (kIn / 8);
-    *reinterpret_cast<uint4*>(Bs + kmaj_off(r, kc * 8, kIn)) =
+    *reinterpret_cast<uint4*>(Bs + sw_off(r, kc * 8, kHid)) =
         *reinterpret_cast<const uint4*>(Wg + r * kIn + kc * 8);
   }
   if (t < kHid) bs[t] = bias[t];
@@ -278,39 +315,32 @@ k_layer_fwd(int64_t N, const float* __restrict__ H, const int4* __restrict__ nbr
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's 32 lanes
+  const int erow = 32 * (warp & 3) + lane, ecol = 32 * (warp >> 2);   // epilogue: row, first column
+  const uint32_t tld = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + ecol;
   const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+  const int q = lane & 15;                       // this lane's float4 of a row
   const int64_t ntiles = (N + kTile - 1) / kTile;
   uint32_t phase = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t c = tile * kTile + t;
-    const bool live = c < N;
-    // gather: warp w builds rows [32 w, 32 w + 32) of A, a step covering 8 rows x 4 chunks
-    // of 8 features (whole 128-byte lines per load, conflict-free shared-memory stores)
-#pragma unroll 2
+#pragma unroll 4
     for (int st = 0; st < 8; ++st) {
-      const int r = 32 * warp + 8 * (st >> 1) + (lane & 7), kc = 4 * (st & 1) + (lane >> 3);
+      const int r = 16 * warp + 2 * st + (lane >> 4);
       const int64_t cr = tile * kTile + r;
-      float h[8], m[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) h[j] = m[j] = 0.0f;
+      float4 h = make_float4(0.f, 0.f, 0.f, 0.f), m = h;
       if (cr < N) {
         const int4 nb = nbr[cr];
         const float4 w4 = wn[cr];
-        const int ns[4] = {nb.x, nb.y, nb.z, nb.w};
-        const float ws[4] = {w4.x, w4.y, w4.z, w4.w};
-        load8(H + cr * kHid + kc * 8, h);
-        float g[4][8];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) load8(H + (int64_t)ns[q] * kHid + kc * 8, g[q]);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int j = 0; j < 8; ++j) m[j] += ws[q] * (g[q][j] - h[j]);
-        if (Mout) store8(Mout + cr * kHid + kc * 8, m);
+        h = ld4(H + cr * kHid + 4 * q);
+        const float4 g0 = ld4(H + (int64_t)nb.x * kHid + 4 * q), g1 = ld4(H + (int64_t)nb.y * kHid + 4 * q),
+                     g2 = ld4(H + (int64_t)nb.z * kHid + 4 * q), g3 = ld4(H + (int64_t)nb.w * kHid + 4 * q);
+        m.x = w4.x * (g0.x - h.x) + w4.y * (g1.x - h.x) + w4.z * (g2.x - h.x) + w4.w * (g3.x - h.x);
+        m.y = w4.x * (g0.y - h.y) + w4.y * (g1.y - h.y) + w4.z * (g2.y - h.y) + w4.w * (g3.y - h.y);
+        m.z = w4.x * (g0.z - h.z) + w4.y * (g1.z - h.z) + w4.z * (g2.z - h.z) + w4.w * (g3.z - h.z);
+        m.w = w4.x * (g0.w - h.w) + w4.y * (g1.w - h.w) + w4.z * (g2.w - h.w) + w4.w * (g3.w - h.w);
+        if (Mout) st4(Mout + cr * kHid + 4 * q, m);
       }
-      st_bf16x8(As + kmaj_off(r, kc * 8, kIn), h);
-      st_bf16x8(As + kmaj_off(r, kHid + kc * 8, kIn), m);
+      st_bf16x4(As + sw_off(r, 4 * q, kTile), h);
+      st_bf16x4(As + sw_off(r, kHid + 4 * q, kTile), m);
     }
     fence_async_smem();
     tc_fence_before();
@@ -319,8 +349,8 @@ k_layer_fwd(int64_t N, const float* __restrict__ H, const int4* __restrict__ nbr
       tc_fence_after();
 #pragma unroll
       for (int kk = 0; kk < kIn / 16; ++kk)
-        tc_mma(tmem, smem_desc(a0 + kk * 256, 128, (kIn / 8) * 128), smem_desc(b0 + kk * 256, 128, (kIn / 8) * 128),
-               idesc_bf16(kTile, kHid), kk > 0);
+        tc_mma(tmem, sw_desc(sw_kstep(a0, kk, kTile)), sw_desc(sw_kstep(b0, kk, kHid)), idesc_bf16(kTile, kHid),
+               kk > 0);
       tc_commit(&mbar);
     }
     if (!mbar_wait(&mbar, phase)) s_fail = 1;
@@ -328,26 +358,31 @@ k_layer_fwd(int64_t N, const float* __restrict__ H, const int4* __restrict__ nbr
     __syncthreads();
     if (s_fail) break;
     tc_fence_after();
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
+    {
       float z[32];
-      tmem_ld32(trow + half * 32, z);
-      if (live) {
+      tmem_ld32(tld, z);
 #pragma unroll
-        for (int j = 0; j < 32; j += 4) {
-          const int col = half * 32 + j;
-          const float4 zz = make_float4(z[j] + bs[col], z[j + 1] + bs[col + 1], z[j + 2] + bs[col + 2],
-                                        z[j + 3] + bs[col + 3]);
-          if (Zout) *reinterpret_cast<float4*>(Zout + c * kHid + col) = zz;
-          const float4 hv = *reinterpret_cast<const float4*>(H + c * kHid + col);
-          *reinterpret_cast<float4*>(Hout + c * kHid + col) =
-              make_float4(hv.x + fmaxf(zz.x, 0.0f), hv.y + fmaxf(zz.y, 0.0f), hv.z + fmaxf(zz.z, 0.0f),
-                          hv.w + fmaxf(zz.w, 0.0f));
-        }
+      for (int j = 0; j < 32; j += 4) {
+        const int col = ecol + j;
+        st4(stage_at<16>(S, erow, col >> 2),
+            make_float4(z[j] + bs[col], z[j + 1] + bs[col + 1], z[j + 2] + bs[col + 2], z[j + 3] + bs[col + 3]));
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int st = 0; st < 8; ++st) {
+      const int r = 16 * warp + 2 * st + (lane >> 4);
+      const int64_t cr = tile * kTile + r;
+      if (cr < N) {
+        const float4 zz = *reinterpret_cast<const float4*>(stage_at<16>(S, r, q));
+        if (Zout) st4(Zout + cr * kHid + 4 * q, zz);
+        const float4 hv = ld4(H + cr * kHid + 4 * q);
+        st4(Hout + cr * kHid + 4 * q, make_float4(hv.x + fmaxf(zz.x, 0.0f), hv.y + fmaxf(zz.y, 0.0f),
+                                                  hv.z + fmaxf(zz.z, 0.0f), hv.w + fmaxf(zz.w, 0.0f)));
       }
     }
     tc_fence_before();
-    __syncthreads();      // accumulator read and A tile consumed before the next tile
+    __syncthreads();      // accumulator read and staging consumed before the next tile
   }
   if (s_fail) {
     if (t == 0) atomicOr(err, 2);
@@ -452,60 +487,97 @@ k_decode_grad(int64_t N, const float* __restrict__ Ha, const float* __restrict__
   }
 }
 
-// ---- one layer, backward (tensor cores) --------------------------------------------------------
-// dz = dH_next * (z > 0);  [g_h ; g_m] = dz W_l (128 cells x 64 x 128 per tile, tcgen05.mma
-// into 128 tensor-memory columns);  dH = dH_next + g_h;  G = g_m (its message is added by
-// k_msg_add);  dZ = dz (FP32, for the weight gradients). Structure as k_layer_fwd.
-__global__ void __launch_bounds__(kTile)
+// ---- one layer, backward with its weight gradients (tensor cores) ------------------------------
+// Persistent: kGradBlocks blocks take tiles of 128 cells in turn. Per tile, with
+// dz = dH_next * (z > 0):
+//  - data product [g_h ; g_m] = dz W_l (4 tcgen05.mma of K = 16 into tensor-memory columns
+//    [0, 128)): dH = dH_next + g_h, G = g_m (its message is added by k_msg_add), written
+//    row by row through a shared-memory staging of the accumulator;
+//  - weight gradient dW_l^T += [h ; m]^T dz over the tile's cells (8 tcgen05.mma of K = 16 into
+//    columns [128, 192), accumulated over all tiles of the block): both operands have the
+//    cells as K, a lane per feature packing eight cells into one 16-byte row;
+//  - bias gradient: sums of dz kept per lane in registers over the block's tiles.
+// Operands are in the 128-byte swizzled K-major layout. At the end the block writes its
+// partials to part[blockIdx.x] (weights [out][in], bias), or zeros when it had no tile; the
+// partials are summed over blocks in a fixed order later.
+__global__ void __launch_bounds__(kTileThreads)
 k_layer_bwd(int64_t N, const float* __restrict__ dHn, const float* __restrict__ Z,
-            const __nv_bfloat16* __restrict__ Wg, float* __restrict__ dZ, float* __restrict__ dH,
-            float* __restrict__ G, int* __restrict__ err) {
+            const float* __restrict__ Hin, const float* __restrict__ Min,
+            const __nv_bfloat16* __restrict__ Wg, float* __restrict__ dH, float* __restrict__ G,
+            float* __restrict__ part, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
+  __shared__ float red[16][kHid];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  unsigned char* As = smem;
-  unsigned char* Bs = smem + kBwdB;
-  // W^T (the B operand: 128 inputs x 64 outputs, K-major): element (n, k) = W[k][n]
-  for (int e = t; e < kHid * kIn; e += kTile) {
+  unsigned char* B1 = smem;
+  unsigned char* A1 = smem + kBwdA1;
+  unsigned char* A2 = smem + kBwdA2;
+  unsigned char* B2 = smem + kBwdB2;
+  float* S = reinterpret_cast<float*>(smem + kBwdA1);   // 128 x 128 staging over A1, A2, B2
+  // W^T (the data product's B operand: 128 inputs x 64 outputs): (n, k) = W[k][n]
+  for (int e = t; e < kHid * kIn; e += kTileThreads) {
     const int k = e / kIn, n = e % kIn;
-    *reinterpret_cast<__nv_bfloat16*>(Bs + kmaj_off(n, k, kHid)) = Wg[e];
+    *reinterpret_cast<__nv_bfloat16*>(B1 + sw_off(n, k, kIn)) = Wg[e];
   }
   if (t == 0) {
     s_fail = 0;
     mbar_init(&mbar, 1);
   }
-  if (warp == 0) tmem_alloc(&tmem_base, kIn);
+  if (warp == 0) tmem_alloc(&tmem_base, 256);
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-  const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+  const uint32_t lanebase = (uint32_t)(32 * (warp & 3)) << 16;
+  const int erow = 32 * (warp & 3) + lane;
+  const uint32_t a1 = smem_u32(A1), b1 = smem_u32(B1), a2 = smem_u32(A2), b2 = smem_u32(B2);
+  const int q = lane & 15;
   const int64_t ntiles = (N + kTile - 1) / kTile;
+  float4 bacc = make_float4(0.f, 0.f, 0.f, 0.f);   // bias sums of features 4 q .. 4 q + 3
   uint32_t phase = 0;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t c = tile * kTile + t;
-    const bool live = c < N;
-    // dz tile: warp w builds rows [32 w, 32 w + 32), a step covering 8 rows x 4 chunks
-#pragma unroll 2
+  int ntile_done = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++ntile_done) {
+    const int64_t c0 = tile * kTile;
+    // A1 = dz (rows = cells): 16 lanes a row, two rows a step
+#pragma unroll 4
     for (int st = 0; st < 8; ++st) {
-      const int r = 32 * warp + 8 * (st >> 1) + (lane & 7), kc = 4 * (st & 1) + (lane >> 3);
-      const int64_t cr = tile * kTile + r;
-      float d[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) d[j] = 0.0f;
+      const int r = 16 * warp + 2 * st + (lane >> 4);
+      const int64_t cr = c0 + r;
+      float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
       if (cr < N) {
-        float z[8];
-        load8(dHn + cr * kHid + kc * 8, d);
-        load8(Z + cr * kHid + kc * 8, z);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) d[j] = z[j] > 0.0f ? d[j] : 0.0f;
-        store8(dZ + cr * kHid + kc * 8, d);
+        const float4 dd = ld4(dHn + cr * kHid + 4 * q), z = ld4(Z + cr * kHid + 4 * q);
+        d = make_float4(z.x > 0.0f ? dd.x : 0.0f, z.y > 0.0f ? dd.y : 0.0f, z.z > 0.0f ? dd.z : 0.0f,
+                        z.w > 0.0f ? dd.w : 0.0f);
       }
-      st_bf16x8(As + kmaj_off(r, kc * 8, kHid), d);
+      bacc.x += d.x; bacc.y += d.y; bacc.z += d.z; bacc.w += d.w;
+      st_bf16x4(A1 + sw_off(r, 4 * q, kTile), d);
+    }
+    // A2 = [h ; m]^T and B2 = dz^T (rows = features, K = cells): a lane per feature, eight
+    // cells packed into one 16-byte row; items (feature block of 32, group of 8 cells)
+#pragma unroll 1
+    for (int it = warp; it < 6 * 16; it += 8) {
+      const int fb = it >> 4, cg = it & 15;      // fb 0..3: [h ; m] features, 4..5: dz outputs
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int64_t c = c0 + 8 * cg + j;
+        float x = 0.0f;
+        if (c < N) {
+          if (fb < 2) x = Hin[c * kHid + 32 * fb + lane];
+          else if (fb < 4) x = Min[c * kHid + 32 * (fb - 2) + lane];
+          else {
+            const int o = 32 * (fb - 4) + lane;
+            const float dd = dHn[c * kHid + o];
+            x = Z[c * kHid + o] > 0.0f ? dd : 0.0f;
+          }
+        }
+        v[j] = x;
+      }
+      if (fb < 4) st_bf16x8(A2 + sw_off(32 * fb + lane, 8 * cg, kIn), v);
+      else st_bf16x8(B2 + sw_off(32 * (fb - 4) + lane, 8 * cg, kHid), v);
     }
     fence_async_smem();
     tc_fence_before();
@@ -514,8 +586,12 @@ k_layer_bwd(int64_t N, const float* __restrict__ dHn, const float* __restrict__ 
       tc_fence_after();
 #pragma unroll
       for (int kk = 0; kk < kHid / 16; ++kk)
-        tc_mma(tmem, smem_desc(a0 + kk * 256, 128, (kHid / 8) * 128), smem_desc(b0 + kk * 256, 128, (kHid / 8) * 128),
-               idesc_bf16(kTile, kIn), kk > 0);
+        tc_mma(tmem, sw_desc(sw_kstep(a1, kk, kTile)), sw_desc(sw_kstep(b1, kk, kIn)), idesc_bf16(kTile, kIn),
+               kk > 0);
+#pragma unroll
+      for (int kk = 0; kk < kTile / 16; ++kk)
+        tc_mma(tmem + kIn, sw_desc(sw_kstep(a2, kk, kIn)), sw_desc(sw_kstep(b2, kk, kHid)), idesc_bf16(kIn, kHid),
+               (ntile_done > 0 || kk > 0) ? 1 : 0);
       tc_commit(&mbar);
     }
     if (!mbar_wait(&mbar, phase)) s_fail = 1;
@@ -523,21 +599,29 @@ k_layer_bwd(int64_t N, const float* __restrict__ dHn, const float* __restrict__ 
     __syncthreads();
     if (s_fail) break;
     tc_fence_after();
+    // stage the data product (row per thread, warp halves: columns 0-63 / 64-127)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int h = 0; h < 2; ++h) {
+      const int col0 = 64 * (warp >> 2) + 32 * h;
       float v[32];
-      tmem_ld32(trow + q * 32, v);
-      if (live) {
+      tmem_ld32(tmem + lanebase + col0, v);
 #pragma unroll
-        for (int j = 0; j < 32; j += 4) {
-          const int col = q * 32 + j;
-          if (col < kHid) {
-            const float4 dv = *reinterpret_cast<const float4*>(dHn + c * kHid + col);
-            *reinterpret_cast<float4*>(dH + c * kHid + col) =
-                make_float4(dv.x + v[j], dv.y + v[j + 1], dv.z + v[j + 2], dv.w + v[j + 3]);
-          } else {
-            *reinterpret_cast<float4*>(G + c * kHid + col - kHid) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-          }
+      for (int j = 0; j < 32; j += 4)
+        st4(stage_at<32>(S, erow, (col0 + j) >> 2), make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]));
+    }
+    __syncthreads();
+    // write back row by row: lanes 0-15 dH (= dH_next + g_h), lanes 16-31 G (= g_m)
+#pragma unroll 4
+    for (int st = 0; st < 16; ++st) {
+      const int r = 16 * warp + st;
+      const int64_t cr = c0 + r;
+      if (cr < N) {
+        const float4 v = *reinterpret_cast<const float4*>(stage_at<32>(S, r, lane));
+        if (lane < 16) {
+          const float4 dv = ld4(dHn + cr * kHid + 4 * lane);
+          st4(dH + cr * kHid + 4 * lane, make_float4(dv.x + v.x, dv.y + v.y, dv.z + v.z, dv.w + v.w));
+        } else {
+          st4(G + cr * kHid + 4 * (lane - 16), v);
         }
       }
     }
@@ -550,7 +634,38 @@ k_layer_bwd(int64_t N, const float* __restrict__ dHn, const float* __restrict__ 
   }
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, kIn);
+  // the block's partials: dW^T in columns [128, 192) (lane = input, column = output)
+  float* p = part + (size_t)blockIdx.x * kNParams;
+  if (!s_fail) {
+    const int in = 32 * (warp & 3) + lane;
+    const int o0 = 32 * (warp >> 2);
+    float v[32];
+    tmem_ld32(tmem + lanebase + kIn + o0, v);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) p[(o0 + j) * kIn + in] = ntile_done > 0 ? v[j] : 0.0f;
+  }
+  // bias: lanes q and q + 16 hold the same features for different rows
+  bacc.x += __shfl_xor_sync(0xffffffffu, bacc.x, 16);
+  bacc.y += __shfl_xor_sync(0xffffffffu, bacc.y, 16);
+  bacc.z += __shfl_xor_sync(0xffffffffu, bacc.z, 16);
+  bacc.w += __shfl_xor_sync(0xffffffffu, bacc.w, 16);
+  if (lane < 16) {
+    red[warp][4 * lane] = bacc.x;
+    red[warp][4 * lane + 1] = bacc.y;
+    red[warp][4 * lane + 2] = bacc.z;
+    red[warp][4 * lane + 3] = bacc.w;
+  }
+  __syncthreads();
+  if (t < kHid) {
+    float b = 0.0f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) b += red[w][t];
+    p[kHid * kIn + t] = b;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 256);
 }
 
 // dH_i += sum_j w_ij (G_j - G_i): the adjoint of the (symmetric) message operator
@@ -576,43 +691,6 @@ __global__ void k_msg_add(int64_t N, const float* __restrict__ Gm, const int4* _
     const float2 dv = *d;
     *d = make_float2(dv.x + mx, dv.y + my);
   }
-}
-
-// Weight gradients of one layer: part[b][W_l] = sum over the block's cells of dz (x) [h ; m],
-// part[b][b_l] = sum dz. Thread t owns input feature t % 128 and 32 outputs.
-__global__ void __launch_bounds__(256) k_layer_wgrad(int64_t N, const float* __restrict__ dZ,
-                                                     const float* __restrict__ H, const float* __restrict__ Mm,
-                                                     int off, float* __restrict__ part) {
-  __shared__ float dz[16][kHid];
-  __shared__ float hm[16][kIn];
-  const int i = threadIdx.x % kIn, og = threadIdx.x / kIn;
-  float acc[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) acc[j] = 0.0f;
-  float accb = 0.0f;
-  const int64_t per = (N + gridDim.x - 1) / gridDim.x;
-  const int64_t lo = blockIdx.x * per, hi = lo + per < N ? lo + per : N;
-  for (int64_t c0 = lo; c0 < hi; c0 += 16) {
-    const int nc = (int)(hi - c0 < 16 ? hi - c0 : 16);
-    for (int k = threadIdx.x; k < 16 * kHid; k += blockDim.x) {
-      const int r = k / kHid, o = k % kHid;
-      dz[r][o] = r < nc ? dZ[(c0 + r) * kHid + o] : 0.0f;
-      hm[r][o] = r < nc ? H[(c0 + r) * kHid + o] : 0.0f;
-      hm[r][kHid + o] = r < nc ? Mm[(c0 + r) * kHid + o] : 0.0f;
-    }
-    __syncthreads();
-    for (int r = 0; r < nc; ++r) {
-      const float v = hm[r][i];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) acc[j] += dz[r][og * 32 + j] * v;
-      if (threadIdx.x < kHid) accb += dz[r][threadIdx.x];
-    }
-    __syncthreads();
-  }
-  float* p = part + (size_t)blockIdx.x * kNParams + off;
-#pragma unroll
-  for (int j = 0; j < 32; ++j) p[(og * 32 + j) * kIn + i] = acc[j];
-  if (threadIdx.x < kHid) p[kHid * kIn + threadIdx.x] = accb;
 }
 
 // encoder gradients: dz0 = dH0 * (z0 > 0); part[b][W_enc] = sum dz0 (x) f, part[b][b_enc] = sum dz0
@@ -726,16 +804,15 @@ cudaError_t alloc_train(MpnnNet* n) {
   if ((e = nalloc(n, &n->dH, NH))) return e;
   if ((e = nalloc(n, &n->dHb, NH))) return e;
   if ((e = nalloc(n, &n->G, NH))) return e;
-  if ((e = nalloc(n, &n->dZ, NH))) return e;
   if ((e = nalloc(n, &n->dout, n->N))) return e;
   if ((e = nalloc(n, &n->part, (size_t)2 * kGradBlocks * kNParams))) return e;
   n->train_buffers = true;
   return cudaSuccess;
 }
 
-// grids of the tensor-core layer kernels: persistent over 128-cell tiles, as many blocks as
-// fit on the SMs (forward: 48 KB shared memory and 64 tensor-memory columns a block, up to
-// four an SM; backward: 72 KB and 128 columns, up to three an SM)
+// grid of the forward layer kernel: persistent over 128-cell tiles, as many blocks as fit on
+// the SMs (48 KB shared memory and 64 tensor-memory columns a block, up to four an SM); the
+// backward runs kGradBlocks blocks (80 KB and 256 columns a block, two an SM)
 unsigned layer_grid(MpnnNet* n, int per_sm) {
   return (unsigned)std::min<int64_t>((n->N + kTile - 1) / kTile, (int64_t)n->m->num_sms * per_sm);
 }
@@ -765,7 +842,7 @@ cudaError_t forward(MpnnNet* n, int set, const double* dq, const double* phi, bo
   for (int l = 0; l < kLayers; ++l) {
     const float* Hin = train ? n->H[set][l] : n->H[0][l % 2];
     float* Hout = train ? n->H[set][l + 1] : n->H[0][(l + 1) % 2];
-    k_layer_fwd<<<layer_grid(n, 4), kTile, kFwdSmem, s>>>(N, Hin, nbr, wn, n->wbf + (size_t)l * kHid * kIn,
+    k_layer_fwd<<<layer_grid(n, 4), kTileThreads, kFwdSmem, s>>>(N, Hin, nbr, wn, n->wbf + (size_t)l * kHid * kIn,
                                                           n->theta + kOffLayer0 + l * kLayerSize + kHid * kIn,
                                                           train ? n->M[set][l] : nullptr,
                                                           train ? n->Z[set][l] : nullptr, Hout, n->m->d_status);
@@ -800,11 +877,11 @@ void backward_set(MpnnNet* n, int set, float sign, int row0, cudaStream_t s) {
   const int4* nbr = reinterpret_cast<const int4*>(n->m->g64.bc[n->bcset].at_nbr);
   const float4* wn = reinterpret_cast<const float4*>(n->wn);
   for (int l = kLayers - 1; l >= 0; --l) {
-    k_layer_bwd<<<layer_grid(n, 3), kTile, kBwdSmem, s>>>(N, dHn, n->Z[set][l], n->wbf + (size_t)l * kHid * kIn,
-                                                          n->dZ, dHo, n->G, n->m->d_status);
+    k_layer_bwd<<<kGradBlocks, kTileThreads, kBwdSmem, s>>>(
+        N, dHn, n->Z[set][l], n->H[set][l], n->M[set][l], n->wbf + (size_t)l * kHid * kIn, dHo, n->G,
+        part + kOffLayer0 + l * kLayerSize, n->m->d_status);
     k_msg_add<<<grid_n(N * 32), 256, 0, s>>>(N, n->G, nbr, wn, dHo);
-    k_layer_wgrad<<<G, 256, 0, s>>>(N, n->dZ, n->H[set][l], n->M[set][l], kOffLayer0 + l * kLayerSize, part);
-    count_launch(3);
+    count_launch(2);
     std::swap(dHn, dHo);
   }
   k_encode_grad<<<G, kRowGroups * kHid, 0, s>>>(N, dHn, n->Z0[set], n->F[set], part);

@@ -100,10 +100,9 @@ def test_training_reduces_loss(dev):
 
 def test_learned_warm_start_beats_previous_potential(dev):
     """Train on streamer runs of the plain solver (18 seeds), evaluate on 2 held-out seed
-    positions: the solves started from the learned guess (kept per part only where its
-    residual is smaller) take fewer CG iterations in total, every step still converged
-    to 1e-8. The same for the start from the linear extrapolation in time: it alone saves
-    most of the iterations; the network trained on its error costs no outer steps."""
+    positions: the solves started from the learned guess take fewer CG iterations in total,
+    every step still converged to 1e-8. The same on top of the start from the linear
+    extrapolation in time, which alone saves most of the iterations."""
     capi, device, learned = dev
     k = 16
     mesh = streamer_mesh(k, 301)
@@ -139,12 +138,13 @@ def test_learned_warm_start_beats_previous_potential(dev):
             outer[name] += sum(i["outer_its"] for i in a[2:])
     print("held-out CG iterations (inner / outer):",
           {n: (inner[n], outer[n]) for n in variants})
-    assert inner["learned"] < 0.9 * inner["plain"], inner
+    # the learned correction (in full where it lowers the residual, else residual-minimising
+    # scaled) saves CG iterations both from the previous potential and on top of the
+    # extrapolation; measured about 10 % each on this mesh
+    assert inner["learned"] < 0.95 * inner["plain"], inner
     assert outer["learned"] <= outer["plain"], outer
     assert inner["extrap"] < 0.6 * inner["plain"], inner
-    # the extrapolation error is smooth and global; the local network corrects little of
-    # it, and the residual safeguard keeps it from costing more than noise
-    assert inner["learned_extrap"] <= 1.05 * inner["extrap"], inner
+    assert inner["learned_extrap"] < 0.95 * inner["extrap"], inner
     assert outer["learned_extrap"] <= outer["extrap"], outer
     for net in nets:
         capi.fvgb_mpnn_free(net)
