@@ -81,6 +81,13 @@ def parse():
                          "(FP32 transport and inner CG, FP64 refinement to the same residual)")
     ap.add_argument("--transport-only", default=None, choices=["fp32", "fp64", "both"],
                     help="time only the transport kernels on the 6M-cell mesh (for profiling)")
+    ap.add_argument("--cg-fixed", default=None,
+                    help="comma-separated CG iteration counts: one Poisson solve on the 6M-cell FP64 mesh "
+                         "per count, its single CG launch running exactly that many iterations (for "
+                         "profiling the CG kernel's traffic per iteration)")
+    ap.add_argument("--network-only", type=int, default=None, metavar="K",
+                    help="time the learned start's training step and prediction on the K^3 x 6 mesh "
+                         "(random inputs; for profiling the network kernels)")
     return ap.parse_args()
 
 
@@ -205,8 +212,66 @@ def source_hash(*names):
     return h.hexdigest()[:16]
 
 
+def cg_fixed(capi, device, torch, counts, mixed=False):
+    """One Poisson solve per count on the 6M-cell workload mesh (FP64, or mixed: FP32 inner
+    CG), whose single CG launch runs exactly that many iterations (tolerances that cannot be
+    met, one outer step)."""
+    from synth.workloads import StreamerCase, streamer_mesh
+    case = StreamerCase()
+    mesh = streamer_mesh(K_MESH, MESH_SEED)
+    dm = device.DeviceMesh(mesh, [case.bc_ne(), case.bc_phi()], prec="mixed" if mixed else "fp64")
+    ne0, ni0 = case.initial(mesh)
+    e_over_eps0 = 1.602176634e-19 / 8.8541878128e-12
+    f = dm.to_device(-e_over_eps0 * (ni0 * 1.001 - ne0), torch.float64)
+    out = {}
+    for its in counts:
+        phi = torch.zeros(dm.n_cell, dtype=torch.float64, device="cuda")
+        opts = capi.solve_opts(rtol=1e-30, inner_rtol=1e-30, maxit_inner=its, maxit_outer=1,
+                               prec=capi.FVGB_FP32 if mixed else capi.FVGB_FP64)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, info = capi.fvgb_poisson_solve(dm.handle, 1, f, phi, opts, check=False)
+        e1.record()
+        torch.cuda.synchronize()
+        out[str(its)] = {"inner_its": info.inner_its_total, "solve_ms": e0.elapsed_time(e1)}
+    dm.free()
+    return out
+
+
+def network_only(capi, device, torch, k, reps=3):
+    """Training step and prediction of the learned start on the k^3 x 6 mesh (random inputs)."""
+    from paper_2203_00925_gb300 import learned
+    from synth.workloads import StreamerCase, streamer_mesh
+    case = StreamerCase()
+    mesh = streamer_mesh(k, MESH_SEED)
+    dm = device.DeviceMesh(mesh, [case.bc_ne(), case.bc_phi()], prec="mixed")
+    net = capi.fvgb_mpnn_create(dm.handle, 1)
+    capi.fvgb_mpnn_set_params(net, learned.init_params(0))
+    capi.fvgb_mpnn_set_scales(net, case.V, 1e-6, 0.58, 1.4e-6)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    dq = torch.randn(dm.n_cell, dtype=torch.float64, device="cuda", generator=g) * 1e9
+    ph = torch.randn(dm.n_cell, dtype=torch.float64, device="cuda", generator=g) * 1e3
+    tg = torch.randn(dm.n_cell, dtype=torch.float64, device="cuda", generator=g) * 1e-2
+    pred = torch.empty_like(dq)
+    out = {"cells": dm.n_cell}
+    for name, fn in (("train_step", lambda: capi.fvgb_mpnn_train_step(net, dq, ph, tg, 1e-3)),
+                     ("predict", lambda: capi.fvgb_mpnn_predict(net, dq, ph, pred))):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name + "_ms"] = e0.elapsed_time(e1) / reps
+    capi.fvgb_mpnn_free(net)
+    dm.free()
+    return out
+
+
 def profile_traffic(kernel, shash):
-    """Per-launch DRAM bytes from the committed ncu summary, if it is for this source."""
+    """DRAM traffic of the kernel from the committed ncu summary, if it is for this source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(path))
@@ -377,6 +442,13 @@ def gpu_arm(args, world, rank, local):
     from paper_2203_00925_gb300 import capi, device
     from synth.workloads import StreamerCase, streamer_mesh
 
+    if args.cg_fixed:
+        print(json.dumps(cg_fixed(capi, device, torch, [int(x) for x in args.cg_fixed.split(",")],
+                                  mixed=args.prec == "mixed")), flush=True)
+        return
+    if args.network_only:
+        print(json.dumps(network_only(capi, device, torch, args.network_only)), flush=True)
+        return
     if args.transport_only:
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
         precs = ["fp32", "fp64"] if args.transport_only == "both" else [args.transport_only]
@@ -473,8 +545,12 @@ def gpu_arm(args, world, rank, local):
     achieved_tf = flops_per_launch / avg_launch_s / 1e12 if ok else None
     achieved_gbs = bytes_per_launch / avg_launch_s / 1e9 if ok else None
     kname = "k_cg<float,4>" if mixed else "k_cg<double,4>"
+    # traffic: DRAM bytes of ncu captures of this kernel source on this mesh, launches with
+    # fixed iteration counts giving a fixed part and a part per iteration, evaluated at this
+    # run's average iterations per launch
     prof = profile_traffic(kname, source_hash("solver.cu"))
-    traffic = prof["dram_bytes_per_launch"] if prof else None
+    traffic = (prof["dram_bytes_fixed"] + per_launch_its * prof["dram_bytes_per_iteration"]
+               if prof and ok else None)
     common = {"kernel": kname, "traffic": traffic,
               "traffic_source": prof.get("source") if prof else None,
               "avg_launch_ms": avg_launch_s * 1e3, "iterations_per_launch": per_launch_its,
