@@ -524,9 +524,9 @@ def gpu_arm(args, world, rank, local):
     log(f"headline {total_ms / args.steps:.2f} ms/step")
 
     # ---- roofline of the dominant kernel: the persistent CG kernel ------------------------
-    # Per CG iteration and cell: operator (ELL-4 indices 16 B, 4 coefficients, diagonal, r and
-    # its 4 neighbours as cache hits, p, q read and written) and the x/r phase (x, p, r, q
-    # read, x, r written): 16 w + 16 bytes; flops 9 (operator) + 12 (four updates, two dots).
+    # Per CG iteration and cell: the p/q phase (ELL-4 indices 16 B, 4 coefficients, diagonal,
+    # r and its 4 neighbours as cache hits, p, q and x read and written) and the r phase (r, q
+    # read, r written): 15 w + 16 bytes; flops 9 (operator) + 12 (four updates, two dots).
     # Per launch add the initial pass (r = rhs, zeroed p, q, x) and the first operator apply.
     # At 6M cells the iteration's working set (~860 MB FP64) is far above L2, so both the HBM
     # and the FP64-pipe views apply; the line reports the one with the larger fraction as the
@@ -535,7 +535,7 @@ def gpu_arm(args, world, rank, local):
     its, launches = stats["cg_iterations"], max(stats["cg_launches"], 1)
     per_launch_its = its / launches
     flops_per_launch = N * (per_launch_its * 21 + 13)
-    bytes_per_launch = N * (per_launch_its * (16 * w + 16) + 10 * w + 24)
+    bytes_per_launch = N * (per_launch_its * (15 * w + 16) + 10 * w + 24)
     avg_launch_s = stats["cg_ms"] / 1e3 / launches
     props = torch.cuda.get_device_properties(local)
     peak_tflops = props.multi_processor_count * 2 * 2 * 2.070e9 / 1e12

@@ -217,29 +217,28 @@ __host__ __device__ constexpr int unroll_rows() { return sizeof(T) == 4 ? 4 : 2;
 template <typename T>
 __host__ __device__ constexpr int unroll_rows_xr() { return 4; }
 
-// CG phase 1 on rows [lo, hi): x += alpha p, r -= alpha q; returns the thread's sum of r^2.
+// CG phase 1 on rows [lo, hi): r -= alpha q; returns the thread's sum of r^2. (The matching
+// x += alpha p is deferred to the next phase 2, which reads p anyway, or to the final pass:
+// the same additions in the same order, without streaming x and p through this phase.)
 template <typename T>
-__device__ __forceinline__ T cg_phase_xr(const SolveArgs<T>& a, int64_t lo, int64_t hi, T alpha) {
+__device__ __forceinline__ T cg_phase_r(const SolveArgs<T>& a, int64_t lo, int64_t hi, T alpha) {
   constexpr int U = unroll_rows_xr<T>();
-  T* __restrict__ X = a.cx;
   T* __restrict__ R = a.cr;
-  const T* __restrict__ P = a.cp;
   const T* __restrict__ Q = a.cq;
   T acc = T(0);
   const int64_t bd = blockDim.x;
   for (int64_t b = lo + threadIdx.x; b < hi; b += U * bd) {
-    T x[U], p[U], r[U], q[U];
+    T r[U], q[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t i = b + u * bd;
-      if (i < hi) { x[u] = X[i]; p[u] = P[i]; r[u] = R[i]; q[u] = Q[i]; }
+      if (i < hi) { r[u] = R[i]; q[u] = Q[i]; }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t i = b + u * bd;
       if (i < hi) {
         const T rn = r[u] - alpha * q[u];
-        X[i] = x[u] + alpha * p[u];
         R[i] = rn;
         acc += rn * rn;
       }
@@ -248,19 +247,29 @@ __device__ __forceinline__ T cg_phase_xr(const SolveArgs<T>& a, int64_t lo, int6
   return acc;
 }
 
-// CG phase 2 on rows [lo, hi): p = r + beta p, q = A_T r + beta q (= A_T p); returns the
-// thread's sum of p.q. Neighbours' r are read through L2 (other blocks wrote them).
+// The deferred x += alpha p of the last phase 1 of a part (rows [lo, hi)).
 template <typename T>
-__device__ __forceinline__ T cg_phase_pq(const SolveArgs<T>& a, int64_t lo, int64_t hi, T beta) {
+__device__ __forceinline__ void cg_phase_x(const SolveArgs<T>& a, int64_t lo, int64_t hi, T alpha) {
+  T* __restrict__ X = a.cx;
+  const T* __restrict__ P = a.cp;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) X[i] = X[i] + alpha * P[i];
+}
+
+// CG phase 2 on rows [lo, hi): x += alpha p (the previous phase 1's update, with the old p),
+// p = r + beta p, q = A_T r + beta q (= A_T p); returns the thread's sum of p.q. Neighbours'
+// r are read through L2 (other blocks wrote them).
+template <typename T>
+__device__ __forceinline__ T cg_phase_pq(const SolveArgs<T>& a, int64_t lo, int64_t hi, T beta, T alpha) {
   constexpr int U = unroll_rows<T>();
   T* __restrict__ P = a.cp;
   T* __restrict__ Q = a.cq;
+  T* __restrict__ X = a.cx;
   const T* __restrict__ R = a.cr;
   const int4* __restrict__ NB = reinterpret_cast<const int4*>(a.at_nbr);
   T acc = T(0);
   const int64_t bd = blockDim.x;
   for (int64_t b = lo + threadIdx.x; b < hi; b += U * bd) {
-    T r[U], p[U], q[U], d[U], g[U][4];
+    T r[U], p[U], q[U], x[U], d[U], g[U][4];
     int4 nb[U];
     Coef4<T> c[U];
 #pragma unroll
@@ -268,7 +277,7 @@ __device__ __forceinline__ T cg_phase_pq(const SolveArgs<T>& a, int64_t lo, int6
       const int64_t i = b + u * bd;
       if (i < hi) {
         nb[u] = __ldg(NB + i);
-        r[u] = R[i]; p[u] = P[i]; q[u] = Q[i];
+        r[u] = R[i]; p[u] = P[i]; q[u] = Q[i]; x[u] = X[i];
         d[u] = __ldg(a.at_diag + i);
         c[u].load(a.at_coef, i);
       }
@@ -294,6 +303,7 @@ __device__ __forceinline__ T cg_phase_pq(const SolveArgs<T>& a, int64_t lo, int6
         y -= c[u].c[3] * g[u][3];
         const T pn = r[u] + beta * p[u];
         const T qn = y + beta * q[u];
+        X[i] = x[u] + alpha * p[u];
         P[i] = pn;
         Q[i] = qn;
         acc += pn * qn;
@@ -314,6 +324,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
   __shared__ T s_alpha[kMaxParts], s_beta[kMaxParts];
   __shared__ int s_cg[kMaxParts];      // 0 running, 1 converged, 2 breakdown, 3 idle
   __shared__ int s_inner[kMaxParts];
+  __shared__ int s_pend[kMaxParts];    // x += alpha p of the part's last phase 1 not yet applied
   __shared__ int s_flag, s_status;
   const unsigned G = gridDim.x;
   const int P = a.n_part;
@@ -323,7 +334,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
   int total_its = 0;
   unsigned target = 0;
   if (threadIdx.x == 0) s_status = 0;
-  for (int p = threadIdx.x; p < P; p += blockDim.x) s_inner[p] = 0;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) { s_inner[p] = 0; s_pend[p] = 0; }
 
   // r = rhs on active parts (0 elsewhere), p = q = x = 0; the first p/q phase (beta = 0)
   // then gives p = r, q = A_T r
@@ -345,7 +356,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
         const T ri = a.cr[i];
         l0 += ri * ri;
       }
-      l1 = cg_phase_pq<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], T(0));
+      l1 = cg_phase_pq<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], T(0), T(0));
     }
     const double t0 = cg_block_sum((double)l0, sh, many);
     const double t1 = cg_block_sum((double)l1, sh, many);
@@ -374,7 +385,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
     for (int sc = sc0; sc < sc1; ++sc) {
       const int p = a.sc_part[sc];
       if (s_cg[p] == 0) {             // uniform in the block
-        const double t = cg_block_sum((double)cg_phase_xr<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], s_alpha[p]), sh, many);
+        const double t = cg_block_sum((double)cg_phase_r<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], s_alpha[p]), sh, many);
         if (threadIdx.x == 0) buf[sc] = t;
       } else if (threadIdx.x == 0) {
         buf[sc] = 0.0;
@@ -387,6 +398,7 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
     __syncthreads();
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
       if (s_cg[p] != 0) continue;
+      s_pend[p] = 1;
       s_inner[p] += 1;
       const double rrn = tot[p];
       if (!isfinite(rrn)) { s_cg[p] = 2; continue; }
@@ -402,7 +414,8 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
     for (int sc = sc0; sc < sc1; ++sc) {
       const int p = a.sc_part[sc];
       if (s_cg[p] == 0) {             // uniform in the block
-        const double t = cg_block_sum((double)cg_phase_pq<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], s_beta[p]), sh, many);
+        const double t = cg_block_sum((double)cg_phase_pq<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], s_beta[p],
+                                                             s_alpha[p]), sh, many);
         if (threadIdx.x == 0) buf[sc] = t;
       } else if (threadIdx.x == 0) {
         buf[sc] = 0.0;
@@ -412,11 +425,18 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
     part_totals<T, 1>(a, buf, tot, stage);
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
       if (s_cg[p] != 0) continue;
+      s_pend[p] = 0;                  // phase 2 applied the pending x update
       const double pq = tot[p];
       if (!(pq > 0.0) || !isfinite(pq)) { s_cg[p] = 2; continue; }
       s_alpha[p] = (T)(s_rr[p] / pq);
     }
     __syncthreads();
+  }
+  // the parts whose last phase was a phase 1: apply its deferred x += alpha p (own rows only)
+  __syncthreads();
+  for (int sc = sc0; sc < sc1; ++sc) {
+    const int p = a.sc_part[sc];
+    if (s_pend[p]) cg_phase_x<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], s_alpha[p]);
   }
   for (int p = threadIdx.x; p < P; p += blockDim.x)
     if (s_cg[p] == 2) s_status = 6;
