@@ -111,7 +111,7 @@ fvgb_status fvgb_mesh_upload(int32_t dim, int64_t n_vert, const double* xyz,
                              const fvgb_bcset* bcsets, int32_t reorder, int32_t prec,
                              void* stream, fvgb_mesh* out);
 
-/* One mesh of an ensemble (BASELINE's batched workload: many independent meshes
+/* One mesh of an ensemble (the batched workload: many independent meshes
  * advanced together). Arrays as in fvgb_mesh_upload; bcsets points at n_bcset sets for
  * this mesh (the same number for every mesh; tags are the mesh's own). */
 typedef struct {
