@@ -239,33 +239,35 @@ def cg_fixed(capi, device, torch, counts, mixed=False):
 
 
 def network_only(capi, device, torch, k, reps=3):
-    """Training step and prediction of the learned start on the k^3 x 6 mesh (random inputs)."""
+    """Training step and prediction of the learned start on the k^3 x 6 mesh (random
+    inputs), for the multilevel and the local architecture."""
     from paper_2203_00925_gb300 import learned
     from synth.workloads import StreamerCase, streamer_mesh
     case = StreamerCase()
     mesh = streamer_mesh(k, MESH_SEED)
     dm = device.DeviceMesh(mesh, [case.bc_ne(), case.bc_phi()], prec="mixed")
-    net = capi.fvgb_mpnn_create(dm.handle, 1)
-    capi.fvgb_mpnn_set_params(net, learned.init_params(0))
-    capi.fvgb_mpnn_set_scales(net, case.V, 1e-6, 0.58, 1.4e-6)
     g = torch.Generator(device="cuda").manual_seed(0)
     dq = torch.randn(dm.n_cell, dtype=torch.float64, device="cuda", generator=g) * 1e9
     ph = torch.randn(dm.n_cell, dtype=torch.float64, device="cuda", generator=g) * 1e3
     tg = torch.randn(dm.n_cell, dtype=torch.float64, device="cuda", generator=g) * 1e-2
     pred = torch.empty_like(dq)
     out = {"cells": dm.n_cell}
-    for name, fn in (("train_step", lambda: capi.fvgb_mpnn_train_step(net, dq, ph, tg, 1e-3)),
-                     ("predict", lambda: capi.fvgb_mpnn_predict(net, dq, ph, pred))):
-        fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
+    for arch, ml in (("multilevel", True), ("local", False)):
+        net = capi.fvgb_mpnn_create(dm.handle, 1, multilevel=ml)
+        capi.fvgb_mpnn_set_params(net, learned.init_params(0, ml))
+        capi.fvgb_mpnn_set_scales(net, case.V, 1e-6, 0.58, 1.4e-6)
+        for name, fn in (("train_step", lambda: capi.fvgb_mpnn_train_step(net, dq, ph, tg, 1e-3)),
+                         ("predict", lambda: capi.fvgb_mpnn_predict(net, dq, ph, pred))):
             fn()
-        e1.record()
-        torch.cuda.synchronize()
-        out[name + "_ms"] = e0.elapsed_time(e1) / reps
-    capi.fvgb_mpnn_free(net)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            out[f"{arch}_{name}_ms"] = e0.elapsed_time(e1) / reps
+        capi.fvgb_mpnn_free(net)
     dm.free()
     return out
 
@@ -394,7 +396,7 @@ def ensemble_block(capi, device, torch, stream, warm, nets):
     for name, (theta_sc, extrap, inner) in runs.items():
         net = None
         if theta_sc is not None:
-            net = capi.fvgb_mpnn_create(dm.handle, 1)
+            net = capi.fvgb_mpnn_create(dm.handle, 1, multilevel=theta_sc[2])
             capi.fvgb_mpnn_set_params(net, theta_sc[0])
             capi.fvgb_mpnn_set_scales(net, c0.V, *theta_sc[1])
         sp = capi.streamer_params(mu=c0.mu, A=c0.A, B=c0.B, De=c0.De, dt=dt, warm=net,
@@ -632,8 +634,8 @@ def gpu_arm(args, world, rank, local):
             meshv, casev, dtv = meshv or mesh, casev or case, dtv or dt
             net = None
             if warm is not None:
-                theta, scales = nets[extrap]
-                net = capi.fvgb_mpnn_create(dmv.handle, 1)
+                theta, scales, ml = nets[extrap]
+                net = capi.fvgb_mpnn_create(dmv.handle, 1, multilevel=ml)
                 capi.fvgb_mpnn_set_params(net, theta)
                 capi.fvgb_mpnn_set_scales(net, casev.V, *scales)
             spv = capi.streamer_params(

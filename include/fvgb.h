@@ -447,18 +447,42 @@ fvgb_status fvgb_streamer_pair(fvgb_mesh m, int32_t which, const double* phi_dev
 /* ---- Learned warm start (no counterpart in the paper) --------------------------------
  * A message-passing network predicts the potential increment of a streamer step:
  *   f_i = [ (e/eps0) dq_i mu_i^(2/3) / (V s0),  phi_prev_i / (V s1) ]
- *   h = relu(W_enc f + b_enc) (width 64); 3 layers: m_i = sum_j w_ij (h_j - h_i) over the
- *   interior faces (w = c1 / max c1 of set bcset), h = h + relu(W_l [h ; m] + b_l);
- *   out = N(f) = w_dec . h + b_dec; increment = V s2 (N(f) - N(f with f0 = 0)), i.e. the
+ *   h0 = relu(W_enc f + b_enc) (width 64);
+ *   layer(l, h; graph): m_i = sum_j w_ij (h_j - h_i), h + relu(W_l [h ; m] + b_l);
+ *   h1 = layer(0, h0; interior faces, w = c1 / max c1 of set bcset);
+ *   local architecture (multilevel = 0): h2 = layer(1, h1; interior faces);
+ *   multilevel architecture (multilevel = 1): the middle layer runs on the aggregate
+ *   hierarchy of fvgb_mpnn_hierarchy, which reaches the whole part: at every
+ *   level, the mean over each aggregate of the level below (h1 for the first), then two
+ *   applications of layer(1, c; face-adjacent aggregates, w = 1/6); then back up, every
+ *   level adds its aggregate's value, down to h2 = h1 + c_1 of the cell's aggregate;
+ *   h3 = layer(2, h2; interior faces);
+ *   out = N(f) = w_dec . h3 + b_dec; increment = V s2 (N(f) - N(f with f0 = 0)), i.e. the
  *   response to the charge change (what the network gives for an unchanged charge is
  *   removed, so no change predicts no increment).
  * Layer products run on the tensor cores (BF16 weights and activations, FP32
  * accumulation); master weights, gradients and Adam state are FP32.
  * Parameters: one FP32 vector of fvgb_mpnn_param_count() entries, blocks in order
  * W_enc [64][2], b_enc [64], then per layer W_l [64][128] (inputs [h ; m]), b_l [64],
- * then w_dec [64], b_dec [1]. A network belongs to one mesh; move weights between
- * meshes with get/set. */
-fvgb_status fvgb_mpnn_create(fvgb_mesh m, int32_t bcset, fvgb_mpnn* out);
+ * then w_dec [64], b_dec [1]. A network belongs to one 3D mesh (FVGB_EINVAL otherwise);
+ * move weights between meshes with get/set. */
+
+/* The aggregate hierarchy of the network (host arrays; needs no GPU). cen: [3][n_cell]
+ * cell centres; part_begin: n_part + 1 cell offsets (0 ... n_cell, parts non-empty).
+ * Per part, with [lo, hi] the bounding box of its centres and r_1 = max(1, round((n /
+ * 6)^(1/3))) boxes per axis, a cell's level-1 box index per axis is min(r_1 - 1,
+ * floor((x - lo) / (hi - lo) r_1)) (0 when hi = lo); level k + 1 halves the indices (r_{k+1}
+ * = ceil(r_k / 2)); levels continue while some part has r > 2 and stop once every part is
+ * one box (16 at most). Aggregates are the non-empty boxes, numbered part by part in
+ * increasing (x, y, z) order. Outputs: *n_levels = L; level_n[0..L) (room for 16) nodes per
+ * level; if parent is not NULL, the aggregate (level-local) of every node of the level
+ * below, levels one after the other (n_cell + level_n[0] + ... + level_n[L-2] entries); if
+ * nbr is not NULL, per level and aggregate 8 slots of face-adjacent aggregates (level-
+ * local), the unused ones holding the aggregate itself. Errors: FVGB_EINVAL for bad
+ * arguments or a non-finite centre. */
+fvgb_status fvgb_mpnn_hierarchy(int64_t n_cell, const double* cen, int32_t n_part, const int64_t* part_begin,
+                                int32_t* n_levels, int64_t* level_n, int32_t* parent, int32_t* nbr);
+fvgb_status fvgb_mpnn_create(fvgb_mesh m, int32_t bcset, int32_t multilevel, fvgb_mpnn* out);
 fvgb_status fvgb_mpnn_free(fvgb_mpnn net);
 int64_t fvgb_mpnn_param_count(void);
 /* Set the FP32 parameters (host array) and reset the optimiser state. */

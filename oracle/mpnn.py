@@ -9,9 +9,11 @@ Architecture (per cell i; fine messages over interior faces, weight w_ij = c1_f 
     h     = relu(W_enc f + b_enc)                                 (64)
     layer(l, h; graph): m_i = sum_j w_ij (h_j - h_i); z = W_l [h ; m] + b_l; h + relu(z)
     h     = layer(0, h; faces)
-    the middle layer runs on a hierarchy of cubic aggregates (``hierarchy``), which gives
-    the network the reach of the whole domain (the potential's increment is the global
-    response to a local charge change):
+    middle layer, one of two architectures:
+    local: h = layer(1, h; faces) (reach: three face hops in all);
+    multilevel: the middle layer runs on a hierarchy of cubic aggregates (``hierarchy``),
+    which gives the network the reach of the whole domain (the potential's increment is
+    the global response to a local charge change):
         c_1 = mean over each level-1 aggregate of h;  c_k = mean over the level-k aggregate
         of c_{k-1};  at every level, before moving down, HOPS times c_k = layer(1, c_k;
         aggregate graph k), whose weights are 1/6 between face-adjacent aggregates
@@ -182,9 +184,9 @@ def features(geo, dq, phi_prev, V, s0, s1):
     return np.stack([f0, f1], axis=1)
 
 
-def network_graph(geo, part_begin=None):
-    """(fine face graph, aggregate levels) of the network on this mesh."""
-    return message_graph(geo), hierarchy(geo.cen, part_begin)
+def network_graph(geo, part_begin=None, multilevel=True):
+    """(fine face graph, aggregate levels or None for the local architecture)."""
+    return message_graph(geo), hierarchy(geo.cen, part_begin) if multilevel else None
 
 
 def sum_children(level, d):
@@ -218,6 +220,11 @@ def forward(net, theta, f):
     h = np.maximum(z0, 0.0)
     cache = {"f": f, "z0": z0}
     h1, cache["l0"] = _layer(p, 0, h, lambda v: messages(fine, v))
+    if levels is None:
+        h2, cache["l1"] = _layer(p, 1, h1, lambda v: messages(fine, v))
+        h3, cache["l2"] = _layer(p, 2, h2, lambda v: messages(fine, v))
+        cache["h3"] = h3
+        return h3 @ p["w_dec"] + p["b_dec"][0], cache
     # down the aggregate levels: mean, then HOPS middle layers per level
     x, down = h1, []
     for lev in levels:
@@ -263,7 +270,9 @@ def _backward_one(net, p, c, dout):
     d = np.outer(dout, p["w_dec"])
     d = _layer_back(p, 2, g, c["l2"], d, fmsg)                  # d h2
     dh1 = d.copy()
-    if levels:
+    if levels is None:
+        dh1 = _layer_back(p, 1, g, c["l1"], d, fmsg)
+    elif levels:
         L = len(levels)
         dC = [None] * L
         du = sum_children(levels[0], d)
@@ -305,15 +314,16 @@ def backward(net, theta, f, t):
 
 
 def init_params(seed):
-    """Kaiming-uniform-like initialisation from numpy's PCG64 stream."""
+    """Uniform weights in +-1 / sqrt(fan_in) (the decoder vector too), zero biases, from
+    numpy's PCG64 stream."""
     rng = np.random.default_rng(seed)
     p = {}
     for name, shape in layout():
         if name.startswith("W"):
-            bound = np.sqrt(6.0 / shape[1])
+            bound = 1.0 / np.sqrt(shape[1])
             p[name] = rng.uniform(-bound, bound, size=shape)
         elif name == "w_dec":
-            p[name] = rng.uniform(-np.sqrt(3.0 / HIDDEN), np.sqrt(3.0 / HIDDEN), size=shape)
+            p[name] = rng.uniform(-1.0 / np.sqrt(HIDDEN), 1.0 / np.sqrt(HIDDEN), size=shape)
         else:
             p[name] = np.zeros(shape)
     return pack(p)

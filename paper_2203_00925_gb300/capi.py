@@ -36,7 +36,8 @@ EXPORTED = [
     "fvgb_fv_residual_noalloc",
     "fvgb_fv_step", "fvgb_poisson_apply", "fvgb_poisson_rhs", "fvgb_poisson_solve",
     "fvgb_streamer_step", "fvgb_streamer_reset", "fvgb_streamer_pair", "fvgb_set_graph_mode",
-    "fvgb_mpnn_create", "fvgb_mpnn_free", "fvgb_mpnn_param_count", "fvgb_mpnn_set_params",
+    "fvgb_mpnn_create", "fvgb_mpnn_hierarchy", "fvgb_mpnn_free", "fvgb_mpnn_param_count",
+    "fvgb_mpnn_set_params",
     "fvgb_mpnn_get_params", "fvgb_mpnn_set_scales", "fvgb_mpnn_predict", "fvgb_mpnn_loss_grad",
     "fvgb_mpnn_train_step", "fvgb_autotune", "fvgb_set_launch_shape",
     "fvgb_integral", "fvgb_stats_enable", "fvgb_stats_get", "fvgb_sync", "fvgb_test_barrier",
@@ -132,8 +133,9 @@ _sig = {
     "fvgb_sync": (C.c_int, [_vp, _vp]),
     "fvgb_test_barrier": (C.c_int, [_vp, _i32, _d]),
     "fvgb_streamer_pair": (C.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
-    "fvgb_mpnn_create": (C.c_int, [_vp, _i32, C.POINTER(_vp)]),
+    "fvgb_mpnn_create": (C.c_int, [_vp, _i32, _i32, C.POINTER(_vp)]),
     "fvgb_mpnn_free": (C.c_int, [_vp]),
+    "fvgb_mpnn_hierarchy": (C.c_int, [_i64, _vp, _i32, _vp, C.POINTER(_i32), _vp, _vp, _vp]),
     "fvgb_mpnn_param_count": (C.c_int64, []),
     "fvgb_mpnn_set_params": (C.c_int, [_vp, _vp]),
     "fvgb_mpnn_get_params": (C.c_int, [_vp, _vp]),
@@ -412,10 +414,37 @@ def fvgb_streamer_pair(m, which, phi, dq, phi_prev, dphi, stream=None):
                                          stream_handle(stream)), "fvgb_streamer_pair")
 
 
-def fvgb_mpnn_create(m, bcset):
+def fvgb_mpnn_create(m, bcset, multilevel=True):
     out = _vp()
-    _check(lib.fvgb_mpnn_create(m, bcset, C.byref(out)), "fvgb_mpnn_create")
+    _check(lib.fvgb_mpnn_create(m, bcset, int(bool(multilevel)), C.byref(out)), "fvgb_mpnn_create")
     return out.value
+
+
+def fvgb_mpnn_hierarchy(cen, part_begin=None):
+    """Aggregate hierarchy of the network from cell centres cen [n][3] (host): a list of
+    (level size, parent of every node below [level-local], neighbours [size][8])."""
+    import numpy as np
+    cen = np.asarray(cen, dtype=np.float64)
+    n = cen.shape[0]
+    soa = np.ascontiguousarray(cen.T)
+    pb = np.ascontiguousarray([0, n] if part_begin is None else part_begin, dtype=np.int64)
+    nl = _i32()
+    sizes = np.zeros(16, dtype=np.int64)
+    _check(lib.fvgb_mpnn_hierarchy(n, soa.ctypes.data, len(pb) - 1, pb.ctypes.data, C.byref(nl),
+                                   sizes.ctypes.data, None, None), "fvgb_mpnn_hierarchy")
+    L = nl.value
+    below = np.concatenate([[n], sizes[:L - 1]]).astype(np.int64)
+    parent = np.zeros(int(below.sum()), dtype=np.int32)
+    nbr = np.zeros(int(sizes[:L].sum()) * 8, dtype=np.int32)
+    _check(lib.fvgb_mpnn_hierarchy(n, soa.ctypes.data, len(pb) - 1, pb.ctypes.data, C.byref(nl),
+                                   sizes.ctypes.data, parent.ctypes.data, nbr.ctypes.data), "fvgb_mpnn_hierarchy")
+    out, po, no = [], 0, 0
+    for k in range(L):
+        nk = int(sizes[k])
+        out.append((nk, parent[po:po + below[k]], nbr[8 * no:8 * (no + nk)].reshape(nk, 8)))
+        po += int(below[k])
+        no += nk
+    return out
 
 
 def fvgb_mpnn_free(net):

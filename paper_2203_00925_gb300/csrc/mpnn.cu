@@ -3,22 +3,30 @@
 //
 //   f_i   = [ (e/eps0) dq_i mu_i^(2/3) / (V s0),  phi_prev_i / (V s1) ]
 //   h0    = relu(W_enc f + b_enc)                                  (hidden 64)
-//   3 x:  m_i = sum_j w_ij (h_j - h_i)   (interior faces, w = c1 / max c1)
-//         z   = W_l [h ; m] + b_l,   h = h + relu(z)
-//   out   = w_dec . h + b_dec,  predicted potential increment V s2 out
+//   layer(l, h; graph): m_i = sum_j w_ij (h_j - h_i), z = W_l [h ; m] + b_l, h + relu(z)
+//   h1    = layer(0, h0; interior faces, w = c1 / max c1)
+//   middle layer on a hierarchy of cubic aggregates of the cells (built on the host when
+//   the network is created): at every level the mean over each aggregate of the level
+//   below, then kHops times layer(1, c; face-adjacent aggregates, w = 1/6); back up, every
+//   level adds its aggregate's value, down to h2 = h1 + c_1 of the cell's aggregate
+//   h3    = layer(2, h2; interior faces)
+//   out   = w_dec . h3 + b_dec,  predicted potential increment V s2 out
 //
-// The layer products [h ; m] W_l^T (128 cells x 128 inputs x 64 outputs per tile) and
-// their backward dz W_l (128 cells x 64 x 128) run on the fifth-generation tensor cores:
-// the block gathers a tile of BF16 operands into shared memory (canonical K-major layout
-// without swizzle), one thread issues tcgen05.mma (kind::f16, FP32 accumulators in tensor
-// memory), completion is signalled through an mbarrier, and every thread reads its
-// cell's row of the accumulator with tcgen05.ld for the fused epilogue (bias, ReLU,
-// residual). Hidden states, messages and pre-activations are kept in FP32. Weight gradients are FP32 outer-product sums per block, reduced over blocks in
-// FP64 in a fixed order (deterministic). Adam updates FP32 master weights and refreshes
-// their BF16 copies.
+// The layer products [h ; m] W_l^T (128 rows x 128 inputs x 64 outputs per tile) and
+// their backward dz W_l (128 rows x 64 x 128) run on the fifth-generation tensor cores:
+// the block gathers a tile of BF16 operands into shared memory (128-byte swizzled K-major
+// layout), one thread issues tcgen05.mma (kind::f16, FP32 accumulators in tensor memory),
+// completion is signalled through an mbarrier, and the warps read the accumulator with
+// tcgen05.ld for the fused epilogue (bias, ReLU, residual). The same kernels run the fine
+// layers (rows = cells, four face neighbours with weights) and the aggregate layers (rows =
+// aggregates, up to six neighbours of weight 1/6). Hidden states, messages and
+// pre-activations are kept in FP32. Weight gradients are per-block sums accumulated in
+// tensor memory, reduced over blocks in FP64 in a fixed order (deterministic). Adam updates
+// FP32 master weights and refreshes their BF16 copies.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -37,6 +45,8 @@ constexpr int kNParams = kOffBdec + 1;                          // 25025
 constexpr int kTile = 128;             // cells per tensor-core tile (the MMA's M)
 constexpr int kTileThreads = 256;      // threads of the layer kernels: two per cell row
 constexpr int kGradBlocks = 304;       // blocks of the gradient reductions (and of the backward)
+constexpr int kHops = 2;               // applications of the middle layer per aggregate level
+constexpr int kMaxLevels = 16;
 // dynamic shared memory of the layer kernels: forward A = [h ; m] (128 x 128 BF16, 32 KB)
 // and W (64 x 128, 16 KB): up to four blocks an SM, 4 x 64 tensor-memory columns.
 // Backward: B1 = W^T (128 x 64, 16 KB), A1 = dz (128 cells x 64, 16 KB), A2 = [h ; m]^T
@@ -59,16 +69,36 @@ struct fvgb_mpnn_s {
   float* grad = nullptr;               // [params]
   __nv_bfloat16* wbf = nullptr;        // [3][64][128]
   float* wn = nullptr;                 // [N][4] message weights
+  // aggregate hierarchy (multilevel architecture; n_lev = 0: the middle layer runs on the
+  // faces): level k (0-based) has lev_n[k] nodes, rows [lev_off[k], + lev_n[k]) of the
+  // coarse arrays; the nodes below it are the cells (k = 0) or level k - 1's
+  int n_lev = 0;
+  int64_t lev_n[fvgb::kMaxLevels] = {};
+  int64_t lev_off[fvgb::kMaxLevels + 1] = {};
+  int64_t below_off[fvgb::kMaxLevels + 1] = {};   // offsets into parent / child_idx
+  int64_t ptr_off[fvgb::kMaxLevels] = {};         // offsets into child_ptr
+  int32_t* parent = nullptr;           // per level: aggregate of each node below (level-local)
+  int32_t* child_ptr = nullptr;        // per level: [lev_n + 1] CSR of the nodes below
+  int32_t* child_idx = nullptr;        // per level: nodes below, by aggregate, ascending
+  float* inv_count = nullptr;          // [coarse rows] 1 / nodes in the aggregate
+  int32_t* cnbr = nullptr;             // [coarse rows][8] face-adjacent aggregates, padded with self
+  int64_t n_coarse = 0;
   // activations of the two evaluations N(f) and N(f0 = 0) (set 0 and set 1)
   float* F[2] = {};                    // [N][2]
   float* Z0[2] = {};                   // [N][64]
-  float* H[2][4] = {};                 // [N][64], layers 0..3
-  float* M[2][3] = {};
+  float* H[2][4] = {};                 // [N][64]: h0, h1, h2, h3
+  float* M[2][3] = {};                 // fine layers (0 and 2; 1 too when local)
   float* Z[2][3] = {};
+  float* Hc[2][fvgb::kHops + 1] = {};  // [coarse rows][64]: hop inputs, last = level output
+  float* Mc[2][fvgb::kHops] = {};
+  float* Zc[2][fvgb::kHops] = {};
   float* dout = nullptr;               // [N]
   float* dH = nullptr;                 // [N][64]
   float* dHb = nullptr;                // [N][64]
   float* G = nullptr;                  // [N][64] message part of dz W
+  float* dC = nullptr;                 // [coarse rows][64] gradients of the level outputs
+  float* cP = nullptr;                 // [lev_n[0]][64] gradient ping-pong of the hops
+  float* cQ = nullptr;
   float* part = nullptr;               // [blocks][params] gradient partials
   double* dpart = nullptr;             // [kGradBlocks] loss partials
   double* dloss = nullptr;             // [1]
@@ -85,21 +115,6 @@ namespace {
 
 // ---- tcgen05 helpers -------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Byte offset of element (r, k) of a K-major tile with K elements a row, without swizzle:
-// 8 x 8 core matrices of 16-byte rows; core matrices adjacent in K are 128 bytes apart,
-// groups of 8 rows are K / 8 x 128 bytes apart.
-__device__ __forceinline__ uint32_t kmaj_off(int r, int k, int K) {
-  return (uint32_t)((r >> 3) * (K >> 3) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
-}
-
-// Shared-memory matrix descriptor of tcgen05.mma for such a tile: start address, leading
-// byte offset (K-adjacent core matrices), stride byte offset (8-row groups), version 1,
-// no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
-         (1ull << 46);
-}
 
 // 128-byte swizzled K-major layout: K in slabs of 64 elements, a slab of R rows taking
 // R x 128 bytes (1024-byte aligned); the 16-byte chunk c of row r sits at chunk c ^ (r % 8)
@@ -193,14 +208,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__device__ __forceinline__ void load8(const float* p, float (&v)[8]) {
-  const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
-  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-}
-__device__ __forceinline__ void store8(float* p, const float (&v)[8]) {
-  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-  *reinterpret_cast<float4*>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
-}
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 v;
   v.x = __float2bfloat16_rn(a);
@@ -275,8 +282,11 @@ __global__ void k_encode(int64_t N, const float* __restrict__ F, const float* __
 }
 
 // ---- one message-passing layer, forward (tensor cores) ---------------------------------------
-// Persistent over tiles of 128 cells. The block's eight warps gather the tile's rows
-// A_c = [h ; m] (m = sum_j w_j (h_j - h), four neighbours) into the BF16 operand tile, 16
+// Persistent over tiles of 128 rows. The block's eight warps gather the tile's rows
+// A_c = [h ; m] into the BF16 operand tile (fine layers: rows are cells, m = sum_j w_j (h_j - h)
+// over four face neighbours, nbr [N] int4 and wn [N] float4; aggregate layers: rows are
+// aggregates, m = (1/6) sum_j (h_j - h) over six slots nbr [2 N] int4 padded with the row
+// itself), 16
 // lanes a row (a float4 of features each: whole 256-byte rows per load), two rows a step,
 // warp w taking rows [16 w, 16 w + 16); the tile is in the 128-byte swizzled K-major layout
 // (h in the first slab, m in the second), so a row's stores are bank-conflict-free. Thread 0
@@ -285,6 +295,7 @@ __global__ void k_encode(int64_t N, const float* __restrict__ F, const float* __
 // 32 (w / 4) .. + 31, adds the bias and stages Z in shared memory (over the consumed A tile);
 // the warps then write Z (training) and H_out = H + relu(Z) row by row, coalesced. A wait
 // that runs out sets bit 2 of *err and the block leaves.
+template <bool kCoarse>
 __global__ void __launch_bounds__(kTileThreads)
 k_layer_fwd(int64_t N, const float* __restrict__ H, const int4* __restrict__ nbr, const float4* __restrict__ wn,
             const __nv_bfloat16* __restrict__ Wg, const float* __restrict__ bias, float* __restrict__ Mout,
@@ -328,15 +339,27 @@ k_layer_fwd(int64_t N, const float* __restrict__ H, const int4* __restrict__ nbr
       const int64_t cr = tile * kTile + r;
       float4 h = make_float4(0.f, 0.f, 0.f, 0.f), m = h;
       if (cr < N) {
-        const int4 nb = nbr[cr];
-        const float4 w4 = wn[cr];
         h = ld4(H + cr * kHid + 4 * q);
-        const float4 g0 = ld4(H + (int64_t)nb.x * kHid + 4 * q), g1 = ld4(H + (int64_t)nb.y * kHid + 4 * q),
-                     g2 = ld4(H + (int64_t)nb.z * kHid + 4 * q), g3 = ld4(H + (int64_t)nb.w * kHid + 4 * q);
-        m.x = w4.x * (g0.x - h.x) + w4.y * (g1.x - h.x) + w4.z * (g2.x - h.x) + w4.w * (g3.x - h.x);
-        m.y = w4.x * (g0.y - h.y) + w4.y * (g1.y - h.y) + w4.z * (g2.y - h.y) + w4.w * (g3.y - h.y);
-        m.z = w4.x * (g0.z - h.z) + w4.y * (g1.z - h.z) + w4.z * (g2.z - h.z) + w4.w * (g3.z - h.z);
-        m.w = w4.x * (g0.w - h.w) + w4.y * (g1.w - h.w) + w4.z * (g2.w - h.w) + w4.w * (g3.w - h.w);
+        if constexpr (kCoarse) {
+          const int4 na = nbr[2 * cr], nb = nbr[2 * cr + 1];
+          const int ns[6] = {na.x, na.y, na.z, na.w, nb.x, nb.y};
+#pragma unroll
+          for (int j = 0; j < 6; ++j) {
+            const float4 g = ld4(H + (int64_t)ns[j] * kHid + 4 * q);
+            m.x += g.x - h.x; m.y += g.y - h.y; m.z += g.z - h.z; m.w += g.w - h.w;
+          }
+          const float sixth = 1.0f / 6.0f;
+          m.x *= sixth; m.y *= sixth; m.z *= sixth; m.w *= sixth;
+        } else {
+          const int4 nb = nbr[cr];
+          const float4 w4 = wn[cr];
+          const float4 g0 = ld4(H + (int64_t)nb.x * kHid + 4 * q), g1 = ld4(H + (int64_t)nb.y * kHid + 4 * q),
+                       g2 = ld4(H + (int64_t)nb.z * kHid + 4 * q), g3 = ld4(H + (int64_t)nb.w * kHid + 4 * q);
+          m.x = w4.x * (g0.x - h.x) + w4.y * (g1.x - h.x) + w4.z * (g2.x - h.x) + w4.w * (g3.x - h.x);
+          m.y = w4.x * (g0.y - h.y) + w4.y * (g1.y - h.y) + w4.z * (g2.y - h.y) + w4.w * (g3.y - h.y);
+          m.z = w4.x * (g0.z - h.z) + w4.y * (g1.z - h.z) + w4.z * (g2.z - h.z) + w4.w * (g3.z - h.z);
+          m.w = w4.x * (g0.w - h.w) + w4.y * (g1.w - h.w) + w4.z * (g2.w - h.w) + w4.w * (g3.w - h.w);
+        }
         if (Mout) st4(Mout + cr * kHid + 4 * q, m);
       }
       st_bf16x4(As + sw_off(r, 4 * q, kTile), h);
@@ -488,7 +511,8 @@ k_decode_grad(int64_t N, const float* __restrict__ Ha, const float* __restrict__
 }
 
 // ---- one layer, backward with its weight gradients (tensor cores) ------------------------------
-// Persistent: kGradBlocks blocks take tiles of 128 cells in turn. Per tile, with
+// Persistent: up to kGradBlocks blocks take tiles of 128 rows in turn (the same kernel for
+// the fine and the aggregate layers: it reads only its tile's rows). Per tile, with
 // dz = dH_next * (z > 0):
 //  - data product [g_h ; g_m] = dz W_l (4 tcgen05.mma of K = 16 into tensor-memory columns
 //    [0, 128)): dH = dH_next + g_h, G = g_m (its message is added by k_msg_add), written
@@ -497,8 +521,9 @@ k_decode_grad(int64_t N, const float* __restrict__ Ha, const float* __restrict__
 //    columns [128, 192), accumulated over all tiles of the block): both operands have the
 //    cells as K, a lane per feature packing eight cells into one 16-byte row;
 //  - bias gradient: sums of dz kept per lane in registers over the block's tiles.
-// Operands are in the 128-byte swizzled K-major layout. At the end the block writes its
-// partials to part[blockIdx.x] (weights [out][in], bias), or zeros when it had no tile; the
+// Operands are in the 128-byte swizzled K-major layout. At the end the block adds its
+// partials to part[blockIdx.x] (weights [out][in], bias; zeroed before the backward, so the
+// middle layer's applications at every level and hop accumulate there in launch order); the
 // partials are summed over blocks in a fixed order later.
 __global__ void __launch_bounds__(kTileThreads)
 k_layer_bwd(int64_t N, const float* __restrict__ dHn, const float* __restrict__ Z,
@@ -641,8 +666,10 @@ k_layer_bwd(int64_t N, const float* __restrict__ dHn, const float* __restrict__ 
     const int o0 = 32 * (warp >> 2);
     float v[32];
     tmem_ld32(tmem + lanebase + kIn + o0, v);
+    if (ntile_done > 0) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) p[(o0 + j) * kIn + in] = ntile_done > 0 ? v[j] : 0.0f;
+      for (int j = 0; j < 32; ++j) p[(o0 + j) * kIn + in] += v[j];
+    }
   }
   // bias: lanes q and q + 16 hold the same features for different rows
   bacc.x += __shfl_xor_sync(0xffffffffu, bacc.x, 16);
@@ -660,7 +687,7 @@ k_layer_bwd(int64_t N, const float* __restrict__ dHn, const float* __restrict__ 
     float b = 0.0f;
 #pragma unroll
     for (int w = 0; w < 8; ++w) b += red[w][t];
-    p[kHid * kIn + t] = b;
+    p[kHid * kIn + t] += b;
   }
   tc_fence_before();
   __syncthreads();
@@ -668,7 +695,10 @@ k_layer_bwd(int64_t N, const float* __restrict__ dHn, const float* __restrict__ 
   if (warp == 0) tmem_dealloc(tmem, 256);
 }
 
-// dH_i += sum_j w_ij (G_j - G_i): the adjoint of the (symmetric) message operator
+// dH_i += sum_j w_ij (G_j - G_i): the adjoint of the (symmetric) message operator; fine
+// rows (four weighted face neighbours) or aggregate rows (six slots of weight 1/6, padded
+// with the row itself)
+template <bool kCoarse>
 __global__ void k_msg_add(int64_t N, const float* __restrict__ Gm, const int4* __restrict__ nbr,
                           const float4* __restrict__ wn, float* __restrict__ dH) {
   const int lane = threadIdx.x & 31;
@@ -676,20 +706,74 @@ __global__ void k_msg_add(int64_t N, const float* __restrict__ Gm, const int4* _
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t c = warp; c < N; c += nwarps) {
     const float2 gi = *reinterpret_cast<const float2*>(Gm + c * kHid + 2 * lane);
-    const int4 nb = nbr[c];
-    const float4 w = wn[c];
-    const int ns[4] = {nb.x, nb.y, nb.z, nb.w};
-    const float ws[4] = {w.x, w.y, w.z, w.w};
     float mx = 0.0f, my = 0.0f;
+    if constexpr (kCoarse) {
+      const int4 na = nbr[2 * c], nb = nbr[2 * c + 1];
+      const int ns[6] = {na.x, na.y, na.z, na.w, nb.x, nb.y};
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const float2 gn = *reinterpret_cast<const float2*>(Gm + (int64_t)ns[s] * kHid + 2 * lane);
-      mx += ws[s] * (gn.x - gi.x);
-      my += ws[s] * (gn.y - gi.y);
+      for (int s = 0; s < 6; ++s) {
+        const float2 gn = *reinterpret_cast<const float2*>(Gm + (int64_t)ns[s] * kHid + 2 * lane);
+        mx += gn.x - gi.x;
+        my += gn.y - gi.y;
+      }
+      mx *= 1.0f / 6.0f;
+      my *= 1.0f / 6.0f;
+    } else {
+      const int4 nb = nbr[c];
+      const float4 w = wn[c];
+      const int ns[4] = {nb.x, nb.y, nb.z, nb.w};
+      const float ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const float2 gn = *reinterpret_cast<const float2*>(Gm + (int64_t)ns[s] * kHid + 2 * lane);
+        mx += ws[s] * (gn.x - gi.x);
+        my += ws[s] * (gn.y - gi.y);
+      }
     }
     float2* d = reinterpret_cast<float2*>(dH + c * kHid + 2 * lane);
     const float2 dv = *d;
     *d = make_float2(dv.x + mx, dv.y + my);
+  }
+}
+
+// ---- aggregate hierarchy: mean over aggregates, copy back ----------------------------------
+// out[a] = s_a sum over the nodes below of aggregate a (child_ptr / child_idx, ascending) of
+// in[child], s_a = inv_count[a] (the mean) or 1 (inv_count null: the adjoint of the copy
+// back); 16 lanes a row, a float4 of features each
+__global__ void k_child_sum(int64_t n, const int32_t* __restrict__ child_ptr, const int32_t* __restrict__ child_idx,
+                            const float* __restrict__ in, const float* __restrict__ inv_count,
+                            float* __restrict__ out) {
+  const int q = threadIdx.x & 15;
+  const int64_t row0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 4;
+  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 4;
+  for (int64_t a = row0; a < n; a += stride) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int32_t e = child_ptr[a + 1];
+    for (int32_t k = child_ptr[a]; k < e; ++k) {
+      const float4 v = ld4(in + (int64_t)child_idx[k] * kHid + 4 * q);
+      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    }
+    if (inv_count) {
+      const float s = inv_count[a];
+      acc.x *= s; acc.y *= s; acc.z *= s; acc.w *= s;
+    }
+    st4(out + a * kHid + 4 * q, acc);
+  }
+}
+
+// out[i] = a[i] + s_p b[p], p = parent[i], s_p = inv_count[p] or 1 (inv_count null): the copy
+// back of the way up, and the adjoint of the mean; out may be a (same row, same thread)
+__global__ void k_add_parent(int64_t n, const float* a, const float* __restrict__ b,
+                             const int32_t* __restrict__ parent, const float* __restrict__ inv_count,
+                             float* out) {
+  const int q = threadIdx.x & 15;
+  const int64_t row0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 4;
+  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 4;
+  for (int64_t i = row0; i < n; i += stride) {
+    const int32_t p = parent[i];
+    const float s = inv_count ? inv_count[p] : 1.0f;
+    const float4 x = ld4(a + i * kHid + 4 * q), y = ld4(b + (int64_t)p * kHid + 4 * q);
+    st4(out + i * kHid + 4 * q, make_float4(x.x + s * y.x, x.y + s * y.y, x.z + s * y.z, x.w + s * y.w));
   }
 }
 
@@ -789,65 +873,272 @@ unsigned grid_n(int64_t n, int t = 256) {
 
 cudaError_t alloc_train(MpnnNet* n) {
   if (n->train_buffers) return cudaSuccess;
-  const size_t NH = (size_t)n->N * kHid;
+  const size_t NH = (size_t)n->N * kHid, CH = (size_t)n->n_coarse * kHid;
   cudaError_t e;
   for (int set = 0; set < 2; ++set) {
     if (set == 1 && (e = nalloc(n, &n->F[1], (size_t)n->N * 2))) return e;
     if ((e = nalloc(n, &n->Z0[set], NH))) return e;
-    for (int l = 0; l < kLayers; ++l) {
+    for (int l = 0; l < kLayers; l += n->n_lev > 0 ? 2 : 1) {   // the fine layers
       if ((e = nalloc(n, &n->M[set][l], NH))) return e;
       if ((e = nalloc(n, &n->Z[set][l], NH))) return e;
     }
     for (int l = set == 0 ? 2 : 0; l <= kLayers; ++l)
       if ((e = nalloc(n, &n->H[set][l], NH))) return e;
+    for (int j = 0; j < kHops && n->n_lev > 0; ++j) {
+      if ((e = nalloc(n, &n->Mc[set][j], CH))) return e;
+      if ((e = nalloc(n, &n->Zc[set][j], CH))) return e;
+    }
+    if (set == 1 && n->n_lev > 0)
+      for (int j = 0; j <= kHops; ++j)
+        if ((e = nalloc(n, &n->Hc[1][j], CH))) return e;
   }
   if ((e = nalloc(n, &n->dH, NH))) return e;
   if ((e = nalloc(n, &n->dHb, NH))) return e;
   if ((e = nalloc(n, &n->G, NH))) return e;
+  if (n->n_lev > 0) {
+    if ((e = nalloc(n, &n->dC, CH))) return e;
+    if ((e = nalloc(n, &n->cP, (size_t)n->lev_n[0] * kHid))) return e;
+    if ((e = nalloc(n, &n->cQ, (size_t)n->lev_n[0] * kHid))) return e;
+  }
   if ((e = nalloc(n, &n->dout, n->N))) return e;
   if ((e = nalloc(n, &n->part, (size_t)2 * kGradBlocks * kNParams))) return e;
   n->train_buffers = true;
   return cudaSuccess;
 }
 
-// grid of the forward layer kernel: persistent over 128-cell tiles, as many blocks as fit on
-// the SMs (48 KB shared memory and 64 tensor-memory columns a block, up to four an SM); the
-// backward runs kGradBlocks blocks (80 KB and 256 columns a block, two an SM)
-unsigned layer_grid(MpnnNet* n, int per_sm) {
-  return (unsigned)std::min<int64_t>((n->N + kTile - 1) / kTile, (int64_t)n->m->num_sms * per_sm);
+// ---- aggregate hierarchy (host, at creation) ---------------------------------------------
+// Per part, with [lo, hi] the bounding box of the part's cell centres and r_1 =
+// max(1, round((n / 6)^(1/3))) boxes per axis, a cell's level-1 box index per axis is
+// min(r_1 - 1, floor((x - lo) / (hi - lo) r_1)) (0 when hi = lo). Level k + 1 halves the box
+// indices (r_{k+1} = ceil(r_k / 2)); levels continue while some part has r_k > 2, and stop
+// early once every part is one box. Aggregates are the non-empty boxes, numbered part by
+// part in increasing (x, y, z) index order; neighbours are the non-empty boxes sharing a
+// face. The same FP64 operations as the oracle's rule, so both build the same hierarchy.
+struct HostHierarchy {
+  std::vector<int64_t> n;                      // nodes per level
+  std::vector<std::vector<int32_t>> parent;    // per level: aggregate of each node below
+  std::vector<std::vector<int32_t>> nbr;       // per level: [n][8] neighbours, padded with self
+};
+
+HostHierarchy build_hierarchy(const double* cen, int64_t N, const std::vector<int64_t>& pb) {
+  const int P = (int)pb.size() - 1;
+  HostHierarchy out;
+  std::vector<int32_t> kc(3 * (size_t)N);      // box coordinates of the nodes below
+  std::vector<int64_t> rad(P), below_begin(pb.begin(), pb.end());
+  for (int p = 0; p < P; ++p) {
+    const int64_t b = pb[p], e = pb[p + 1], np = e - b;
+    const int64_t r = std::max<int64_t>(1, (int64_t)std::nearbyint(std::pow((double)np / 6.0, 1.0 / 3.0)));
+    rad[p] = r;
+    for (int a = 0; a < 3; ++a) {
+      const double* x = cen + (size_t)a * N;
+      double lo = x[b], hi = x[b];
+      for (int64_t i = b; i < e; ++i) { lo = std::min(lo, x[i]); hi = std::max(hi, x[i]); }
+      for (int64_t i = b; i < e; ++i) {
+        int64_t k = 0;
+        if (hi > lo) k = std::min<int64_t>(r - 1, (int64_t)std::floor((x[i] - lo) / (hi - lo) * (double)r));
+        kc[3 * i + a] = (int32_t)k;
+      }
+    }
+  }
+  int64_t n_below = N;
+  for (bool first = true;; first = false) {
+    if (!first) {
+      bool more = false;
+      for (int p = 0; p < P; ++p) more |= rad[p] > 2;
+      if (!more) break;
+      for (auto& k : kc) k >>= 1;
+      for (auto& r : rad) r = (r + 1) / 2;
+    }
+    std::vector<int32_t> parent(n_below), nbr;
+    std::vector<int32_t> next_kc;
+    std::vector<int64_t> next_begin(P + 1, 0);
+    int64_t offset = 0;
+    for (int p = 0; p < P; ++p) {
+      const int64_t r = rad[p];
+      std::vector<int64_t> rank((size_t)(r * r * r), -1);
+      for (int64_t i = below_begin[p]; i < below_begin[p + 1]; ++i)
+        rank[(size_t)((kc[3 * i] * r + kc[3 * i + 1]) * r + kc[3 * i + 2])] = 0;
+      int64_t nb = 0;                              // present keys get ranks in key order
+      for (auto& v : rank)
+        if (v == 0) v = nb++;
+      for (int64_t i = below_begin[p]; i < below_begin[p + 1]; ++i)
+        parent[i] = (int32_t)(offset + rank[(size_t)((kc[3 * i] * r + kc[3 * i + 1]) * r + kc[3 * i + 2])]);
+      for (int64_t key = 0; key < r * r * r; ++key) {
+        if (rank[key] < 0) continue;
+        const int64_t x = key / (r * r), y = (key / r) % r, z = key % r;
+        const int64_t self = offset + rank[key];
+        int32_t slots[8];
+        int ns = 0;
+        const int64_t d[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+        for (int q = 0; q < 6; ++q) {
+          const int64_t nx = x + d[q][0], ny = y + d[q][1], nz = z + d[q][2];
+          if (nx < 0 || ny < 0 || nz < 0 || nx >= r || ny >= r || nz >= r) continue;
+          const int64_t rk = rank[(size_t)((nx * r + ny) * r + nz)];
+          if (rk >= 0) slots[ns++] = (int32_t)(offset + rk);
+        }
+        while (ns < 8) slots[ns++] = (int32_t)self;
+        nbr.insert(nbr.end(), slots, slots + 8);
+        next_kc.push_back((int32_t)x);
+        next_kc.push_back((int32_t)y);
+        next_kc.push_back((int32_t)z);
+      }
+      next_begin[p] = offset;
+      offset += nb;
+    }
+    next_begin[P] = offset;
+    out.n.push_back(offset);
+    out.parent.push_back(std::move(parent));
+    out.nbr.push_back(std::move(nbr));
+    kc = std::move(next_kc);
+    below_begin = next_begin;
+    n_below = offset;
+    if (offset <= P || (int)out.n.size() == kMaxLevels) break;
+  }
+  return out;
 }
+
+// upload the hierarchy: parents, children (CSR, ascending), 1 / counts, neighbours
+cudaError_t upload_hierarchy(MpnnNet* n, const HostHierarchy& h) {
+  const int L = (int)h.n.size();
+  n->n_lev = L;
+  std::vector<int32_t> parent, cptr, cidx, nbr;
+  std::vector<float> inv;
+  int64_t off = 0, boff = 0, poff = 0;
+  for (int k = 0; k < L; ++k) {
+    const int64_t nk = h.n[k];
+    const std::vector<int32_t>& par = h.parent[k];
+    n->lev_n[k] = nk;
+    n->lev_off[k] = off;
+    n->below_off[k] = boff;
+    n->ptr_off[k] = poff;
+    std::vector<int32_t> cnt(nk + 1, 0);
+    for (int32_t a : par) cnt[a + 1] += 1;
+    for (int64_t a = 0; a < nk; ++a) {
+      inv.push_back(1.0f / (float)cnt[a + 1]);
+      cnt[a + 1] += cnt[a];
+    }
+    std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1), idx(par.size());
+    for (size_t i = 0; i < par.size(); ++i) idx[fill[par[i]]++] = (int32_t)i;
+    parent.insert(parent.end(), par.begin(), par.end());   // level-local aggregate indices
+    cptr.insert(cptr.end(), cnt.begin(), cnt.end());
+    cidx.insert(cidx.end(), idx.begin(), idx.end());
+    nbr.insert(nbr.end(), h.nbr[k].begin(), h.nbr[k].end());
+    off += nk;
+    boff += (int64_t)par.size();
+    poff += nk + 1;
+  }
+  n->lev_off[L] = off;
+  n->below_off[L] = boff;
+  n->n_coarse = off;
+  cudaError_t e;
+  if ((e = nalloc(n, &n->parent, parent.size()))) return e;
+  if ((e = nalloc(n, &n->child_ptr, cptr.size()))) return e;
+  if ((e = nalloc(n, &n->child_idx, cidx.size()))) return e;
+  if ((e = nalloc(n, &n->inv_count, inv.size()))) return e;
+  if ((e = nalloc(n, &n->cnbr, nbr.size()))) return e;
+  if ((e = cudaMemcpy(n->parent, parent.data(), parent.size() * 4, cudaMemcpyHostToDevice))) return e;
+  if ((e = cudaMemcpy(n->child_ptr, cptr.data(), cptr.size() * 4, cudaMemcpyHostToDevice))) return e;
+  if ((e = cudaMemcpy(n->child_idx, cidx.data(), cidx.size() * 4, cudaMemcpyHostToDevice))) return e;
+  if ((e = cudaMemcpy(n->inv_count, inv.data(), inv.size() * 4, cudaMemcpyHostToDevice))) return e;
+  return cudaMemcpy(n->cnbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice);
+}
+
+// grid of the forward layer kernel over ``rows``: persistent over 128-row tiles, as many
+// blocks as fit on the SMs (48 KB shared memory and 64 tensor-memory columns a block, up to
+// four an SM); the backward runs up to kGradBlocks blocks (80 KB and 256 columns a block,
+// two an SM)
+unsigned fwd_grid(const MpnnNet* n, int64_t rows) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + kTile - 1) / kTile, (int64_t)n->m->num_sms * 4));
+}
+unsigned bwd_grid(int64_t rows) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + kTile - 1) / kTile, kGradBlocks));
+}
+unsigned row16_grid(int64_t rows) { return grid_n(rows * 16); }
 
 // dynamic shared memory above 48 KB must be enabled per kernel (current device)
 cudaError_t layer_kernels_setup() {
-  cudaError_t e = cudaFuncSetAttribute(k_layer_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_layer_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_layer_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_layer_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
   return e;
 }
 
-// One evaluation of the network. train: activation set ``set`` keeps every layer;
-// otherwise hidden states ping-pong in H[0][0..1]. zero_charge: f0 = 0.
+// level-local views of the hierarchy arrays
+const int32_t* lev_parent(const MpnnNet* n, int k) { return n->parent + n->below_off[k]; }
+const int32_t* lev_child_ptr(const MpnnNet* n, int k) { return n->child_ptr + n->ptr_off[k]; }
+const int32_t* lev_child_idx(const MpnnNet* n, int k) { return n->child_idx + n->below_off[k]; }
+const float* lev_inv(const MpnnNet* n, int k) { return n->inv_count + n->lev_off[k]; }
+const int4* lev_nbr(const MpnnNet* n, int k) {
+  return reinterpret_cast<const int4*>(n->cnbr + (size_t)8 * n->lev_off[k]);
+}
+float* rows_at(float* base, const MpnnNet* n, int k) { return base ? base + (size_t)n->lev_off[k] * kHid : nullptr; }
+
+// result buffer of an inference evaluation
+float* infer_out(MpnnNet* n) { return n->n_lev > 0 ? n->H[0][0] : n->H[0][1]; }
+
+// One evaluation of the network. train: activation set ``set`` keeps every layer (hidden
+// states H[set][0..3], aggregate hops Hc/Mc/Zc[set]); otherwise set 0's buffers without the
+// messages and pre-activations, the fine hidden states ping-ponging in H[0][0..1] (result
+// in infer_out). zero_charge: f0 = 0.
 cudaError_t forward(MpnnNet* n, int set, const double* dq, const double* phi, bool train,
                     bool zero_charge, cudaStream_t s) {
   fvgb_mesh m = n->m;
   const int64_t N = n->N;
   constexpr double kEoverEps0 = 1.602176634e-19 / 8.8541878128e-12;
   float* F = n->F[train ? set : 0];
+  float* h0 = n->H[train ? set : 0][0];
+  float* h1 = n->H[train ? set : 0][1];
+  // inference: multilevel h2 = h1 + ... in place, h3 over h0; local h2 over h0, h3 over h1
+  float* h2 = train ? n->H[set][2] : (n->n_lev > 0 ? h1 : n->H[0][0]);
+  float* h3 = train ? n->H[set][3] : infer_out(n);
   k_features<<<grid_n(N), 256, 0, s>>>(N, dq, phi, m->g64.vol, kEoverEps0 / (n->V * n->s0),
                                        1.0 / (n->V * n->s1), zero_charge ? 1 : 0, F);
-  k_encode<<<grid_n(N * kHid), 256, 0, s>>>(N, F, n->theta, train ? n->Z0[set] : nullptr, n->H[train ? set : 0][0]);
+  k_encode<<<grid_n(N * kHid), 256, 0, s>>>(N, F, n->theta, train ? n->Z0[set] : nullptr, h0);
   count_launch(2);
   const int4* nbr = reinterpret_cast<const int4*>(m->g64.bc[n->bcset].at_nbr);
   const float4* wn = reinterpret_cast<const float4*>(n->wn);
-  for (int l = 0; l < kLayers; ++l) {
-    const float* Hin = train ? n->H[set][l] : n->H[0][l % 2];
-    float* Hout = train ? n->H[set][l + 1] : n->H[0][(l + 1) % 2];
-    k_layer_fwd<<<layer_grid(n, 4), kTileThreads, kFwdSmem, s>>>(N, Hin, nbr, wn, n->wbf + (size_t)l * kHid * kIn,
-                                                          n->theta + kOffLayer0 + l * kLayerSize + kHid * kIn,
-                                                          train ? n->M[set][l] : nullptr,
-                                                          train ? n->Z[set][l] : nullptr, Hout, n->m->d_status);
+  auto layer = [&](int l, const float* Hin, float* Mout, float* Zout, float* Hout, bool coarse, int64_t rows,
+                   const int4* nb) {
+    const __nv_bfloat16* W = n->wbf + (size_t)l * kHid * kIn;
+    const float* b = n->theta + kOffLayer0 + l * kLayerSize + kHid * kIn;
+    if (coarse)
+      k_layer_fwd<true><<<fwd_grid(n, rows), kTileThreads, kFwdSmem, s>>>(rows, Hin, nb, nullptr, W, b, Mout, Zout,
+                                                                           Hout, m->d_status);
+    else
+      k_layer_fwd<false><<<fwd_grid(n, rows), kTileThreads, kFwdSmem, s>>>(rows, Hin, nb, wn, W, b, Mout, Zout,
+                                                                            Hout, m->d_status);
+    count_launch();
+  };
+  layer(0, h0, train ? n->M[set][0] : nullptr, train ? n->Z[set][0] : nullptr, h1, false, N, nbr);
+  if (n->n_lev == 0) {
+    layer(1, h1, train ? n->M[set][1] : nullptr, train ? n->Z[set][1] : nullptr, h2, false, N, nbr);
+    layer(2, h2, train ? n->M[set][2] : nullptr, train ? n->Z[set][2] : nullptr, h3, false, N, nbr);
+    return cudaGetLastError();
+  }
+  // down the aggregate levels: mean of the level below, then kHops middle layers
+  const int cs = train ? set : 0;
+  for (int k = 0; k < n->n_lev; ++k) {
+    const int64_t nk = n->lev_n[k];
+    const float* below = k == 0 ? h1 : rows_at(n->Hc[cs][kHops], n, k - 1);
+    k_child_sum<<<row16_grid(nk), 256, 0, s>>>(nk, lev_child_ptr(n, k), lev_child_idx(n, k), below, lev_inv(n, k),
+                                               rows_at(n->Hc[cs][0], n, k));
+    count_launch();
+    for (int j = 0; j < kHops; ++j)
+      layer(1, rows_at(n->Hc[cs][j], n, k), train ? rows_at(n->Mc[set][j], n, k) : nullptr,
+            train ? rows_at(n->Zc[set][j], n, k) : nullptr, rows_at(n->Hc[cs][j + 1], n, k), true, nk, lev_nbr(n, k));
+  }
+  // back up: every level adds its aggregate's output, down to the cells
+  for (int k = n->n_lev - 1; k >= 1; --k) {
+    float* up = rows_at(n->Hc[cs][kHops], n, k - 1);
+    k_add_parent<<<row16_grid(n->lev_n[k - 1]), 256, 0, s>>>(n->lev_n[k - 1], up, rows_at(n->Hc[cs][kHops], n, k),
+                                                            lev_parent(n, k), nullptr, up);
     count_launch();
   }
+  k_add_parent<<<row16_grid(N), 256, 0, s>>>(N, h1, rows_at(n->Hc[cs][kHops], n, 0), lev_parent(n, 0), nullptr, h2);
+  count_launch();
+  layer(2, h2, train ? n->M[set][2] : nullptr, train ? n->Z[set][2] : nullptr, h3, false, N, nbr);
   return cudaGetLastError();
 }
 
@@ -855,7 +1146,7 @@ cudaError_t forward(MpnnNet* n, int set, const double* dq, const double* phi, bo
 cudaError_t predict(MpnnNet* n, const double* dq, const double* phi, double* dphi, cudaStream_t s) {
   cudaError_t e;
   const double scale = n->V * n->s2;
-  const float* last = n->H[0][kLayers % 2];
+  const float* last = infer_out(n);
   if ((e = forward(n, 0, dq, phi, false, false, s))) return e;
   k_decode<<<grid_n(n->N), 256, 0, s>>>(n->N, last, n->theta, scale, 0, dphi);
   if ((e = forward(n, 0, dq, phi, false, true, s))) return e;
@@ -864,27 +1155,63 @@ cudaError_t predict(MpnnNet* n, const double* dq, const double* phi, double* dph
   return cudaGetLastError();
 }
 
-// backward of sum_i dout_i sign N_set(f)_i through the layers and the encoder into the
-// gradient partial rows [row0, row0 + kGradBlocks)
+// backward of sum_i dout_i sign N_set(f)_i through the layers, the hierarchy and the encoder
+// into the gradient partial rows [row0, row0 + kGradBlocks) (zeroed by the caller)
 void backward_set(MpnnNet* n, int set, float sign, int row0, cudaStream_t s) {
   const int64_t N = n->N;
-  const int G = kGradBlocks;
   float* part = n->part + (size_t)row0 * kNParams;
-  k_head_dh<<<grid_n(N * kHid), 256, 0, s>>>(N, n->dout, n->theta, sign, n->dH);
-  count_launch();
-  float* dHn = n->dH;
-  float* dHo = n->dHb;
   const int4* nbr = reinterpret_cast<const int4*>(n->m->g64.bc[n->bcset].at_nbr);
   const float4* wn = reinterpret_cast<const float4*>(n->wn);
-  for (int l = kLayers - 1; l >= 0; --l) {
-    k_layer_bwd<<<kGradBlocks, kTileThreads, kBwdSmem, s>>>(
-        N, dHn, n->Z[set][l], n->H[set][l], n->M[set][l], n->wbf + (size_t)l * kHid * kIn, dHo, n->G,
-        part + kOffLayer0 + l * kLayerSize, n->m->d_status);
-    k_msg_add<<<grid_n(N * 32), 256, 0, s>>>(N, n->G, nbr, wn, dHo);
+  int* err = n->m->d_status;
+  auto layer_back = [&](int l, int64_t rows, const float* dHn, const float* Z, const float* Hin, const float* Min,
+                        float* dHo, bool coarse, const int4* nb) {
+    k_layer_bwd<<<bwd_grid(rows), kTileThreads, kBwdSmem, s>>>(rows, dHn, Z, Hin, Min, n->wbf + (size_t)l * kHid * kIn,
+                                                               dHo, n->G, part + kOffLayer0 + l * kLayerSize, err);
+    if (coarse) k_msg_add<true><<<grid_n(rows * 32), 256, 0, s>>>(rows, n->G, nb, nullptr, dHo);
+    else k_msg_add<false><<<grid_n(rows * 32), 256, 0, s>>>(rows, n->G, nb, wn, dHo);
     count_launch(2);
-    std::swap(dHn, dHo);
+  };
+  k_head_dh<<<grid_n(N * kHid), 256, 0, s>>>(N, n->dout, n->theta, sign, n->dH);
+  count_launch();
+  // layer 2: d h3 (dH) -> d h2 (dHb)
+  layer_back(2, N, n->dH, n->Z[set][2], n->H[set][2], n->M[set][2], n->dHb, false, nbr);
+  float* X = n->dHb;
+  if (n->n_lev == 0) {
+    // local: layer 1, d h2 (dHb) -> d h1 (dH); layer 0, -> d h0 (dHb)
+    layer_back(1, N, X, n->Z[set][1], n->H[set][1], n->M[set][1], n->dH, false, nbr);
+    layer_back(0, N, n->dH, n->Z[set][0], n->H[set][0], n->M[set][0], n->dHb, false, nbr);
+    k_encode_grad<<<kGradBlocks, kRowGroups * kHid, 0, s>>>(N, n->dHb, n->Z0[set], n->F[set], part);
+    count_launch();
+    return;
   }
-  k_encode_grad<<<G, kRowGroups * kHid, 0, s>>>(N, dHn, n->Z0[set], n->F[set], part);
+  // adjoint of the way up: the output of level k receives the sum over its nodes of theirs
+  const int L = n->n_lev;
+  k_child_sum<<<row16_grid(n->lev_n[0]), 256, 0, s>>>(n->lev_n[0], lev_child_ptr(n, 0), lev_child_idx(n, 0), X,
+                                                      nullptr, rows_at(n->dC, n, 0));
+  count_launch();
+  for (int k = 1; k < L; ++k) {
+    k_child_sum<<<row16_grid(n->lev_n[k]), 256, 0, s>>>(n->lev_n[k], lev_child_ptr(n, k), lev_child_idx(n, k),
+                                                        rows_at(n->dC, n, k - 1), nullptr, rows_at(n->dC, n, k));
+    count_launch();
+  }
+  // adjoint of the way down, coarsest level first: the hops in reverse, then the mean
+  for (int k = L - 1; k >= 0; --k) {
+    const int64_t nk = n->lev_n[k];
+    const float* cur = rows_at(n->dC, n, k);
+    for (int j = kHops - 1; j >= 0; --j) {
+      float* nxt = (j % 2 == (kHops - 1) % 2) ? n->cP : n->cQ;
+      layer_back(1, nk, cur, rows_at(n->Zc[set][j], n, k), rows_at(n->Hc[set][j], n, k), rows_at(n->Mc[set][j], n, k),
+                 nxt, true, lev_nbr(n, k));
+      cur = nxt;
+    }
+    float* down = k > 0 ? rows_at(n->dC, n, k - 1) : X;
+    const int64_t nb = k > 0 ? n->lev_n[k - 1] : N;
+    k_add_parent<<<row16_grid(nb), 256, 0, s>>>(nb, down, cur, lev_parent(n, k), lev_inv(n, k), down);
+    count_launch();
+  }
+  // layer 0: d h1 (dHb) -> d h0 (dH)
+  layer_back(0, N, X, n->Z[set][0], n->H[set][0], n->M[set][0], n->dH, false, nbr);
+  k_encode_grad<<<kGradBlocks, kRowGroups * kHid, 0, s>>>(N, n->dH, n->Z0[set], n->F[set], part);
   count_launch();
 }
 
@@ -916,10 +1243,12 @@ using namespace fvgb;
 
 extern "C" {
 
-fvgb_status fvgb_mpnn_create(fvgb_mesh m, int32_t bcset, fvgb_mpnn* out) {
+fvgb_status fvgb_mpnn_create(fvgb_mesh m, int32_t bcset, int32_t multilevel, fvgb_mpnn* out) {
   if (!m || !out) { set_error("null argument"); return FVGB_EINVAL; }
   *out = nullptr;
   if (bcset < 0 || bcset >= (int32_t)m->g64.bc.size()) { set_error("bcset index out of range"); return FVGB_EINVAL; }
+  if (m->topo.dim != 3 || m->topo.N < 1) { set_error("the network needs a non-empty 3D mesh"); return FVGB_EINVAL; }
+  if (multilevel != 0 && multilevel != 1) { set_error("multilevel must be 0 or 1"); return FVGB_EINVAL; }
   fvgb_mpnn_s* n = new fvgb_mpnn_s();
   n->m = m;
   n->bcset = bcset;
@@ -941,6 +1270,15 @@ fvgb_status fvgb_mpnn_create(fvgb_mesh m, int32_t bcset, fvgb_mpnn* out) {
   if ((e = nalloc(n, &n->F[0], (size_t)n->N * 2))) return fail("allocation");
   if ((e = nalloc(n, &n->H[0][0], NH))) return fail("allocation");
   if ((e = nalloc(n, &n->H[0][1], NH))) return fail("allocation");
+  if (multilevel) {
+    std::vector<double> cen((size_t)3 * n->N);
+    if ((e = cudaMemcpy(cen.data(), m->g64.cen, cen.size() * sizeof(double), cudaMemcpyDeviceToHost)))
+      return fail("centre copy");
+    if ((e = upload_hierarchy(n, build_hierarchy(cen.data(), n->N, m->part_cell_begin))))
+      return fail("aggregate hierarchy");
+  }
+  for (int j = 0; j <= kHops && n->n_lev > 0; ++j)
+    if ((e = nalloc(n, &n->Hc[0][j], (size_t)n->n_coarse * kHid))) return fail("allocation");
   if ((e = nalloc(n, &n->dloss, 2))) return fail("allocation");
   if ((e = cudaMallocHost((void**)&n->hloss, sizeof(double)))) return fail("pinned allocation");
   if ((e = cudaMemset(n->theta, 0, kNParams * sizeof(float)))) return fail("memset");
@@ -956,6 +1294,28 @@ fvgb_status fvgb_mpnn_create(fvgb_mesh m, int32_t bcset, fvgb_mpnn* out) {
   count_launch(3);
   if ((e = cudaDeviceSynchronize())) return fail("message weights");
   *out = n;
+  return FVGB_OK;
+}
+
+fvgb_status fvgb_mpnn_hierarchy(int64_t n_cell, const double* cen, int32_t n_part, const int64_t* part_begin,
+                                int32_t* n_levels, int64_t* level_n, int32_t* parent, int32_t* nbr) {
+  if (n_cell < 1 || !cen || n_part < 1 || !part_begin || !n_levels || !level_n) {
+    set_error("bad arguments");
+    return FVGB_EINVAL;
+  }
+  std::vector<int64_t> pb(part_begin, part_begin + n_part + 1);
+  if (pb[0] != 0 || pb[n_part] != n_cell) { set_error("part ranges must cover the cells"); return FVGB_EINVAL; }
+  for (int p = 0; p < n_part; ++p)
+    if (pb[p + 1] <= pb[p]) { set_error("empty or decreasing part range"); return FVGB_EINVAL; }
+  for (int64_t i = 0; i < 3 * n_cell; ++i)
+    if (!std::isfinite(cen[i])) { set_error("non-finite centre"); return FVGB_EINVAL; }
+  const HostHierarchy h = build_hierarchy(cen, n_cell, pb);
+  *n_levels = (int32_t)h.n.size();
+  for (size_t k = 0; k < h.n.size(); ++k) level_n[k] = h.n[k];
+  for (size_t k = 0; k < h.n.size(); ++k) {
+    if (parent) parent = std::copy(h.parent[k].begin(), h.parent[k].end(), parent);
+    if (nbr) nbr = std::copy(h.nbr[k].begin(), h.nbr[k].end(), nbr);
+  }
   return FVGB_OK;
 }
 

@@ -15,21 +15,22 @@ from . import capi
 E_OVER_EPS0 = 1.602176634e-19 / 8.8541878128e-12
 
 
-def init_params(seed):
-    """Seeded initial parameters (FP32): weight matrices uniform in +-sqrt(6 / fan_in),
-    the decoder vector in +-sqrt(3 / 64), biases zero; layout of fvgb_mpnn_set_params."""
+def init_params(seed, multilevel=True):
+    """Seeded initial parameters (FP32), layout of fvgb_mpnn_set_params: weight matrices and
+    the decoder vector uniform in +-b, biases zero; b = 1 / sqrt(fan_in) for the multilevel
+    architecture (its middle layer is applied twice on every aggregate level and the levels'
+    outputs are summed, so larger initial weights compound into outputs far above the
+    targets), b = sqrt(6 / fan_in) for the local one (measured the better start for each)."""
     rng = np.random.default_rng(seed)
     blocks = [("W", 64, 2), ("b", 64, 0)]
     for _ in range(3):
         blocks += [("W", 64, 128), ("b", 64, 0)]
-    blocks += [("d", 64, 0), ("b", 1, 0)]
+    blocks += [("W", 1, 64), ("b", 1, 0)]
     out = []
     for kind, n, fan in blocks:
         if kind == "W":
-            bound = np.sqrt(6.0 / fan)
+            bound = 1.0 / np.sqrt(fan) if multilevel else np.sqrt(6.0 / fan)
             out.append(rng.uniform(-bound, bound, size=(n, fan)).ravel())
-        elif kind == "d":
-            out.append(rng.uniform(-np.sqrt(3.0 / 64), np.sqrt(3.0 / 64), size=n))
         else:
             out.append(np.zeros(n))
     theta = np.concatenate(out).astype(np.float32)
@@ -114,15 +115,23 @@ def _rms_scales(sums, count, V, n_cell):
     return max(E_OVER_EPS0 * rq * h2 / V, 1e-30), max(rp / V, 1e-30), max(rd / V, 1e-30)
 
 
+# architecture of each network: the start from the previous potential needs the reach of
+# the aggregate hierarchy (the increment is the global response to the charge change); the
+# correction of the extrapolation does better with the local network (measured)
+MULTILEVEL = {False: True, True: False}
+
+
 def train_streaming(dm, mesh, cases, dt, steps, solve, V, lr=1e-3, lr_final=3e-4, seed=0,
-                    log_every=25, log=None):
+                    log_every=25, log=None, multilevel=None):
     """Train the two networks of the learned start (start from the previous potential, and
     correction of the extrapolation) while the solver generates their pairs: one Adam step
     per pair, as each streamer step of each case produces it, so that no pair is stored.
     The normalisation scales come from a first run of cases[0]. The cases run in a seeded
-    random order; the last third of them with the smaller learning rate.
+    random order; the last third of them with the smaller learning rate. multilevel: the
+    architecture per network ({extrapolated: bool}, default MULTILEVEL).
 
-    Returns ({False: (theta, scales), True: (theta, scales)}, info)."""
+    Returns ({False: (theta, scales, multilevel), True: (...)}, info)."""
+    arch = dict(MULTILEVEL if multilevel is None else multilevel)
     nets = {}
     sums = {w: [torch.zeros((), dtype=torch.float64, device=dm.device) for _ in range(3)] for w in (0, 1)}
     count = {0: 0, 1: 0}
@@ -135,8 +144,8 @@ def train_streaming(dm, mesh, cases, dt, steps, solve, V, lr=1e-3, lr_final=3e-4
     streamer_run(dm, cases[0], mesh, dt, steps, solve, on_pair=acc)
     scales = {w: _rms_scales(sums[w], count[w], V, dm.n_cell) for w in (0, 1)}
     for w in (0, 1):
-        nets[w] = capi.fvgb_mpnn_create(dm.handle, 1)
-        capi.fvgb_mpnn_set_params(nets[w], init_params(w))
+        nets[w] = capi.fvgb_mpnn_create(dm.handle, 1, multilevel=arch[bool(w)])
+        capi.fvgb_mpnn_set_params(nets[w], init_params(w, arch[bool(w)]))
         capi.fvgb_mpnn_set_scales(nets[w], V, *scales[w])
     order = np.random.default_rng(seed).permutation(len(cases))
     hist = {0: [], 1: []}
@@ -156,24 +165,26 @@ def train_streaming(dm, mesh, cases, dt, steps, solve, V, lr=1e-3, lr_final=3e-4
             log(f"trained on case {rank + 1}/{len(cases)}")
     out = {}
     for w in (0, 1):
-        out[bool(w)] = (capi.fvgb_mpnn_get_params(nets[w]), scales[w])
+        out[bool(w)] = (capi.fvgb_mpnn_get_params(nets[w]), scales[w], arch[bool(w)])
         capi.fvgb_mpnn_free(nets[w])
     info = {"pairs_trained": {"previous_phi": n_pairs[0], "extrapolated": n_pairs[1]},
             "loss_first_last": {"previous_phi": [hist[0][0], hist[0][-1]] if hist[0] else None,
                                 "extrapolated": [hist[1][0], hist[1][-1]] if hist[1] else None},
             "loss_history_every": log_every,
             "scales": {"previous_phi": scales[0], "extrapolated": scales[1]},
-            "learning_rates": [lr, lr_final]}
+            "learning_rates": [lr, lr_final],
+            "architecture": {"previous_phi": "multilevel" if arch[False] else "local",
+                             "extrapolated": "multilevel" if arch[True] else "local"}}
     return out, info
 
 
 def held_out_run(dm, mesh, case, dt, steps, solve, V, net=None, extrapolate=False, skip=2):
-    """Steps of a held-out case with the learned start ``net`` = (theta, scales) or without
+    """Steps of a held-out case with the learned start ``net`` = (theta, scales, multilevel) or without
     it; returns inner / outer iterations and device time summed over steps skip.., the
     largest relative residual and how many learned starts passed the residual check."""
     handle = None
     if net is not None:
-        handle = capi.fvgb_mpnn_create(dm.handle, 1)
+        handle = capi.fvgb_mpnn_create(dm.handle, 1, multilevel=net[2])
         capi.fvgb_mpnn_set_params(handle, net[0])
         capi.fvgb_mpnn_set_scales(handle, V, *net[1])
     ne0, ni0 = case.initial(mesh)

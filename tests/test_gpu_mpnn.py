@@ -1,5 +1,6 @@
-"""GPU message-passing warm start against the FP64 oracle: forward, loss and gradient
-(BF16 tensor-core products, so a BF16 tolerance), training, and the gain of the learned
+"""GPU message-passing warm start against the FP64 oracle: forward, loss and gradient of
+the multilevel network (BF16 tensor-core products, so a BF16 tolerance) on a mesh with
+three aggregate levels and on an ensemble of parts, training, and the gain of the learned
 warm start over the previous potential on held-out streamer runs."""
 import numpy as np
 import pytest
@@ -36,7 +37,8 @@ def _bf16_layers(theta):
     return om.pack(p)
 
 
-def test_forward_loss_gradient_parity(dev):
+@pytest.mark.parametrize("multilevel", [True, False])
+def test_forward_loss_gradient_parity(dev, multilevel):
     capi, device, _ = dev
     m = jittered_cube(6, seed=21)
     g = geometry_of(m)
@@ -48,7 +50,7 @@ def test_forward_loss_gradient_parity(dev):
     dq = 1e9 * rng.normal(size=g.n_cell) * np.exp(-20 * ((g.cen - 0.5) ** 2).sum(1))
     phi = V * g.cen[:, 2] + 50.0 * rng.normal(size=g.n_cell)
     target = V * s2 * rng.normal(size=g.n_cell)
-    net = capi.fvgb_mpnn_create(dm.handle, 1)
+    net = capi.fvgb_mpnn_create(dm.handle, 1, multilevel=multilevel)
     capi.fvgb_mpnn_set_params(net, theta)
     capi.fvgb_mpnn_set_scales(net, V, s0, s1, s2)
     assert np.array_equal(capi.fvgb_mpnn_get_params(net), theta)
@@ -57,7 +59,8 @@ def test_forward_loss_gradient_parity(dev):
     capi.fvgb_mpnn_predict(net, dqd, phid, pred)
     loss, grad = capi.fvgb_mpnn_loss_grad(net, dqd, phid, td)
     torch.cuda.synchronize()
-    graph = om.message_graph(g)
+    graph = om.network_graph(g, multilevel=multilevel)
+    assert not multilevel or len(graph[1]) == 3
     f = om.features(g, dq, phi, V, s0, s1)
     th = _bf16_layers(theta)
     want = V * s2 * om.predict(graph, th, f)
@@ -71,6 +74,53 @@ def test_forward_loss_gradient_parity(dev):
     capi.fvgb_mpnn_predict(net, torch.zeros_like(dqd), phid, pred)
     torch.cuda.synchronize()
     assert torch.count_nonzero(pred).item() == 0
+    capi.fvgb_mpnn_free(net)
+    dm.free()
+
+
+def test_ensemble_parity(dev):
+    """Two meshes as one ensemble: the hierarchy is built per part (no aggregate and no
+    message crosses between the meshes); message weights are normalised by the largest
+    c1 of the whole ensemble."""
+    from oracle import fv
+    capi, device, _ = dev
+    meshes = [jittered_cube(5, seed=31), jittered_cube(6, seed=32)]
+    geos = [geometry_of(m) for m in meshes]
+    case = StreamerCase()
+    dm = device.DeviceMesh(meshes, [[case.bc_ne(), case.bc_phi()]] * 2, ensemble=True)
+    nb = np.cumsum([0] + [g.n_cell for g in geos])
+    assert list(dm.part_begin) == list(nb)
+    L, R, c1 = [], [], []
+    for g, o in zip(geos, nb):
+        inr = g.face_R >= 0
+        L.append(g.face_L[inr] + o)
+        R.append(g.face_R[inr] + o)
+        c1.append(fv.diamond_coefficients(g)[inr, 0])
+    c1 = np.concatenate(c1)
+    cen = np.concatenate([g.cen for g in geos])
+    graph = ((np.concatenate(L), np.concatenate(R), c1 / c1.max()), om.hierarchy(cen, nb))
+    rng = np.random.default_rng(8)
+    theta = (om.init_params(4) + 0.02 * rng.normal(size=om.n_params())).astype(np.float32)
+    V, s0, s1, s2 = 1.0e4, 3.0e-6, 0.5, 1.0e-6
+    dq = 1e9 * rng.normal(size=nb[-1]) * np.exp(-20 * ((cen - 0.5) ** 2).sum(1))
+    phi = V * cen[:, 2] + 50.0 * rng.normal(size=nb[-1])
+    target = V * s2 * rng.normal(size=nb[-1])
+    net = capi.fvgb_mpnn_create(dm.handle, 1)
+    capi.fvgb_mpnn_set_params(net, theta)
+    capi.fvgb_mpnn_set_scales(net, V, s0, s1, s2)
+    dqd, phid, td = (dm.to_device(x, torch.float64) for x in (dq, phi, target))
+    pred = torch.empty_like(dqd)
+    capi.fvgb_mpnn_predict(net, dqd, phid, pred)
+    loss, grad = capi.fvgb_mpnn_loss_grad(net, dqd, phid, td)
+    torch.cuda.synchronize()
+    f = np.concatenate([om.features(g, dq[a:b], phi[a:b], V, s0, s1) for g, a, b in zip(geos, nb[:-1], nb[1:])])
+    th = _bf16_layers(theta)
+    want = V * s2 * om.predict(graph, th, f)
+    assert rel(dm.to_host(pred), want) < 3e-2
+    ol, og = om.backward(graph, th, f, target / (V * s2))
+    assert loss == pytest.approx(ol, rel=3e-2)
+    cos = float(np.dot(grad, og) / (np.linalg.norm(grad) * np.linalg.norm(og)))
+    assert rel(grad, og) < 5e-2 and cos > 0.998
     capi.fvgb_mpnn_free(net)
     dm.free()
 
@@ -102,7 +152,8 @@ def test_learned_warm_start_beats_previous_potential(dev):
     """Train on streamer runs of the plain solver (18 seeds), evaluate on 2 held-out seed
     positions: the solves started from the learned guess take fewer CG iterations in total,
     every step still converged to 1e-8. The same on top of the start from the linear
-    extrapolation in time, which alone saves most of the iterations."""
+    extrapolation in time, which alone saves most of the iterations. The first network is
+    multilevel, the correction of the extrapolation local (the trainer's choice)."""
     capi, device, learned = dev
     k = 16
     mesh = streamer_mesh(k, 301)
@@ -119,9 +170,9 @@ def test_learned_warm_start_beats_previous_potential(dev):
         pairs_p += pp
         pairs_x += px
     nets = []
-    for pairs in (pairs_p, pairs_x):
-        net = capi.fvgb_mpnn_create(dm.handle, 1)
-        capi.fvgb_mpnn_set_params(net, om.init_params(0).astype(np.float32))
+    for pairs, extrap in ((pairs_p, False), (pairs_x, True)):
+        net = capi.fvgb_mpnn_create(dm.handle, 1, multilevel=learned.MULTILEVEL[extrap])
+        capi.fvgb_mpnn_set_params(net, learned.init_params(0, learned.MULTILEVEL[extrap]))
         capi.fvgb_mpnn_set_scales(net, c0.V, *learned.scales_for(pairs, c0.V, dm.n_cell))
         for ep in range(4):
             learned.train(net, pairs, epochs=1, lr=1e-3 if ep < 3 else 3e-4, seed=ep)
@@ -148,4 +199,36 @@ def test_learned_warm_start_beats_previous_potential(dev):
     assert outer["learned_extrap"] <= outer["extrap"], outer
     for net in nets:
         capi.fvgb_mpnn_free(net)
+    dm.free()
+
+
+@pytest.mark.parametrize("multilevel,extrapolate", [(True, False), (False, True)])
+def test_learned_start_graph_matches_host(dev, multilevel, extrapolate):
+    """Streamer steps with the learned start: captured as graphs (the network's kernels
+    inside the captured step) they give bitwise the results of host-driven steps."""
+    capi, device, learned = dev
+    m = jittered_cube(8, seed=41)
+    case = StreamerCase()
+    dm = device.DeviceMesh(m, [case.bc_ne(), case.bc_phi()], prec="mixed")
+    net = capi.fvgb_mpnn_create(dm.handle, 1, multilevel=multilevel)
+    capi.fvgb_mpnn_set_params(net, learned.init_params(3, multilevel))
+    capi.fvgb_mpnn_set_scales(net, case.V, 1e-6, 0.6, 1e-5)
+    sp = capi.streamer_params(mu=case.mu, A=case.A, B=case.B, De=case.De, dt=case.dt(1.0 / 8),
+                              solve=capi.solve_opts(rtol=1e-8, prec=capi.FVGB_FP32), warm=net,
+                              extrapolate=extrapolate)
+    ne0, ni0 = case.initial(m)
+    out = []
+    for graph in (False, True):
+        ne, ni = dm.to_device(ne0), dm.to_device(ni0)
+        phi = torch.zeros(dm.n_cell, dtype=torch.float64, device="cuda")
+        capi.fvgb_streamer_reset(dm.handle)
+        capi.fvgb_set_graph_mode(dm.handle, graph)
+        infos = capi.fvgb_streamer_step(dm.handle, sp, ne, ni, phi, None, 6)
+        torch.cuda.synchronize()
+        out.append((ne.clone(), ni.clone(), phi.clone(), [i["inner_its_total"] for i in infos]))
+    capi.fvgb_set_graph_mode(dm.handle, False)
+    assert out[0][3] == out[1][3]
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert torch.equal(a, b)
+    capi.fvgb_mpnn_free(net)
     dm.free()

@@ -56,6 +56,11 @@ def test_gradient_matches_finite_differences():
     _fd_check(net, g.n_cell, 0)
 
 
+def test_gradient_matches_finite_differences_local():
+    g = geometry_of(jittered_cube(3, seed=9))
+    _fd_check(mpnn.network_graph(g, multilevel=False), g.n_cell, 4)
+
+
 def test_gradient_matches_finite_differences_two_parts():
     """Two parts (the halves of the cell list): levels per part, three levels deep."""
     g = geometry_of(jittered_cube(6, seed=5))
@@ -128,8 +133,8 @@ def test_level_operators():
 
 def test_network_reaches_the_whole_domain():
     """A charge change in one cell changes the prediction in every cell (the coarse
-    levels carry it), while without the levels the network reaches only the cells within
-    two face hops (its two fine layers)."""
+    levels carry it), while the local network reaches only the cells within three face
+    hops."""
     g = geometry_of(jittered_cube(4, seed=9))
     net = mpnn.network_graph(g)
     theta = mpnn.init_params(7)
@@ -140,9 +145,15 @@ def test_network_reaches_the_whole_domain():
     f2[0, 0] += 1.0
     delta = np.abs(mpnn.forward(net, theta, f2)[0] - base)
     assert np.all(delta > 0.0)
-    fine_only = (net[0], [])
-    delta_fine = np.abs(mpnn.forward(fine_only, theta, f2)[0] - mpnn.forward(fine_only, theta, f)[0])
-    assert np.count_nonzero(delta_fine) < g.n_cell // 2
+    local = mpnn.network_graph(g, multilevel=False)
+    delta_local = np.abs(mpnn.forward(local, theta, f2)[0] - mpnn.forward(local, theta, f)[0])
+    # cells within three face hops of cell 0
+    L, R, _ = local[0]
+    near = {0}
+    for _ in range(3):
+        near |= {int(b) for a, b in zip(L, R) if a in near} | {int(a) for a, b in zip(L, R) if b in near}
+    far = np.setdiff1d(np.arange(g.n_cell), sorted(near))
+    assert far.size > 0 and np.all(delta_local[far] == 0.0) and np.any(delta_local > 0.0)
 
 
 def test_layout_and_bf16_rounding():
