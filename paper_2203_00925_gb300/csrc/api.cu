@@ -342,8 +342,11 @@ fvgb_status solve_impl(fvgb_mesh m, int bcset, const double* f, double* phi,
   if (fp32 && !is_fp32(m)) { set_error("FP32 inner solve needs a mesh uploaded with FVGB_FP32 or FVGB_MIXED"); return FVGB_EINVAL; }
   double* b = m->dphi_tmp2;
   double* r = m->dphi_tmp;
+  // after a learned start of a streamer step, b and the start's residual are already formed
+  const bool primed = m->solve_primed == bcset;
+  m->solve_primed = -1;
   if (o->inner > 0) FVGB_TRY_ST(amg_ensure(m, bcset, fp32, s));
-  fvgb_status st = poisson_rhs_impl(m, bcset, f, b, s);
+  fvgb_status st = primed ? FVGB_OK : poisson_rhs_impl(m, bcset, f, b, s);
   if (st) return st;
   // host staging in pinned memory: [0, P) norms, [P, 2P) ints (active flags, inner its)
   double* hn = m->h_scal + 8;
@@ -381,18 +384,22 @@ fvgb_status solve_impl(fvgb_mesh m, int bcset, const double* f, double* phi,
     if (bn2[p] == 0.0) any_zero = true;
   }
   loc.bnorm = std::sqrt(bsum);
-  if (any_zero) {   // a part with b = 0 has the solution 0
+  if (any_zero) {   // a part with b = 0 has the solution 0 (and then the residual 0)
     for (int p = 0; p < P; ++p)
-      if (bn2[p] == 0.0)
-        FVGB_TRY(cudaMemsetAsync(phi + m->part_cell_begin[p], 0,
-                                 (m->part_cell_begin[p + 1] - m->part_cell_begin[p]) * sizeof(double), s), "memset");
+      if (bn2[p] == 0.0) {
+        const size_t bytes = (m->part_cell_begin[p + 1] - m->part_cell_begin[p]) * sizeof(double);
+        FVGB_TRY(cudaMemsetAsync(phi + m->part_cell_begin[p], 0, bytes, s), "memset");
+        if (primed) FVGB_TRY(cudaMemsetAsync(r + m->part_cell_begin[p], 0, bytes, s), "memset");
+      }
   }
   m->last_outer.assign(P, 0);
   m->last_inner.assign(P, 0);
   m->last_rel.assign(P, 0.0);
   for (int outer = 0;; ++outer) {
-    st = poisson_residual(m, bcset, phi, b, r, s);
-    if (st) return st;
+    if (!(primed && outer == 0)) {
+      st = poisson_residual(m, bcset, phi, b, r, s);
+      if (st) return st;
+    }
     FVGB_TRY(launch_part_sumsq(m, r, m->parts.norms, s), "norm kernel");
     FVGB_TRY(cudaMemcpyAsync(hn, m->parts.norms, P * sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
     if (outer > 0) {
@@ -470,6 +477,7 @@ fvgb_status warm_start(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, voi
                        int hist, cudaStream_t s) {
   const int64_t N = m->topo.N;
   const int P = m->parts.n_part;
+  m->solve_primed = -1;
   if (!m->q_prev) {
     FVGB_TRY(dalloc(m, &m->q_prev, N), "allocation");
     FVGB_TRY(dalloc(m, &m->dq, N), "allocation");
@@ -502,8 +510,11 @@ fvgb_status warm_start(fvgb_mesh m, const fvgb_streamer_params* p, void* ne, voi
   // r0 - r1 = A pred: the residual-minimising scale of the correction, per part
   FVGB_TRY(launch_part_dots(m, r0, r1, m->warm_norms, s), "dot kernel");
   m->warm_check_pending = true;
-  return cuda_status(launch_scale_start(m, m->warm_norms, m->phi_save, m->dphi_pred, phi, m->warm_used,
-                                        m->warm_scale, s), "start kernel");
+  FVGB_TRY(launch_scale_start(m, m->warm_norms, m->phi_save, m->dphi_pred, phi, m->warm_used, m->warm_scale,
+                              r0, r1, s), "start kernel");
+  // b and the start's residual are in place for this step's solve (same source, same set)
+  m->solve_primed = p->bcset_phi;
+  return FVGB_OK;
 }
 
 // Field, cell physics and one transport stage of eq. 6 (after the stage's solve):
@@ -937,6 +948,7 @@ fvgb_status fvgb_poisson_solve(fvgb_mesh m, int32_t bcset, const double* f, doub
   if (fvgb_status st = check_mesh(m)) return st;
   if (fvgb_status st = check_bcset(m, bcset)) return st;
   if (!phi || !opts_ok(o)) { set_error("bad solve arguments"); return FVGB_EINVAL; }
+  m->solve_primed = -1;   // a caller's own right-hand side: nothing left by a streamer step applies
   return solve_impl(m, bcset, f, phi, o, info, (cudaStream_t)stream);
 }
 
@@ -970,6 +982,7 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
   int n0 = 0;
   const bool warm = warm_requested(p);
   const int stages = p->stages == 3 ? 3 : 1;
+  m->solve_primed = -1;     // only a learned start of this call primes a solve
   if (m->use_graph && stages == 1) {
     // a captured step assumes a full warm-start history: build it with host-driven steps
     const int need = warm ? std::max(0, 2 - m->warm_hist) : 0;
@@ -980,6 +993,7 @@ fvgb_status fvgb_streamer_step(fvgb_mesh m, const fvgb_streamer_params* p, void*
   const bool fp32 = is_fp32(m);
   double* f = m->w64.tmp;   // FP64 scratch of the mesh (unused by the FP64 transport path)
   for (int n = 0; n < nsteps; ++n) {
+    m->solve_primed = -1;
     if (warm) {
       fvgb_status st = warm_start(m, p, ne, ni, phi, m->warm_hist, s);
       if (st) return st;

@@ -110,11 +110,14 @@ __global__ void k_graph_init(int P, int* __restrict__ ctl, int* __restrict__ out
 
 // A part whose right-hand side is zero has the solution zero (block p handles part p).
 __global__ void k_zero_parts(const double* __restrict__ bn2, const int32_t* __restrict__ part_sc,
-                             const int64_t* __restrict__ sc_begin, double* __restrict__ phi) {
-  const int p = blockIdx.x;
+                             const int64_t* __restrict__ sc_begin, double* __restrict__ phi, double* __restrict__ r) {
+  const int p = blockIdx.y;
   if (bn2[p] != 0.0) return;
   const int64_t lo = sc_begin[part_sc[p]], hi = sc_begin[part_sc[p + 1]];
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) phi[i] = 0.0;
+  for (int64_t i = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < hi; i += (int64_t)gridDim.x * blockDim.x) {
+    phi[i] = 0.0;
+    if (r) r[i] = 0.0;
+  }
 }
 
 bool same_spots(const std::vector<fvgb_spot>& a, const fvgb_streamer_params& b) {
@@ -170,13 +173,19 @@ fvgb_status build_graph(fvgb_mesh m, GraphState& g, const fvgb_streamer_params* 
   // ---- before the loop
   if (warm_requested(p) && (st = warm_start(m, p, ne, ni, phi, 2, g.cs))) return bail(st);
   m->warm_check_pending = false;   // captured, not run: graph steps are not counted
-  if ((st = cuda_status(launch_poisson_source(m, ne, ni, is_fp32(m), f, g.cs), "source kernel"))) return bail(st);
-  if ((st = poisson_rhs_impl(m, p->bcset_phi, f, b, g.cs))) return bail(st);
+  // after a learned start, b and the start's residual are already formed (as in solve_impl)
+  const bool primed = m->solve_primed == p->bcset_phi;
+  m->solve_primed = -1;
+  if (!primed) {
+    if ((st = cuda_status(launch_poisson_source(m, ne, ni, is_fp32(m), f, g.cs), "source kernel"))) return bail(st);
+    if ((st = poisson_rhs_impl(m, p->bcset_phi, f, b, g.cs))) return bail(st);
+  }
   if ((st = cuda_status(launch_part_sumsq(m, b, g.bn2, g.cs), "norm kernel"))) return bail(st);
   k_graph_init<<<1, 128, 0, g.cs>>>(P, g.ctl, g.outer, g.inner);
-  k_zero_parts<<<P, 256, 0, g.cs>>>(g.bn2, m->parts.part_sc, m->parts.sc_begin, phi);
+  k_zero_parts<<<part_grid(m), 256, 0, g.cs>>>(g.bn2, m->parts.part_sc, m->parts.sc_begin, phi,
+                                               primed ? r : nullptr);
   count_launch(2);
-  if ((st = poisson_residual(m, p->bcset_phi, phi, b, r, g.cs))) return bail(st);
+  if (!primed && (st = poisson_residual(m, p->bcset_phi, phi, b, r, g.cs))) return bail(st);
   if ((st = cuda_status(launch_part_sumsq(m, r, m->parts.norms, g.cs), "norm kernel"))) return bail(st);
   k_decide<<<1, 128, 0, g.cs>>>(P, m->parts.norms, g.bn2, p->solve.rtol, p->solve.maxit_outer, 0,
                                 m->parts.out_inner, m->d_cg_info, m->barrier, g.ctl, m->parts.active,

@@ -176,6 +176,9 @@ struct fvgb_mesh_s {
   int* warm_used = nullptr;             // [P] 1 where the learned correction was used (scale > 0)
   double* warm_scale = nullptr;         // [P] scale of the learned correction in the start
   bool warm_check_pending = false;      // warm_used of a host-driven step not yet counted
+  int solve_primed = -1;                // boundary set whose next solve finds its b and its start's
+                                        // residual already in dphi_tmp2 / dphi_tmp (left by the
+                                        // learned start); -1: none
   int warm_hist = 0;                    // streamer steps recorded in the history (capped at 3)
   fvgb::GraphState* graph = nullptr;    // captured step graph (graph.cu)
   fvgb::AmgState* amg = nullptr;        // multigrid hierarchies per boundary set (amg.cu)
@@ -257,8 +260,10 @@ cudaError_t launch_extrapolate(fvgb_mesh_s* m, bool extrap, double* phi, double*
                                cudaStream_t s);
 cudaError_t launch_history_pair(fvgb_mesh_s* m, int which, const double* phi, double* q_out, double* p_out,
                                 double* d_out, cudaStream_t s);
+dim3 part_grid(const fvgb_mesh_s* m);   // blocks per part x parts of per-part elementwise kernels
 cudaError_t launch_scale_start(fvgb_mesh_s* m, const double* dots, const double* saved, const double* pred,
-                               double* phi, int* used, double* scale, cudaStream_t s);
+                               double* phi, int* used, double* scale, double* r0, const double* r1,
+                               cudaStream_t s);
 cudaError_t launch_axpy_d(const double* x, double a, double* y, int64_t n, cudaStream_t s);
 cudaError_t launch_add_to_double(const void* x, bool fp32, double* y, int64_t n, cudaStream_t s);
 cudaError_t launch_convert(const double* x, float* y, int64_t n, cudaStream_t s);

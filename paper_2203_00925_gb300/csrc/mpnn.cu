@@ -69,6 +69,7 @@ struct fvgb_mpnn_s {
   float* grad = nullptr;               // [params]
   __nv_bfloat16* wbf = nullptr;        // [3][64][128]
   float* wn = nullptr;                 // [N][4] message weights
+  double* hcell = nullptr;             // [N] mu^(1/3)
   // aggregate hierarchy (multilevel architecture; n_lev = 0: the middle layer runs on the
   // faces): level k (0-based) has lev_n[k] nodes, rows [lev_off[k], + lev_n[k]) of the
   // coarse arrays; the nodes below it are the cells (k = 0) or level k - 1's
@@ -82,6 +83,7 @@ struct fvgb_mpnn_s {
   int32_t* child_idx = nullptr;        // per level: nodes below, by aggregate, ascending
   float* inv_count = nullptr;          // [coarse rows] 1 / nodes in the aggregate
   int32_t* cnbr = nullptr;             // [coarse rows][8] face-adjacent aggregates, padded with self
+  int32_t* nparent = nullptr;          // [N][4] level-1 aggregate of each face-neighbour slot
   int64_t n_coarse = 0;
   // activations of the two evaluations N(f) and N(f0 = 0) (set 0 and set 1)
   float* F[2] = {};                    // [N][2]
@@ -232,11 +234,17 @@ __device__ __forceinline__ float* stage_at(float* S, int r, int q) {
 }
 
 // ---- features and message weights ---------------------------------------------------------
+// hcell = mu^(1/3) of every cell, once per network (the features' length scale)
+__global__ void k_cell_size(int64_t N, const double* __restrict__ vol, double* __restrict__ hcell) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    hcell[i] = cbrt(vol[i]);
+}
+
 __global__ void k_features(int64_t N, const double* __restrict__ dq, const double* __restrict__ phi,
-                           const double* __restrict__ vol, double c0, double c1, int zero_charge,
+                           const double* __restrict__ hcell, double c0, double c1, int zero_charge,
                            float* __restrict__ F) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const double h = cbrt(vol[i]);
+    const double h = hcell[i];
     F[2 * i] = zero_charge ? 0.0f : (float)(c0 * dq[i] * h * h);
     F[2 * i + 1] = (float)(c1 * phi[i]);
   }
@@ -282,28 +290,77 @@ __global__ void k_encode(int64_t N, const float* __restrict__ F, const float* __
 }
 
 // ---- one message-passing layer, forward (tensor cores) ---------------------------------------
+// Where the layer's input rows come from and where its output goes:
+//  kInH:      h_j = H[j]
+//  kInEncode: h_j = relu(W_enc F[j] + b_enc), the encoder recomputed from the two features
+//             (inference: the encoder's 256-byte rows are never written)
+//  kInParent: h_j = H[j] + U[parent[j]], the copy back of the aggregate hierarchy applied on
+//             the fly (inference)
+// Output: Hout = h + relu(z) (and M, Z when given), or with dec set the decoder on the fly,
+// o = w_dec . (h + relu(z)) + b_dec, pred = scale o (mode 0) or pred - scale o (mode 1).
+enum LayerIn { kInH = 0, kInEncode = 1, kInParent = 2 };
+
+struct LayerArgs {
+  const float* H = nullptr;          // [rows][64] (kInH, kInParent)
+  const float* F = nullptr;          // [rows][2] features (kInEncode)
+  const float* enc = nullptr;        // W_enc [64][2], b_enc [64] (kInEncode)
+  const float* U = nullptr;          // [aggregates][64] (kInParent)
+  const int32_t* parent = nullptr;   // [rows] (kInParent)
+  const int4* nparent = nullptr;     // [rows] parents of the four face-neighbour slots (kInParent)
+  float* M = nullptr;                // outputs: messages, pre-activations, hidden state
+  float* Z = nullptr;
+  float* Hout = nullptr;
+  const float* dec = nullptr;        // w_dec [64], b_dec: decode instead of writing Hout
+  double scale = 1.0;
+  int mode = 0;
+  double* pred = nullptr;
+};
+
 // Persistent over tiles of 128 rows. The block's eight warps gather the tile's rows
 // A_c = [h ; m] into the BF16 operand tile (fine layers: rows are cells, m = sum_j w_j (h_j - h)
 // over four face neighbours, nbr [N] int4 and wn [N] float4; aggregate layers: rows are
 // aggregates, m = (1/6) sum_j (h_j - h) over six slots nbr [2 N] int4 padded with the row
-// itself), 16
-// lanes a row (a float4 of features each: whole 256-byte rows per load), two rows a step,
-// warp w taking rows [16 w, 16 w + 16); the tile is in the 128-byte swizzled K-major layout
-// (h in the first slab, m in the second), so a row's stores are bank-conflict-free. Thread 0
-// issues Z = A W^T as 8 tcgen05.mma of K = 16 into 64 tensor-memory columns; after the
-// mbarrier signals completion warp w reads lanes 32 (w % 4) .. + 31 and columns
-// 32 (w / 4) .. + 31, adds the bias and stages Z in shared memory (over the consumed A tile);
-// the warps then write Z (training) and H_out = H + relu(Z) row by row, coalesced. A wait
-// that runs out sets bit 2 of *err and the block leaves.
-template <bool kCoarse>
+// itself), 16 lanes a row (a float4 of features each: whole 256-byte rows per load), two
+// rows a step, warp w taking rows [16 w, 16 w + 16); the tile is in the 128-byte swizzled
+// K-major layout (h in the first slab, m in the second), so a row's stores are
+// bank-conflict-free. Thread 0 issues Z = A W^T as 8 tcgen05.mma of K = 16 into 64
+// tensor-memory columns; after the mbarrier signals completion warp w reads lanes
+// 32 (w % 4) .. + 31 and columns 32 (w / 4) .. + 31, adds the bias and stages Z in shared
+// memory (over the consumed A tile); the warps then write Z (training) and H_out = H + relu(Z)
+// row by row, coalesced, or decode the rows. A wait that runs out sets bit 2 of *err and the
+// block leaves.
+// es: the encoder in shared memory, [w_0 of the 64 features][w_1][b] (kInEncode)
+template <int kSrc>
+__device__ __forceinline__ float4 layer_row(const LayerArgs& a, int64_t j, int q, const float* es, int32_t pj = -1) {
+  if constexpr (kSrc == kInEncode) {
+    const float2 f = *reinterpret_cast<const float2*>(a.F + 2 * j);
+    const float4 w0 = *reinterpret_cast<const float4*>(es + 4 * q);
+    const float4 w1 = *reinterpret_cast<const float4*>(es + kHid + 4 * q);
+    const float4 b = *reinterpret_cast<const float4*>(es + 2 * kHid + 4 * q);
+    return make_float4(fmaxf(w0.x * f.x + w1.x * f.y + b.x, 0.0f), fmaxf(w0.y * f.x + w1.y * f.y + b.y, 0.0f),
+                       fmaxf(w0.z * f.x + w1.z * f.y + b.z, 0.0f), fmaxf(w0.w * f.x + w1.w * f.y + b.w, 0.0f));
+  } else if constexpr (kSrc == kInParent) {
+    const float4 h = ld4(a.H + j * kHid + 4 * q);
+    const float4 u = ld4(a.U + (int64_t)(pj >= 0 ? pj : a.parent[j]) * kHid + 4 * q);
+    return make_float4(h.x + u.x, h.y + u.y, h.z + u.z, h.w + u.w);
+  } else {
+    return ld4(a.H + j * kHid + 4 * q);
+  }
+}
+
+// (ptxas holds these at 64 registers a thread: four blocks an SM)
+template <bool kCoarse, int kSrc>
 __global__ void __launch_bounds__(kTileThreads)
-k_layer_fwd(int64_t N, const float* __restrict__ H, const int4* __restrict__ nbr, const float4* __restrict__ wn,
-            const __nv_bfloat16* __restrict__ Wg, const float* __restrict__ bias, float* __restrict__ Mout,
-            float* __restrict__ Zout, float* __restrict__ Hout, int* __restrict__ err) {
+k_layer_fwd(int64_t N, LayerArgs a, const int4* __restrict__ nbr, const float4* __restrict__ wn,
+            const __nv_bfloat16* __restrict__ Wg, const float* __restrict__ bias, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
   __shared__ float bs[kHid];
+  __shared__ float ds[kHid + 1];
+  __shared__ __align__(16) float es[3 * kHid];
+  __shared__ int4 snbr[2 * kTile];              // the tile's neighbour lists (fine: + the neighbours' parents)
+  __shared__ int32_t sparent[kTile];             // the tile's rows' parents (kInParent)
   __shared__ int s_fail;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   unsigned char* As = smem;
@@ -316,6 +373,12 @@ k_layer_fwd(int64_t N, const float* __restrict__ H, const int4* __restrict__ nbr
         *reinterpret_cast<const uint4*>(Wg + r * kIn + kc * 8);
   }
   if (t < kHid) bs[t] = bias[t];
+  if (a.dec && t <= kHid) ds[t] = a.dec[t];
+  if (kSrc == kInEncode && t < kHid) {
+    es[t] = a.enc[2 * t];
+    es[kHid + t] = a.enc[2 * t + 1];
+    es[2 * kHid + t] = a.enc[2 * kHid + t];
+  }
   if (t == 0) {
     s_fail = 0;
     mbar_init(&mbar, 1);
@@ -333,34 +396,51 @@ k_layer_fwd(int64_t N, const float* __restrict__ H, const int4* __restrict__ nbr
   const int64_t ntiles = (N + kTile - 1) / kTile;
   uint32_t phase = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // the tile's neighbour lists (and parents) into shared memory in one coalesced pass, so
+    // that each gather below waits on one global load (the rows) instead of an index first
+    {
+      const int64_t r0 = tile * kTile;
+      if constexpr (kCoarse) {
+        if (r0 + t / 2 < N) snbr[t] = nbr[2 * r0 + t];
+      } else if (t < kTile) {
+        if (r0 + t < N) snbr[t] = nbr[r0 + t];
+      } else if constexpr (kSrc == kInParent) {
+        if (r0 + t - kTile < N) {
+          snbr[t] = a.nparent[r0 + t - kTile];
+          sparent[t - kTile] = a.parent[r0 + t - kTile];
+        }
+      }
+    }
+    __syncthreads();
 #pragma unroll 4
     for (int st = 0; st < 8; ++st) {
       const int r = 16 * warp + 2 * st + (lane >> 4);
       const int64_t cr = tile * kTile + r;
       float4 h = make_float4(0.f, 0.f, 0.f, 0.f), m = h;
       if (cr < N) {
-        h = ld4(H + cr * kHid + 4 * q);
+        h = layer_row<kSrc>(a, cr, q, es, kSrc == kInParent ? sparent[r] : -1);
         if constexpr (kCoarse) {
-          const int4 na = nbr[2 * cr], nb = nbr[2 * cr + 1];
+          const int4 na = snbr[2 * r], nb = snbr[2 * r + 1];
           const int ns[6] = {na.x, na.y, na.z, na.w, nb.x, nb.y};
 #pragma unroll
           for (int j = 0; j < 6; ++j) {
-            const float4 g = ld4(H + (int64_t)ns[j] * kHid + 4 * q);
+            const float4 g = layer_row<kSrc>(a, ns[j], q, es);
             m.x += g.x - h.x; m.y += g.y - h.y; m.z += g.z - h.z; m.w += g.w - h.w;
           }
           const float sixth = 1.0f / 6.0f;
           m.x *= sixth; m.y *= sixth; m.z *= sixth; m.w *= sixth;
         } else {
-          const int4 nb = nbr[cr];
+          const int4 nb = snbr[r];
           const float4 w4 = wn[cr];
-          const float4 g0 = ld4(H + (int64_t)nb.x * kHid + 4 * q), g1 = ld4(H + (int64_t)nb.y * kHid + 4 * q),
-                       g2 = ld4(H + (int64_t)nb.z * kHid + 4 * q), g3 = ld4(H + (int64_t)nb.w * kHid + 4 * q);
+          const int4 np = kSrc == kInParent ? snbr[kTile + r] : make_int4(-1, -1, -1, -1);
+          const float4 g0 = layer_row<kSrc>(a, nb.x, q, es, np.x), g1 = layer_row<kSrc>(a, nb.y, q, es, np.y),
+                       g2 = layer_row<kSrc>(a, nb.z, q, es, np.z), g3 = layer_row<kSrc>(a, nb.w, q, es, np.w);
           m.x = w4.x * (g0.x - h.x) + w4.y * (g1.x - h.x) + w4.z * (g2.x - h.x) + w4.w * (g3.x - h.x);
           m.y = w4.x * (g0.y - h.y) + w4.y * (g1.y - h.y) + w4.z * (g2.y - h.y) + w4.w * (g3.y - h.y);
           m.z = w4.x * (g0.z - h.z) + w4.y * (g1.z - h.z) + w4.z * (g2.z - h.z) + w4.w * (g3.z - h.z);
           m.w = w4.x * (g0.w - h.w) + w4.y * (g1.w - h.w) + w4.z * (g2.w - h.w) + w4.w * (g3.w - h.w);
         }
-        if (Mout) st4(Mout + cr * kHid + 4 * q, m);
+        if (a.M) st4(a.M + cr * kHid + 4 * q, m);
       }
       st_bf16x4(As + sw_off(r, 4 * q, kTile), h);
       st_bf16x4(As + sw_off(r, kHid + 4 * q, kTile), m);
@@ -396,12 +476,26 @@ k_layer_fwd(int64_t N, const float* __restrict__ H, const int4* __restrict__ nbr
     for (int st = 0; st < 8; ++st) {
       const int r = 16 * warp + 2 * st + (lane >> 4);
       const int64_t cr = tile * kTile + r;
+      float4 ho = make_float4(0.f, 0.f, 0.f, 0.f);
       if (cr < N) {
         const float4 zz = *reinterpret_cast<const float4*>(stage_at<16>(S, r, q));
-        if (Zout) st4(Zout + cr * kHid + 4 * q, zz);
-        const float4 hv = ld4(H + cr * kHid + 4 * q);
-        st4(Hout + cr * kHid + 4 * q, make_float4(hv.x + fmaxf(zz.x, 0.0f), hv.y + fmaxf(zz.y, 0.0f),
-                                                  hv.z + fmaxf(zz.z, 0.0f), hv.w + fmaxf(zz.w, 0.0f)));
+        if (a.Z) st4(a.Z + cr * kHid + 4 * q, zz);
+        const float4 hv = layer_row<kSrc>(a, cr, q, es, kSrc == kInParent ? sparent[r] : -1);
+        ho = make_float4(hv.x + fmaxf(zz.x, 0.0f), hv.y + fmaxf(zz.y, 0.0f), hv.z + fmaxf(zz.z, 0.0f),
+                         hv.w + fmaxf(zz.w, 0.0f));
+        if (!a.dec) st4(a.Hout + cr * kHid + 4 * q, ho);
+      }
+      if (a.dec) {                    // uniform over the block: every lane takes part
+        float o = ds[4 * q] * ho.x + ds[4 * q + 1] * ho.y + ds[4 * q + 2] * ho.z + ds[4 * q + 3] * ho.w;
+        o += __shfl_xor_sync(0xffffffffu, o, 8);
+        o += __shfl_xor_sync(0xffffffffu, o, 4);
+        o += __shfl_xor_sync(0xffffffffu, o, 2);
+        o += __shfl_xor_sync(0xffffffffu, o, 1);
+        if (q == 0 && cr < N) {
+          // separately rounded product and difference: equal outputs cancel exactly
+          const double v = __dmul_rn(a.scale, (double)(o + ds[kHid]));
+          a.pred[cr] = a.mode == 0 ? v : __dsub_rn(a.pred[cr], v);
+        }
       }
     }
     tc_fence_before();
@@ -414,28 +508,6 @@ k_layer_fwd(int64_t N, const float* __restrict__ H, const int4* __restrict__ nbr
   __syncthreads();
   tc_fence_after();
   if (warp == 0) tmem_dealloc(tmem, kHid);
-}
-
-// ---- decoder: out = w_dec . h + b_dec ----------------------------------------------------------
-// mode 0: pred = scale out; mode 1: pred -= scale out (second evaluation, f0 = 0)
-__global__ void k_decode(int64_t N, const float* __restrict__ H, const float* __restrict__ theta,
-                         double scale, int mode, double* __restrict__ pred) {
-  __shared__ float w[kHid + 1];
-  for (int k = threadIdx.x; k <= kHid; k += blockDim.x) w[k] = theta[kOffWdec + k];
-  __syncthreads();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    const float4* h = reinterpret_cast<const float4*>(H + i * kHid);
-    float o = w[kHid];
-#pragma unroll
-    for (int q = 0; q < kHid / 4; ++q) {
-      const float4 v = h[q];
-      o += w[4 * q] * v.x + w[4 * q + 1] * v.y + w[4 * q + 2] * v.z + w[4 * q + 3] * v.w;
-    }
-    // separately rounded product and difference: equal outputs cancel exactly
-    const double v = __dmul_rn(scale, (double)o);
-    if (mode == 0) pred[i] = v;
-    else pred[i] = __dsub_rn(pred[i], v);
-  }
 }
 
 // Training head: pred = N(f) - N(f0 = 0) from the two last hidden states (b_dec cancels),
@@ -737,9 +809,21 @@ __global__ void k_msg_add(int64_t N, const float* __restrict__ Gm, const int4* _
 }
 
 // ---- aggregate hierarchy: mean over aggregates, copy back ----------------------------------
+// nparent[i][s] = parent[nbr[i][s]]: the level-1 aggregates of a cell's four neighbour slots
+__global__ void k_neighbour_parents(int64_t n, const int4* __restrict__ nbr, const int32_t* __restrict__ parent,
+                                    int4* __restrict__ nparent) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int4 b = nbr[i];
+    nparent[i] = make_int4(parent[b.x], parent[b.y], parent[b.z], parent[b.w]);
+  }
+}
+
+
 // out[a] = s_a sum over the nodes below of aggregate a (child_ptr / child_idx, ascending) of
 // in[child], s_a = inv_count[a] (the mean) or 1 (inv_count null: the adjoint of the copy
-// back); 16 lanes a row, a float4 of features each
+// back); 16 lanes a row, a float4 of features each. The first kChildBatch child indices are
+// read before any child's row, so those rows' loads are in flight together.
+constexpr int kChildBatch = 8;
 __global__ void k_child_sum(int64_t n, const int32_t* __restrict__ child_ptr, const int32_t* __restrict__ child_idx,
                             const float* __restrict__ in, const float* __restrict__ inv_count,
                             float* __restrict__ out) {
@@ -748,10 +832,19 @@ __global__ void k_child_sum(int64_t n, const int32_t* __restrict__ child_ptr, co
   const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 4;
   for (int64_t a = row0; a < n; a += stride) {
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int32_t e = child_ptr[a + 1];
-    for (int32_t k = child_ptr[a]; k < e; ++k) {
-      const float4 v = ld4(in + (int64_t)child_idx[k] * kHid + 4 * q);
-      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    const int32_t b = child_ptr[a], e = child_ptr[a + 1];
+    for (int32_t k0 = b; k0 < e; k0 += kChildBatch) {
+      int32_t c[kChildBatch];
+#pragma unroll
+      for (int j = 0; j < kChildBatch; ++j) c[j] = k0 + j < e ? child_idx[k0 + j] : -1;
+      float4 v[kChildBatch];
+#pragma unroll
+      for (int j = 0; j < kChildBatch; ++j)
+        v[j] = c[j] >= 0 ? ld4(in + (int64_t)c[j] * kHid + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < kChildBatch; ++j) {     // in child order
+        acc.x += v[j].x; acc.y += v[j].y; acc.z += v[j].z; acc.w += v[j].w;
+      }
     }
     if (inv_count) {
       const float s = inv_count[a];
@@ -762,18 +855,35 @@ __global__ void k_child_sum(int64_t n, const int32_t* __restrict__ child_ptr, co
 }
 
 // out[i] = a[i] + s_p b[p], p = parent[i], s_p = inv_count[p] or 1 (inv_count null): the copy
-// back of the way up, and the adjoint of the mean; out may be a (same row, same thread)
+// back of the way up, and the adjoint of the mean; out may be a (same row, same thread).
+// 16 lanes a row; each thread takes kParentRows rows, their loads issued together.
+constexpr int kParentRows = 4;
 __global__ void k_add_parent(int64_t n, const float* a, const float* __restrict__ b,
                              const int32_t* __restrict__ parent, const float* __restrict__ inv_count,
                              float* out) {
   const int q = threadIdx.x & 15;
-  const int64_t row0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 4;
-  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 4;
-  for (int64_t i = row0; i < n; i += stride) {
-    const int32_t p = parent[i];
-    const float s = inv_count ? inv_count[p] : 1.0f;
-    const float4 x = ld4(a + i * kHid + 4 * q), y = ld4(b + (int64_t)p * kHid + 4 * q);
-    st4(out + i * kHid + 4 * q, make_float4(x.x + s * y.x, x.y + s * y.y, x.z + s * y.z, x.w + s * y.w));
+  const int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 4;   // row group
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) >> 4;
+  for (int64_t i0 = g; i0 < n; i0 += ngroups * kParentRows) {
+    int32_t p[kParentRows];
+    float4 x[kParentRows], y[kParentRows];
+#pragma unroll
+    for (int j = 0; j < kParentRows; ++j) {
+      const int64_t i = i0 + j * ngroups;
+      p[j] = i < n ? parent[i] : -1;
+      x[j] = i < n ? ld4(a + i * kHid + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < kParentRows; ++j)
+      y[j] = p[j] >= 0 ? ld4(b + (int64_t)p[j] * kHid + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < kParentRows; ++j) {
+      const int64_t i = i0 + j * ngroups;
+      if (i >= n) continue;
+      const float sc = inv_count ? inv_count[p[j]] : 1.0f;
+      st4(out + i * kHid + 4 * q, make_float4(x[j].x + sc * y[j].x, x[j].y + sc * y[j].y, x[j].z + sc * y[j].z,
+                                             x[j].w + sc * y[j].w));
+    }
   }
 }
 
@@ -1054,15 +1164,21 @@ unsigned bwd_grid(int64_t rows) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + kTile - 1) / kTile, kGradBlocks));
 }
 unsigned row16_grid(int64_t rows) { return grid_n(rows * 16); }
+// k_add_parent: kParentRows rows a 16-lane group, about eight 256-thread blocks an SM at most
+unsigned parent_grid(const MpnnNet* n, int64_t rows) {
+  const int64_t groups = (rows + kParentRows - 1) / kParentRows;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((groups * 16 + 255) / 256, (int64_t)n->m->num_sms * 8));
+}
 
 // dynamic shared memory above 48 KB must be enabled per kernel (current device)
 cudaError_t layer_kernels_setup() {
-  cudaError_t e = cudaFuncSetAttribute(k_layer_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_layer_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_layer_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
-  return e;
+  const void* fwd[] = {(const void*)k_layer_fwd<false, kInH>, (const void*)k_layer_fwd<true, kInH>,
+                       (const void*)k_layer_fwd<false, kInEncode>, (const void*)k_layer_fwd<false, kInParent>};
+  for (const void* f : fwd) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaFuncSetAttribute(k_layer_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
 }
 
 // level-local views of the hierarchy arrays
@@ -1075,84 +1191,122 @@ const int4* lev_nbr(const MpnnNet* n, int k) {
 }
 float* rows_at(float* base, const MpnnNet* n, int k) { return base ? base + (size_t)n->lev_off[k] * kHid : nullptr; }
 
-// result buffer of an inference evaluation
-float* infer_out(MpnnNet* n) { return n->n_lev > 0 ? n->H[0][0] : n->H[0][1]; }
+// one forward layer launch over ``rows`` rows (fine: face neighbours and weights; coarse:
+// the level's aggregate neighbours)
+template <bool kCoarse, int kSrc>
+void launch_layer(MpnnNet* n, int l, int64_t rows, const LayerArgs& a, const int4* nb, cudaStream_t s) {
+  const __nv_bfloat16* W = n->wbf + (size_t)l * kHid * kIn;
+  const float* b = n->theta + kOffLayer0 + l * kLayerSize + kHid * kIn;
+  const float4* wn = kCoarse ? nullptr : reinterpret_cast<const float4*>(n->wn);
+  k_layer_fwd<kCoarse, kSrc><<<fwd_grid(n, rows), kTileThreads, kFwdSmem, s>>>(rows, a, nb, wn, W, b, n->m->d_status);
+  count_launch();
+}
 
-// One evaluation of the network. train: activation set ``set`` keeps every layer (hidden
-// states H[set][0..3], aggregate hops Hc/Mc/Zc[set]); otherwise set 0's buffers without the
-// messages and pre-activations, the fine hidden states ping-ponging in H[0][0..1] (result
-// in infer_out). zero_charge: f0 = 0.
-cudaError_t forward(MpnnNet* n, int set, const double* dq, const double* phi, bool train,
-                    bool zero_charge, cudaStream_t s) {
-  fvgb_mesh m = n->m;
-  const int64_t N = n->N;
-  constexpr double kEoverEps0 = 1.602176634e-19 / 8.8541878128e-12;
-  float* F = n->F[train ? set : 0];
-  float* h0 = n->H[train ? set : 0][0];
-  float* h1 = n->H[train ? set : 0][1];
-  // inference: multilevel h2 = h1 + ... in place, h3 over h0; local h2 over h0, h3 over h1
-  float* h2 = train ? n->H[set][2] : (n->n_lev > 0 ? h1 : n->H[0][0]);
-  float* h3 = train ? n->H[set][3] : infer_out(n);
-  k_features<<<grid_n(N), 256, 0, s>>>(N, dq, phi, m->g64.vol, kEoverEps0 / (n->V * n->s0),
-                                       1.0 / (n->V * n->s1), zero_charge ? 1 : 0, F);
-  k_encode<<<grid_n(N * kHid), 256, 0, s>>>(N, F, n->theta, train ? n->Z0[set] : nullptr, h0);
-  count_launch(2);
-  const int4* nbr = reinterpret_cast<const int4*>(m->g64.bc[n->bcset].at_nbr);
-  const float4* wn = reinterpret_cast<const float4*>(n->wn);
-  auto layer = [&](int l, const float* Hin, float* Mout, float* Zout, float* Hout, bool coarse, int64_t rows,
-                   const int4* nb) {
-    const __nv_bfloat16* W = n->wbf + (size_t)l * kHid * kIn;
-    const float* b = n->theta + kOffLayer0 + l * kLayerSize + kHid * kIn;
-    if (coarse)
-      k_layer_fwd<true><<<fwd_grid(n, rows), kTileThreads, kFwdSmem, s>>>(rows, Hin, nb, nullptr, W, b, Mout, Zout,
-                                                                           Hout, m->d_status);
-    else
-      k_layer_fwd<false><<<fwd_grid(n, rows), kTileThreads, kFwdSmem, s>>>(rows, Hin, nb, wn, W, b, Mout, Zout,
-                                                                            Hout, m->d_status);
-    count_launch();
-  };
-  layer(0, h0, train ? n->M[set][0] : nullptr, train ? n->Z[set][0] : nullptr, h1, false, N, nbr);
-  if (n->n_lev == 0) {
-    layer(1, h1, train ? n->M[set][1] : nullptr, train ? n->Z[set][1] : nullptr, h2, false, N, nbr);
-    layer(2, h2, train ? n->M[set][2] : nullptr, train ? n->Z[set][2] : nullptr, h3, false, N, nbr);
-    return cudaGetLastError();
-  }
-  // down the aggregate levels: mean of the level below, then kHops middle layers
-  const int cs = train ? set : 0;
+LayerArgs hidden_io(const float* H, float* M, float* Z, float* Hout) {
+  LayerArgs a;
+  a.H = H;
+  a.M = M;
+  a.Z = Z;
+  a.Hout = Hout;
+  return a;
+}
+
+// the aggregate levels of one evaluation: down (mean of the level below, then kHops middle
+// layers, keeping messages and pre-activations when M / Z are given), then up to level 0:
+// every level's output adds its aggregate's (the cells' copy back is left to the caller)
+void levels_forward(MpnnNet* n, const float* h1, float* const* Hc, float* const* Mc, float* const* Zc,
+                    cudaStream_t s) {
   for (int k = 0; k < n->n_lev; ++k) {
     const int64_t nk = n->lev_n[k];
-    const float* below = k == 0 ? h1 : rows_at(n->Hc[cs][kHops], n, k - 1);
+    const float* below = k == 0 ? h1 : rows_at(Hc[kHops], n, k - 1);
     k_child_sum<<<row16_grid(nk), 256, 0, s>>>(nk, lev_child_ptr(n, k), lev_child_idx(n, k), below, lev_inv(n, k),
-                                               rows_at(n->Hc[cs][0], n, k));
+                                               rows_at(Hc[0], n, k));
     count_launch();
     for (int j = 0; j < kHops; ++j)
-      layer(1, rows_at(n->Hc[cs][j], n, k), train ? rows_at(n->Mc[set][j], n, k) : nullptr,
-            train ? rows_at(n->Zc[set][j], n, k) : nullptr, rows_at(n->Hc[cs][j + 1], n, k), true, nk, lev_nbr(n, k));
+      launch_layer<true, kInH>(n, 1, nk,
+                               hidden_io(rows_at(Hc[j], n, k), Mc ? rows_at(Mc[j], n, k) : nullptr,
+                                         Zc ? rows_at(Zc[j], n, k) : nullptr, rows_at(Hc[j + 1], n, k)),
+                               lev_nbr(n, k), s);
   }
-  // back up: every level adds its aggregate's output, down to the cells
   for (int k = n->n_lev - 1; k >= 1; --k) {
-    float* up = rows_at(n->Hc[cs][kHops], n, k - 1);
-    k_add_parent<<<row16_grid(n->lev_n[k - 1]), 256, 0, s>>>(n->lev_n[k - 1], up, rows_at(n->Hc[cs][kHops], n, k),
+    float* up = rows_at(Hc[kHops], n, k - 1);
+    k_add_parent<<<parent_grid(n, n->lev_n[k - 1]), 256, 0, s>>>(n->lev_n[k - 1], up, rows_at(Hc[kHops], n, k),
                                                             lev_parent(n, k), nullptr, up);
     count_launch();
   }
-  k_add_parent<<<row16_grid(N), 256, 0, s>>>(N, h1, rows_at(n->Hc[cs][kHops], n, 0), lev_parent(n, 0), nullptr, h2);
+}
+
+// One training evaluation of the network into activation set ``set`` (every layer's input,
+// messages and pre-activations kept for the backward: H[set][0..3], Hc/Mc/Zc[set]).
+// zero_charge: f0 = 0.
+cudaError_t forward(MpnnNet* n, int set, const double* dq, const double* phi, bool zero_charge, cudaStream_t s) {
+  fvgb_mesh m = n->m;
+  const int64_t N = n->N;
+  constexpr double kEoverEps0 = 1.602176634e-19 / 8.8541878128e-12;
+  float** H = n->H[set];
+  k_features<<<grid_n(N), 256, 0, s>>>(N, dq, phi, n->hcell, kEoverEps0 / (n->V * n->s0),
+                                       1.0 / (n->V * n->s1), zero_charge ? 1 : 0, n->F[set]);
+  k_encode<<<grid_n(N * kHid), 256, 0, s>>>(N, n->F[set], n->theta, n->Z0[set], H[0]);
+  count_launch(2);
+  const int4* nbr = reinterpret_cast<const int4*>(m->g64.bc[n->bcset].at_nbr);
+  launch_layer<false, kInH>(n, 0, N, hidden_io(H[0], n->M[set][0], n->Z[set][0], H[1]), nbr, s);
+  if (n->n_lev == 0) {
+    launch_layer<false, kInH>(n, 1, N, hidden_io(H[1], n->M[set][1], n->Z[set][1], H[2]), nbr, s);
+  } else {
+    levels_forward(n, H[1], n->Hc[set], n->Mc[set], n->Zc[set], s);
+    k_add_parent<<<parent_grid(n, N), 256, 0, s>>>(N, H[1], rows_at(n->Hc[set][kHops], n, 0), lev_parent(n, 0), nullptr,
+                                               H[2]);
+    count_launch();
+  }
+  launch_layer<false, kInH>(n, 2, N, hidden_io(H[2], n->M[set][2], n->Z[set][2], H[3]), nbr, s);
+  return cudaGetLastError();
+}
+
+// One inference evaluation, decoded into pred (mode 0: pred = V s2 N(f); mode 1: pred -=
+// V s2 N(f)). The encoder runs inside layer 0's gathers, the cells' copy back of the
+// hierarchy inside layer 2's, and the decoder in layer 2's epilogue: the cells' hidden
+// states are written once (h1; h2 too for the local architecture).
+cudaError_t forward_infer(MpnnNet* n, const double* dq, const double* phi, bool zero_charge, double* pred,
+                          int mode, cudaStream_t s) {
+  fvgb_mesh m = n->m;
+  const int64_t N = n->N;
+  constexpr double kEoverEps0 = 1.602176634e-19 / 8.8541878128e-12;
+  k_features<<<grid_n(N), 256, 0, s>>>(N, dq, phi, n->hcell, kEoverEps0 / (n->V * n->s0),
+                                       1.0 / (n->V * n->s1), zero_charge ? 1 : 0, n->F[0]);
   count_launch();
-  layer(2, h2, train ? n->M[set][2] : nullptr, train ? n->Z[set][2] : nullptr, h3, false, N, nbr);
+  const int4* nbr = reinterpret_cast<const int4*>(m->g64.bc[n->bcset].at_nbr);
+  float* h1 = n->H[0][1];
+  LayerArgs a0;
+  a0.F = n->F[0];
+  a0.enc = n->theta + kOffWenc;
+  a0.Hout = h1;
+  launch_layer<false, kInEncode>(n, 0, N, a0, nbr, s);
+  LayerArgs a2;
+  a2.dec = n->theta + kOffWdec;
+  a2.scale = n->V * n->s2;
+  a2.mode = mode;
+  a2.pred = pred;
+  if (n->n_lev == 0) {
+    float* h2 = n->H[0][0];
+    launch_layer<false, kInH>(n, 1, N, hidden_io(h1, nullptr, nullptr, h2), nbr, s);
+    a2.H = h2;
+    launch_layer<false, kInH>(n, 2, N, a2, nbr, s);
+  } else {
+    levels_forward(n, h1, n->Hc[0], nullptr, nullptr, s);
+    a2.H = h1;
+    a2.U = rows_at(n->Hc[0][kHops], n, 0);
+    a2.parent = lev_parent(n, 0);
+    a2.nparent = reinterpret_cast<const int4*>(n->nparent);
+    launch_layer<false, kInParent>(n, 2, N, a2, nbr, s);
+  }
   return cudaGetLastError();
 }
 
 // prediction dphi = V s2 (N(f) - N(f0 = 0))
 cudaError_t predict(MpnnNet* n, const double* dq, const double* phi, double* dphi, cudaStream_t s) {
   cudaError_t e;
-  const double scale = n->V * n->s2;
-  const float* last = infer_out(n);
-  if ((e = forward(n, 0, dq, phi, false, false, s))) return e;
-  k_decode<<<grid_n(n->N), 256, 0, s>>>(n->N, last, n->theta, scale, 0, dphi);
-  if ((e = forward(n, 0, dq, phi, false, true, s))) return e;
-  k_decode<<<grid_n(n->N), 256, 0, s>>>(n->N, last, n->theta, scale, 1, dphi);
-  count_launch(2);
-  return cudaGetLastError();
+  if ((e = forward_infer(n, dq, phi, false, dphi, 0, s))) return e;
+  return forward_infer(n, dq, phi, true, dphi, 1, s);
 }
 
 // backward of sum_i dout_i sign N_set(f)_i through the layers, the hierarchy and the encoder
@@ -1206,7 +1360,7 @@ void backward_set(MpnnNet* n, int set, float sign, int row0, cudaStream_t s) {
     }
     float* down = k > 0 ? rows_at(n->dC, n, k - 1) : X;
     const int64_t nb = k > 0 ? n->lev_n[k - 1] : N;
-    k_add_parent<<<row16_grid(nb), 256, 0, s>>>(nb, down, cur, lev_parent(n, k), lev_inv(n, k), down);
+    k_add_parent<<<parent_grid(n, nb), 256, 0, s>>>(nb, down, cur, lev_parent(n, k), lev_inv(n, k), down);
     count_launch();
   }
   // layer 0: d h1 (dHb) -> d h0 (dH)
@@ -1219,8 +1373,8 @@ void backward_set(MpnnNet* n, int set, float sign, int row0, cudaStream_t s) {
 cudaError_t loss_grad(MpnnNet* n, const double* dq, const double* phi, const double* target, cudaStream_t s) {
   cudaError_t e;
   if ((e = alloc_train(n))) return e;
-  if ((e = forward(n, 0, dq, phi, true, false, s))) return e;
-  if ((e = forward(n, 1, dq, phi, true, true, s))) return e;
+  if ((e = forward(n, 0, dq, phi, false, s))) return e;
+  if ((e = forward(n, 1, dq, phi, true, s))) return e;
   const int64_t N = n->N;
   const int G = kGradBlocks;
   if ((e = cudaMemsetAsync(n->part, 0, (size_t)2 * G * kNParams * sizeof(float), s))) return e;
@@ -1268,6 +1422,9 @@ fvgb_status fvgb_mpnn_create(fvgb_mesh m, int32_t bcset, int32_t multilevel, fvg
   if ((e = nalloc(n, &n->wbf, (size_t)kLayers * kHid * kIn))) return fail("allocation");
   if ((e = nalloc(n, &n->wn, (size_t)n->N * 4))) return fail("allocation");
   if ((e = nalloc(n, &n->F[0], (size_t)n->N * 2))) return fail("allocation");
+  if ((e = nalloc(n, &n->hcell, (size_t)n->N))) return fail("allocation");
+  k_cell_size<<<grid_n(n->N), 256>>>(n->N, m->g64.vol, n->hcell);
+  count_launch();
   if ((e = nalloc(n, &n->H[0][0], NH))) return fail("allocation");
   if ((e = nalloc(n, &n->H[0][1], NH))) return fail("allocation");
   if (multilevel) {
@@ -1279,6 +1436,12 @@ fvgb_status fvgb_mpnn_create(fvgb_mesh m, int32_t bcset, int32_t multilevel, fvg
   }
   for (int j = 0; j <= kHops && n->n_lev > 0; ++j)
     if ((e = nalloc(n, &n->Hc[0][j], (size_t)n->n_coarse * kHid))) return fail("allocation");
+  if (n->n_lev > 0) {
+    if ((e = nalloc(n, &n->nparent, (size_t)4 * n->N))) return fail("allocation");
+    k_neighbour_parents<<<grid_n(n->N), 256>>>(n->N, reinterpret_cast<const int4*>(m->g64.bc[bcset].at_nbr),
+                                               n->parent, reinterpret_cast<int4*>(n->nparent));
+    count_launch();
+  }
   if ((e = nalloc(n, &n->dloss, 2))) return fail("allocation");
   if ((e = cudaMallocHost((void**)&n->hloss, sizeof(double)))) return fail("pinned allocation");
   if ((e = cudaMemset(n->theta, 0, kNParams * sizeof(float)))) return fail("memset");

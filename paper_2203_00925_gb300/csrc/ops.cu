@@ -1072,26 +1072,39 @@ cudaError_t launch_history_pair(fvgb_mesh_s* m, int which, const double* phi, do
 // ||r0||^2, ||r1||^2 (r1 the residual of saved + pred). s = 1 where ||r1|| < ||r0||, else
 // s = <r0, A pred> / ||A pred||^2, the scale that minimises the FP64 residual
 // ||r0 - s A pred|| along the prediction; s = 0 where that is undefined. used[p] = (s > 0).
+// The start's residual follows from the two residuals already formed (A is linear):
+// r = b - A (saved + s pred) = r0 + s (r1 - r0), written over r0.
 __global__ void k_scale_start(const double* __restrict__ dots, int P, const int32_t* __restrict__ part_sc,
                               const int64_t* __restrict__ sc_begin, const double* __restrict__ saved,
                               const double* __restrict__ pred, double* __restrict__ phi, int* __restrict__ used,
-                              double* __restrict__ scale) {
-  const int p = blockIdx.x;
+                              double* __restrict__ scale, double* __restrict__ r0, const double* __restrict__ r1) {
+  const int p = blockIdx.y;              // gridDim.x blocks share each part's cell range
   const double num = dots[p], den = dots[P + p], n0 = dots[2 * P + p], n1 = dots[3 * P + p];
   double sc = n1 < n0 ? 1.0 : (den > 0.0 ? num / den : 0.0);
   if (!isfinite(sc)) sc = 0.0;
-  if (threadIdx.x == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     used[p] = sc > 0.0 ? 1 : 0;
     scale[p] = sc;
   }
   const int64_t lo = sc_begin[part_sc[p]], hi = sc_begin[part_sc[p + 1]];
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) phi[i] = saved[i] + sc * pred[i];
+  for (int64_t i = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < hi; i += (int64_t)gridDim.x * blockDim.x) {
+    phi[i] = saved[i] + sc * pred[i];
+    const double a = r0[i];
+    r0[i] = a + sc * (r1[i] - a);
+  }
+}
+
+// blocks per part of the per-part elementwise kernels: about four an SM in all
+dim3 part_grid(const fvgb_mesh_s* m) {
+  const int P = m->parts.n_part;
+  return dim3((unsigned)std::max(1, (4 * m->num_sms + P - 1) / P), (unsigned)P);
 }
 
 cudaError_t launch_scale_start(fvgb_mesh_s* m, const double* dots, const double* saved, const double* pred,
-                               double* phi, int* used, double* scale, cudaStream_t s) {
-  k_scale_start<<<m->parts.n_part, 256, 0, s>>>(dots, m->parts.n_part, m->parts.part_sc, m->parts.sc_begin,
-                                                saved, pred, phi, used, scale);
+                               double* phi, int* used, double* scale, double* r0, const double* r1,
+                               cudaStream_t s) {
+  k_scale_start<<<part_grid(m), 256, 0, s>>>(dots, m->parts.n_part, m->parts.part_sc, m->parts.sc_begin,
+                                             saved, pred, phi, used, scale, r0, r1);
   count_launch();
   return cudaGetLastError();
 }
