@@ -71,6 +71,43 @@ void build_sell(const std::vector<int32_t>& ptr, const std::vector<int32_t>& idx
 // Halo lists of the shared-memory gradient (see TopoDev): per tile of kGradTile rows, its
 // own rows, then every other cell met in the rows' padded node-neighbour lists (sorted);
 // lidx[pos] is the position of sidx[pos] in its row's tile list. Returns the longest list.
+// Order each lane's neighbour entries of a SELL-32 slice so that, column by column, the
+// eight lanes of a quarter warp read records in different shared-memory bank groups
+// (record k of 16 bytes sits in group k % 8; a quarter warp's 16-byte reads are served in
+// one pass when their groups differ, or when they read the same record). Greedy: per
+// column and quarter, each lane takes an entry of the least used group it still has. The
+// least-squares sum is the same set of terms in another order.
+void order_slice_for_banks(int16_t* lid, int width) {
+  thread_local std::vector<int16_t> bucket[32][8];   // reused across slices
+  for (int lane = 0; lane < 32; ++lane) {
+    for (int g = 0; g < 8; ++g) bucket[lane][g].clear();
+    for (int c = width - 1; c >= 0; --c) {            // popped from the back: original order
+      const int16_t v = lid[32 * c + lane];
+      bucket[lane][v & 7].push_back(v);
+    }
+  }
+  for (int c = 0; c < width; ++c) {
+    for (int qw = 0; qw < 4; ++qw) {
+      int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};          // distinct records read in each group
+      int first[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+      for (int lane = 8 * qw; lane < 8 * qw + 8; ++lane) {
+        int best = -1, best_cost = 1 << 30;
+        for (int g = 0; g < 8; ++g) {
+          if (bucket[lane][g].empty()) continue;
+          // a record another lane of the quarter already reads costs nothing
+          const int cost = bucket[lane][g].back() == first[g] ? 0 : cnt[g] + 1;
+          if (cost < best_cost) { best = g; best_cost = cost; }
+        }
+        const int16_t v = bucket[lane][best].back();
+        bucket[lane][best].pop_back();
+        if (first[best] < 0) first[best] = v;
+        if (best_cost > 0) cnt[best] += 1;
+        lid[32 * c + lane] = v;
+      }
+    }
+  }
+}
+
 int build_grad_tiles(int64_t N, const std::vector<int64_t>& sptr, const std::vector<int32_t>& sidx,
                      std::vector<int32_t>& tptr, std::vector<int32_t>& tidx, std::vector<int16_t>& lidx) {
   const int64_t ntile = (N + kGradTile - 1) / kGradTile;
@@ -93,8 +130,11 @@ int build_grad_tiles(int64_t N, const std::vector<int64_t>& sptr, const std::vec
       }
       std::sort(L.begin() + own, L.end());
       for (size_t k = 0; k < L.size(); ++k) pos[L[k]] = (int32_t)k;
-      if (L.size() <= 32767)
+      if (L.size() <= 32767) {
         for (int64_t q = sptr[s0]; q < sptr[s1]; ++q) lidx[q] = (int16_t)pos[sidx[q]];
+        for (int64_t sl = s0; sl < s1; ++sl)
+          order_slice_for_banks(lidx.data() + sptr[sl], (int)((sptr[sl + 1] - sptr[sl]) / 32));
+      }
       max_len = std::max(max_len, (int)L.size());
     }
   }
