@@ -19,8 +19,10 @@
 // completion is signalled through an mbarrier, and the warps read the accumulator with
 // tcgen05.ld for the fused epilogue (bias, ReLU, residual). The same kernels run the fine
 // layers (rows = cells, four face neighbours with weights) and the aggregate layers (rows =
-// aggregates, up to six neighbours of weight 1/6). Hidden states, messages and
-// pre-activations are kept in FP32. Weight gradients are per-block sums accumulated in
+// aggregates, up to six neighbours of weight 1/6). Training keeps hidden states, messages
+// and pre-activations in FP32; the inference path writes the cells' hidden states once, as
+// BF16 (the tensor-core operands are BF16 anyway), with the encoder, the hierarchy's copy
+// back and the decoder fused into the layers. Weight gradients are per-block sums accumulated in
 // tensor memory, reduced over blocks in FP64 in a fixed order (deterministic). Adam updates
 // FP32 master weights and refreshes their BF16 copies.
 #include <cuda_bf16.h>
@@ -70,6 +72,7 @@ struct fvgb_mpnn_s {
   __nv_bfloat16* wbf = nullptr;        // [3][64][128]
   float* wn = nullptr;                 // [N][4] message weights
   double* hcell = nullptr;             // [N] mu^(1/3)
+  __nv_bfloat16* Hb[2] = {};           // [N][64] BF16 hidden states of the inference path
   // aggregate hierarchy (multilevel architecture; n_lev = 0: the middle layer runs on the
   // faces): level k (0-based) has lev_n[k] nodes, rows [lev_off[k], + lev_n[k]) of the
   // coarse arrays; the nodes below it are the cells (k = 0) or level k - 1's
@@ -225,6 +228,13 @@ __device__ __forceinline__ void st_bf16x4(unsigned char* p, const float4& v) {
   *reinterpret_cast<uint2*>(p) = make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
 }
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+// four BF16 values (8 bytes) widened to FP32
+__device__ __forceinline__ float4 ld_bf16x4(const __nv_bfloat16* p) {
+  const uint2 v = *reinterpret_cast<const uint2*>(p);
+  const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&v.x);
+  const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&v.y);
+  return make_float4(__bfloat162float(a.x), __bfloat162float(a.y), __bfloat162float(b.x), __bfloat162float(b.y));
+}
 __device__ __forceinline__ void st4(float* p, const float4& v) { *reinterpret_cast<float4*>(p) = v; }
 // staging of a row-per-thread accumulator: float4 q of row r at q ^ (r % Q) (Q = float4s
 // per row), so that 32 rows writing one quad, or one row read by quads, hit distinct banks
@@ -294,22 +304,26 @@ __global__ void k_encode(int64_t N, const float* __restrict__ F, const float* __
 //  kInH:      h_j = H[j]
 //  kInEncode: h_j = relu(W_enc F[j] + b_enc), the encoder recomputed from the two features
 //             (inference: the encoder's 256-byte rows are never written)
-//  kInParent: h_j = H[j] + U[parent[j]], the copy back of the aggregate hierarchy applied on
-//             the fly (inference)
+//  kInHb:     h_j = Hb[j], a BF16 copy (inference, where the cells' hidden states are
+//             written once and read by the next layer: half the bytes)
+//  kInParentB: h_j = Hb[j] + U[parent[j]], the copy back of the aggregate hierarchy applied
+//             on the fly (inference)
 // Output: Hout = h + relu(z) (and M, Z when given), or with dec set the decoder on the fly,
 // o = w_dec . (h + relu(z)) + b_dec, pred = scale o (mode 0) or pred - scale o (mode 1).
-enum LayerIn { kInH = 0, kInEncode = 1, kInParent = 2 };
+enum LayerIn { kInH = 0, kInEncode = 1, kInHb = 2, kInParentB = 3 };
 
 struct LayerArgs {
-  const float* H = nullptr;          // [rows][64] (kInH, kInParent)
+  const float* H = nullptr;          // [rows][64] (kInH)
+  const __nv_bfloat16* Hb = nullptr; // [rows][64] BF16 (kInHb, kInParentB)
   const float* F = nullptr;          // [rows][2] features (kInEncode)
   const float* enc = nullptr;        // W_enc [64][2], b_enc [64] (kInEncode)
-  const float* U = nullptr;          // [aggregates][64] (kInParent)
-  const int32_t* parent = nullptr;   // [rows] (kInParent)
-  const int4* nparent = nullptr;     // [rows] parents of the four face-neighbour slots (kInParent)
+  const float* U = nullptr;          // [aggregates][64] (kInParentB)
+  const int32_t* parent = nullptr;   // [rows] (kInParentB)
+  const int4* nparent = nullptr;     // [rows] parents of the four face-neighbour slots (kInParentB)
   float* M = nullptr;                // outputs: messages, pre-activations, hidden state
   float* Z = nullptr;
   float* Hout = nullptr;
+  __nv_bfloat16* Houtb = nullptr;    // or the hidden state as BF16
   const float* dec = nullptr;        // w_dec [64], b_dec: decode instead of writing Hout
   double scale = 1.0;
   int mode = 0;
@@ -339,10 +353,12 @@ __device__ __forceinline__ float4 layer_row(const LayerArgs& a, int64_t j, int q
     const float4 b = *reinterpret_cast<const float4*>(es + 2 * kHid + 4 * q);
     return make_float4(fmaxf(w0.x * f.x + w1.x * f.y + b.x, 0.0f), fmaxf(w0.y * f.x + w1.y * f.y + b.y, 0.0f),
                        fmaxf(w0.z * f.x + w1.z * f.y + b.z, 0.0f), fmaxf(w0.w * f.x + w1.w * f.y + b.w, 0.0f));
-  } else if constexpr (kSrc == kInParent) {
-    const float4 h = ld4(a.H + j * kHid + 4 * q);
+  } else if constexpr (kSrc == kInParentB) {
+    const float4 h = ld_bf16x4(a.Hb + j * kHid + 4 * q);
     const float4 u = ld4(a.U + (int64_t)(pj >= 0 ? pj : a.parent[j]) * kHid + 4 * q);
     return make_float4(h.x + u.x, h.y + u.y, h.z + u.z, h.w + u.w);
+  } else if constexpr (kSrc == kInHb) {
+    return ld_bf16x4(a.Hb + j * kHid + 4 * q);
   } else {
     return ld4(a.H + j * kHid + 4 * q);
   }
@@ -360,7 +376,7 @@ k_layer_fwd(int64_t N, LayerArgs a, const int4* __restrict__ nbr, const float4* 
   __shared__ float ds[kHid + 1];
   __shared__ __align__(16) float es[3 * kHid];
   __shared__ int4 snbr[2 * kTile];              // the tile's neighbour lists (fine: + the neighbours' parents)
-  __shared__ int32_t sparent[kTile];             // the tile's rows' parents (kInParent)
+  __shared__ int32_t sparent[kTile];             // the tile's rows' parents (kInParentB)
   __shared__ int s_fail;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   unsigned char* As = smem;
@@ -404,7 +420,7 @@ k_layer_fwd(int64_t N, LayerArgs a, const int4* __restrict__ nbr, const float4* 
         if (r0 + t / 2 < N) snbr[t] = nbr[2 * r0 + t];
       } else if (t < kTile) {
         if (r0 + t < N) snbr[t] = nbr[r0 + t];
-      } else if constexpr (kSrc == kInParent) {
+      } else if constexpr (kSrc == kInParentB) {
         if (r0 + t - kTile < N) {
           snbr[t] = a.nparent[r0 + t - kTile];
           sparent[t - kTile] = a.parent[r0 + t - kTile];
@@ -418,7 +434,7 @@ k_layer_fwd(int64_t N, LayerArgs a, const int4* __restrict__ nbr, const float4* 
       const int64_t cr = tile * kTile + r;
       float4 h = make_float4(0.f, 0.f, 0.f, 0.f), m = h;
       if (cr < N) {
-        h = layer_row<kSrc>(a, cr, q, es, kSrc == kInParent ? sparent[r] : -1);
+        h = layer_row<kSrc>(a, cr, q, es, kSrc == kInParentB ? sparent[r] : -1);
         if constexpr (kCoarse) {
           const int4 na = snbr[2 * r], nb = snbr[2 * r + 1];
           const int ns[6] = {na.x, na.y, na.z, na.w, nb.x, nb.y};
@@ -432,7 +448,7 @@ k_layer_fwd(int64_t N, LayerArgs a, const int4* __restrict__ nbr, const float4* 
         } else {
           const int4 nb = snbr[r];
           const float4 w4 = wn[cr];
-          const int4 np = kSrc == kInParent ? snbr[kTile + r] : make_int4(-1, -1, -1, -1);
+          const int4 np = kSrc == kInParentB ? snbr[kTile + r] : make_int4(-1, -1, -1, -1);
           const float4 g0 = layer_row<kSrc>(a, nb.x, q, es, np.x), g1 = layer_row<kSrc>(a, nb.y, q, es, np.y),
                        g2 = layer_row<kSrc>(a, nb.z, q, es, np.z), g3 = layer_row<kSrc>(a, nb.w, q, es, np.w);
           m.x = w4.x * (g0.x - h.x) + w4.y * (g1.x - h.x) + w4.z * (g2.x - h.x) + w4.w * (g3.x - h.x);
@@ -480,10 +496,13 @@ k_layer_fwd(int64_t N, LayerArgs a, const int4* __restrict__ nbr, const float4* 
       if (cr < N) {
         const float4 zz = *reinterpret_cast<const float4*>(stage_at<16>(S, r, q));
         if (a.Z) st4(a.Z + cr * kHid + 4 * q, zz);
-        const float4 hv = layer_row<kSrc>(a, cr, q, es, kSrc == kInParent ? sparent[r] : -1);
+        const float4 hv = layer_row<kSrc>(a, cr, q, es, kSrc == kInParentB ? sparent[r] : -1);
         ho = make_float4(hv.x + fmaxf(zz.x, 0.0f), hv.y + fmaxf(zz.y, 0.0f), hv.z + fmaxf(zz.z, 0.0f),
                          hv.w + fmaxf(zz.w, 0.0f));
-        if (!a.dec) st4(a.Hout + cr * kHid + 4 * q, ho);
+        if (!a.dec) {
+          if (a.Houtb) st_bf16x4(reinterpret_cast<unsigned char*>(a.Houtb + cr * kHid + 4 * q), ho);
+          else st4(a.Hout + cr * kHid + 4 * q, ho);
+        }
       }
       if (a.dec) {                    // uniform over the block: every lane takes part
         float o = ds[4 * q] * ho.x + ds[4 * q + 1] * ho.y + ds[4 * q + 2] * ho.z + ds[4 * q + 3] * ho.w;
@@ -824,8 +843,11 @@ __global__ void k_neighbour_parents(int64_t n, const int4* __restrict__ nbr, con
 // back); 16 lanes a row, a float4 of features each. The first kChildBatch child indices are
 // read before any child's row, so those rows' loads are in flight together.
 constexpr int kChildBatch = 8;
+__device__ __forceinline__ float4 ld_row4(const float* p) { return ld4(p); }
+__device__ __forceinline__ float4 ld_row4(const __nv_bfloat16* p) { return ld_bf16x4(p); }
+template <typename Tin>
 __global__ void k_child_sum(int64_t n, const int32_t* __restrict__ child_ptr, const int32_t* __restrict__ child_idx,
-                            const float* __restrict__ in, const float* __restrict__ inv_count,
+                            const Tin* __restrict__ in, const float* __restrict__ inv_count,
                             float* __restrict__ out) {
   const int q = threadIdx.x & 15;
   const int64_t row0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 4;
@@ -840,7 +862,7 @@ __global__ void k_child_sum(int64_t n, const int32_t* __restrict__ child_ptr, co
       float4 v[kChildBatch];
 #pragma unroll
       for (int j = 0; j < kChildBatch; ++j)
-        v[j] = c[j] >= 0 ? ld4(in + (int64_t)c[j] * kHid + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[j] = c[j] >= 0 ? ld_row4(in + (int64_t)c[j] * kHid + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int j = 0; j < kChildBatch; ++j) {     // in child order
         acc.x += v[j].x; acc.y += v[j].y; acc.z += v[j].z; acc.w += v[j].w;
@@ -992,7 +1014,7 @@ cudaError_t alloc_train(MpnnNet* n) {
       if ((e = nalloc(n, &n->M[set][l], NH))) return e;
       if ((e = nalloc(n, &n->Z[set][l], NH))) return e;
     }
-    for (int l = set == 0 ? 2 : 0; l <= kLayers; ++l)
+    for (int l = 0; l <= kLayers; ++l)
       if ((e = nalloc(n, &n->H[set][l], NH))) return e;
     for (int j = 0; j < kHops && n->n_lev > 0; ++j) {
       if ((e = nalloc(n, &n->Mc[set][j], CH))) return e;
@@ -1173,7 +1195,8 @@ unsigned parent_grid(const MpnnNet* n, int64_t rows) {
 // dynamic shared memory above 48 KB must be enabled per kernel (current device)
 cudaError_t layer_kernels_setup() {
   const void* fwd[] = {(const void*)k_layer_fwd<false, kInH>, (const void*)k_layer_fwd<true, kInH>,
-                       (const void*)k_layer_fwd<false, kInEncode>, (const void*)k_layer_fwd<false, kInParent>};
+                       (const void*)k_layer_fwd<false, kInEncode>, (const void*)k_layer_fwd<false, kInHb>,
+                       (const void*)k_layer_fwd<false, kInParentB>};
   for (const void* f : fwd) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
     if (e != cudaSuccess) return e;
@@ -1214,13 +1237,17 @@ LayerArgs hidden_io(const float* H, float* M, float* Z, float* Hout) {
 // the aggregate levels of one evaluation: down (mean of the level below, then kHops middle
 // layers, keeping messages and pre-activations when M / Z are given), then up to level 0:
 // every level's output adds its aggregate's (the cells' copy back is left to the caller)
-void levels_forward(MpnnNet* n, const float* h1, float* const* Hc, float* const* Mc, float* const* Zc,
-                    cudaStream_t s) {
+void levels_forward(MpnnNet* n, const float* h1, const __nv_bfloat16* h1b, float* const* Hc, float* const* Mc,
+                    float* const* Zc, cudaStream_t s) {
   for (int k = 0; k < n->n_lev; ++k) {
     const int64_t nk = n->lev_n[k];
-    const float* below = k == 0 ? h1 : rows_at(Hc[kHops], n, k - 1);
-    k_child_sum<<<row16_grid(nk), 256, 0, s>>>(nk, lev_child_ptr(n, k), lev_child_idx(n, k), below, lev_inv(n, k),
-                                               rows_at(Hc[0], n, k));
+    if (k == 0 && h1b)
+      k_child_sum<__nv_bfloat16><<<row16_grid(nk), 256, 0, s>>>(nk, lev_child_ptr(n, k), lev_child_idx(n, k), h1b,
+                                                                lev_inv(n, k), rows_at(Hc[0], n, k));
+    else
+      k_child_sum<float><<<row16_grid(nk), 256, 0, s>>>(nk, lev_child_ptr(n, k), lev_child_idx(n, k),
+                                                        k == 0 ? h1 : rows_at(Hc[kHops], n, k - 1), lev_inv(n, k),
+                                                        rows_at(Hc[0], n, k));
     count_launch();
     for (int j = 0; j < kHops; ++j)
       launch_layer<true, kInH>(n, 1, nk,
@@ -1253,7 +1280,7 @@ cudaError_t forward(MpnnNet* n, int set, const double* dq, const double* phi, bo
   if (n->n_lev == 0) {
     launch_layer<false, kInH>(n, 1, N, hidden_io(H[1], n->M[set][1], n->Z[set][1], H[2]), nbr, s);
   } else {
-    levels_forward(n, H[1], n->Hc[set], n->Mc[set], n->Zc[set], s);
+    levels_forward(n, H[1], nullptr, n->Hc[set], n->Mc[set], n->Zc[set], s);
     k_add_parent<<<parent_grid(n, N), 256, 0, s>>>(N, H[1], rows_at(n->Hc[set][kHops], n, 0), lev_parent(n, 0), nullptr,
                                                H[2]);
     count_launch();
@@ -1265,7 +1292,7 @@ cudaError_t forward(MpnnNet* n, int set, const double* dq, const double* phi, bo
 // One inference evaluation, decoded into pred (mode 0: pred = V s2 N(f); mode 1: pred -=
 // V s2 N(f)). The encoder runs inside layer 0's gathers, the cells' copy back of the
 // hierarchy inside layer 2's, and the decoder in layer 2's epilogue: the cells' hidden
-// states are written once (h1; h2 too for the local architecture).
+// states are written once, as BF16 (h1; h2 too for the local architecture).
 cudaError_t forward_infer(MpnnNet* n, const double* dq, const double* phi, bool zero_charge, double* pred,
                           int mode, cudaStream_t s) {
   fvgb_mesh m = n->m;
@@ -1275,11 +1302,11 @@ cudaError_t forward_infer(MpnnNet* n, const double* dq, const double* phi, bool 
                                        1.0 / (n->V * n->s1), zero_charge ? 1 : 0, n->F[0]);
   count_launch();
   const int4* nbr = reinterpret_cast<const int4*>(m->g64.bc[n->bcset].at_nbr);
-  float* h1 = n->H[0][1];
+  __nv_bfloat16* h1 = n->Hb[0];
   LayerArgs a0;
   a0.F = n->F[0];
   a0.enc = n->theta + kOffWenc;
-  a0.Hout = h1;
+  a0.Houtb = h1;
   launch_layer<false, kInEncode>(n, 0, N, a0, nbr, s);
   LayerArgs a2;
   a2.dec = n->theta + kOffWdec;
@@ -1287,17 +1314,19 @@ cudaError_t forward_infer(MpnnNet* n, const double* dq, const double* phi, bool 
   a2.mode = mode;
   a2.pred = pred;
   if (n->n_lev == 0) {
-    float* h2 = n->H[0][0];
-    launch_layer<false, kInH>(n, 1, N, hidden_io(h1, nullptr, nullptr, h2), nbr, s);
-    a2.H = h2;
-    launch_layer<false, kInH>(n, 2, N, a2, nbr, s);
+    LayerArgs a1;
+    a1.Hb = h1;
+    a1.Houtb = n->Hb[1];
+    launch_layer<false, kInHb>(n, 1, N, a1, nbr, s);
+    a2.Hb = n->Hb[1];
+    launch_layer<false, kInHb>(n, 2, N, a2, nbr, s);
   } else {
-    levels_forward(n, h1, n->Hc[0], nullptr, nullptr, s);
-    a2.H = h1;
+    levels_forward(n, nullptr, h1, n->Hc[0], nullptr, nullptr, s);
+    a2.Hb = h1;
     a2.U = rows_at(n->Hc[0][kHops], n, 0);
     a2.parent = lev_parent(n, 0);
     a2.nparent = reinterpret_cast<const int4*>(n->nparent);
-    launch_layer<false, kInParent>(n, 2, N, a2, nbr, s);
+    launch_layer<false, kInParentB>(n, 2, N, a2, nbr, s);
   }
   return cudaGetLastError();
 }
@@ -1340,11 +1369,11 @@ void backward_set(MpnnNet* n, int set, float sign, int row0, cudaStream_t s) {
   }
   // adjoint of the way up: the output of level k receives the sum over its nodes of theirs
   const int L = n->n_lev;
-  k_child_sum<<<row16_grid(n->lev_n[0]), 256, 0, s>>>(n->lev_n[0], lev_child_ptr(n, 0), lev_child_idx(n, 0), X,
+  k_child_sum<float><<<row16_grid(n->lev_n[0]), 256, 0, s>>>(n->lev_n[0], lev_child_ptr(n, 0), lev_child_idx(n, 0), X,
                                                       nullptr, rows_at(n->dC, n, 0));
   count_launch();
   for (int k = 1; k < L; ++k) {
-    k_child_sum<<<row16_grid(n->lev_n[k]), 256, 0, s>>>(n->lev_n[k], lev_child_ptr(n, k), lev_child_idx(n, k),
+    k_child_sum<float><<<row16_grid(n->lev_n[k]), 256, 0, s>>>(n->lev_n[k], lev_child_ptr(n, k), lev_child_idx(n, k),
                                                         rows_at(n->dC, n, k - 1), nullptr, rows_at(n->dC, n, k));
     count_launch();
   }
@@ -1423,10 +1452,10 @@ fvgb_status fvgb_mpnn_create(fvgb_mesh m, int32_t bcset, int32_t multilevel, fvg
   if ((e = nalloc(n, &n->wn, (size_t)n->N * 4))) return fail("allocation");
   if ((e = nalloc(n, &n->F[0], (size_t)n->N * 2))) return fail("allocation");
   if ((e = nalloc(n, &n->hcell, (size_t)n->N))) return fail("allocation");
+  if ((e = nalloc(n, &n->Hb[0], NH))) return fail("allocation");
+  if (!multilevel && (e = nalloc(n, &n->Hb[1], NH))) return fail("allocation");
   k_cell_size<<<grid_n(n->N), 256>>>(n->N, m->g64.vol, n->hcell);
   count_launch();
-  if ((e = nalloc(n, &n->H[0][0], NH))) return fail("allocation");
-  if ((e = nalloc(n, &n->H[0][1], NH))) return fail("allocation");
   if (multilevel) {
     std::vector<double> cen((size_t)3 * n->N);
     if ((e = cudaMemcpy(cen.data(), m->g64.cen, cen.size() * sizeof(double), cudaMemcpyDeviceToHost)))
