@@ -526,18 +526,20 @@ def gpu_arm(args, world, rank, local):
     log(f"headline {total_ms / args.steps:.2f} ms/step")
 
     # ---- roofline of the dominant kernel: the persistent CG kernel ------------------------
-    # Per CG iteration and cell: the p/q phase (ELL-4 indices 16 B, 4 coefficients, diagonal,
-    # r and its 4 neighbours as cache hits, p, q and x read and written) and the r phase (r, q
-    # read, r written): 15 w + 16 bytes; flops 9 (operator) + 12 (four updates, two dots).
-    # Per launch add the initial pass (r = rhs, zeroed p, q, x) and the first operator apply.
+    # Per CG iteration and cell: the p/q phase (ELL-4 indices 16 B, 4 coefficients of the
+    # unit-diagonal scaled operator, r and its 4 neighbours as cache hits, p, q and x read and
+    # written) and the r phase (r, q read, r written): 14 w + 16 bytes; flops 8 (operator) +
+    # 12 (four updates, two dots). Per launch add the initial pass (r = D^-1/2 rhs, zeroed p,
+    # q, x), the first operator apply and the final pass (x = D^-1/2 x): 13 w + 24 bytes and
+    # 14 flops.
     # At 6M cells the iteration's working set (~860 MB FP64) is far above L2, so both the HBM
     # and the FP64-pipe views apply; the line reports the one with the larger fraction as the
     # bound and the other beside it.
     w = 4 if mixed else 8
     its, launches = stats["cg_iterations"], max(stats["cg_launches"], 1)
     per_launch_its = its / launches
-    flops_per_launch = N * (per_launch_its * 21 + 13)
-    bytes_per_launch = N * (per_launch_its * (15 * w + 16) + 10 * w + 24)
+    flops_per_launch = N * (per_launch_its * 20 + 14)
+    bytes_per_launch = N * (per_launch_its * (14 * w + 16) + 13 * w + 24)
     avg_launch_s = stats["cg_ms"] / 1e3 / launches
     props = torch.cuda.get_device_properties(local)
     peak_tflops = props.multi_processor_count * 2 * 2 * 2.070e9 / 1e12

@@ -191,6 +191,8 @@ cudaError_t upload_geo(fvgb_mesh_s* m, const HostMesh& h, const std::vector<doub
     if ((e = dupload(m, &d.at_nbr, b.at_nbr, s))) return e;
     if ((e = dupload(m, &d.at_coef, cast<T>(b.at_coef), s))) return e;
     if ((e = dupload(m, &d.at_diag, cast<T>(b.at_diag), s))) return e;
+    if ((e = dupload(m, &d.at_scoef, cast<T>(b.at_scoef), s))) return e;
+    if ((e = dupload(m, &d.at_isd, cast<T>(b.at_isd), s))) return e;
   }
   return cudaSuccess;
 }

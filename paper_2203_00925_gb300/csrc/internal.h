@@ -33,6 +33,8 @@ struct BCDev {
   int32_t* at_nbr = nullptr; // [N][4] (unused slot: the cell itself)
   T* at_coef = nullptr;      // [N][4] (unused slot: 0)
   T* at_diag = nullptr;      // [N]
+  T* at_scoef = nullptr;     // [N][4] coefficients of D^-1/2 A_T D^-1/2 (the inner CG's operator)
+  T* at_isd = nullptr;       // [N] D^-1/2
 };
 
 // Real-valued geometry in one precision.

@@ -641,6 +641,15 @@ int build_host_mesh(int dim, int64_t n_vert, const double* xyz_in, int64_t n_cel
       }
       B.at_diag[i] = diag;
     }
+    // symmetric Jacobi scaling (a cell without any coupling keeps scale 1)
+    B.at_isd.assign(N, 1.0);
+    B.at_scoef.assign((size_t)4 * N, 0.0);
+    for (int64_t i = 0; i < N; ++i)
+      if (B.at_diag[i] > 0.0) B.at_isd[i] = 1.0 / std::sqrt(B.at_diag[i]);
+#pragma omp parallel for
+    for (int64_t i = 0; i < N; ++i)
+      for (int k = 0; k < 4; ++k)
+        B.at_scoef[i * 4 + k] = B.at_coef[i * 4 + k] * B.at_isd[i] * B.at_isd[B.at_nbr[i * 4 + k]];
   }
   return 0;
 }

@@ -21,6 +21,10 @@ struct BCSetHost {
   std::vector<int32_t> at_nbr;    // [N][4] two-point operator: neighbour (the cell itself if none)
   std::vector<double> at_coef;    // [N][4] off-diagonal coefficient c1 (0 if none)
   std::vector<double> at_diag;    // [N]
+  // the same operator scaled symmetrically to unit diagonal, D^-1/2 A_T D^-1/2, for the
+  // inner CG: at_scoef[i][k] = at_coef[i][k] / sqrt(d_i d_j), at_isd[i] = 1 / sqrt(d_i)
+  std::vector<double> at_scoef;   // [N][4]
+  std::vector<double> at_isd;     // [N]
   int n_dirichlet_faces = 0;
 };
 

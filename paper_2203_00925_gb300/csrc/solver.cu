@@ -116,10 +116,10 @@ __device__ __forceinline__ double cg_block_sum(double v, double* sh, bool many_p
 template <typename T>
 struct SolveArgs {
   int64_t N;
-  // two-point operator in T, cell-major [N][4]
+  // two-point operator scaled to unit diagonal, D^-1/2 A_T D^-1/2, in T, cell-major [N][4]
   const int32_t* at_nbr;
-  const T* at_coef;
-  const T* at_diag;
+  const T* at_scoef;
+  const T* at_isd;          // [N] D^-1/2: the CG solves for D^1/2 x from D^-1/2 r
   const double* r_in;       // [N] right-hand side (FP64 outer residual)
   T* cx;
   T* cr;
@@ -247,17 +247,22 @@ __device__ __forceinline__ T cg_phase_r(const SolveArgs<T>& a, int64_t lo, int64
   return acc;
 }
 
-// The deferred x += alpha p of the last phase 1 of a part (rows [lo, hi)).
+// The final pass on rows [lo, hi): the deferred x += alpha p of the part's last phase 1
+// (pending), then back from the scaled unknowns, x = D^-1/2 x.
 template <typename T>
-__device__ __forceinline__ void cg_phase_x(const SolveArgs<T>& a, int64_t lo, int64_t hi, T alpha) {
+__device__ __forceinline__ void cg_phase_x(const SolveArgs<T>& a, int64_t lo, int64_t hi, bool pending, T alpha) {
   T* __restrict__ X = a.cx;
   const T* __restrict__ P = a.cp;
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) X[i] = X[i] + alpha * P[i];
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const T x = pending ? X[i] + alpha * P[i] : X[i];
+    X[i] = x * __ldg(a.at_isd + i);
+  }
 }
 
 // CG phase 2 on rows [lo, hi): x += alpha p (the previous phase 1's update, with the old p),
-// p = r + beta p, q = A_T r + beta q (= A_T p); returns the thread's sum of p.q. Neighbours'
-// r are read through L2 (other blocks wrote them).
+// p = r + beta p, q = S r + beta q (= S p, S = D^-1/2 A_T D^-1/2 with unit diagonal);
+// returns the thread's sum of p.q. Neighbours' r are read through L2 (other blocks wrote
+// them).
 template <typename T>
 __device__ __forceinline__ T cg_phase_pq(const SolveArgs<T>& a, int64_t lo, int64_t hi, T beta, T alpha) {
   constexpr int U = unroll_rows<T>();
@@ -269,7 +274,7 @@ __device__ __forceinline__ T cg_phase_pq(const SolveArgs<T>& a, int64_t lo, int6
   T acc = T(0);
   const int64_t bd = blockDim.x;
   for (int64_t b = lo + threadIdx.x; b < hi; b += U * bd) {
-    T r[U], p[U], q[U], x[U], d[U], g[U][4];
+    T r[U], p[U], q[U], x[U], g[U][4];
     int4 nb[U];
     Coef4<T> c[U];
 #pragma unroll
@@ -278,8 +283,7 @@ __device__ __forceinline__ T cg_phase_pq(const SolveArgs<T>& a, int64_t lo, int6
       if (i < hi) {
         nb[u] = __ldg(NB + i);
         r[u] = R[i]; p[u] = P[i]; q[u] = Q[i]; x[u] = X[i];
-        d[u] = __ldg(a.at_diag + i);
-        c[u].load(a.at_coef, i);
+        c[u].load(a.at_scoef, i);
       }
     }
 #pragma unroll
@@ -296,7 +300,7 @@ __device__ __forceinline__ T cg_phase_pq(const SolveArgs<T>& a, int64_t lo, int6
     for (int u = 0; u < U; ++u) {
       const int64_t i = b + u * bd;
       if (i < hi) {
-        T y = d[u] * r[u];
+        T y = r[u];                     // unit diagonal
         y -= c[u].c[0] * g[u][0];
         y -= c[u].c[1] * g[u][1];
         y -= c[u].c[2] * g[u][2];
@@ -336,12 +340,12 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
   if (threadIdx.x == 0) s_status = 0;
   for (int p = threadIdx.x; p < P; p += blockDim.x) { s_inner[p] = 0; s_pend[p] = 0; }
 
-  // r = rhs on active parts (0 elsewhere), p = q = x = 0; the first p/q phase (beta = 0)
-  // then gives p = r, q = A_T r
+  // r = D^-1/2 rhs on active parts (0 elsewhere), p = q = x = 0; the first p/q phase
+  // (beta = 0) then gives p = r, q = S r
   for (int sc = sc0; sc < sc1; ++sc) {
     const bool act = a.active[a.sc_part[sc]] != 0;
     for (int64_t i = a.sc_begin[sc] + threadIdx.x; i < a.sc_begin[sc + 1]; i += blockDim.x) {
-      a.cr[i] = act ? (T)a.r_in[i] : T(0);
+      a.cr[i] = act ? (T)(a.r_in[i] * (double)__ldg(a.at_isd + i)) : T(0);
       a.cp[i] = T(0);
       a.cq[i] = T(0);
       a.cx[i] = T(0);
@@ -432,11 +436,12 @@ __global__ void __launch_bounds__(kCgThreads, kCgBlocksPerSm) k_cg(SolveArgs<T> 
     }
     __syncthreads();
   }
-  // the parts whose last phase was a phase 1: apply its deferred x += alpha p (own rows only)
+  // own rows: the deferred x += alpha p of the parts whose last phase was a phase 1, and
+  // every row back to the unscaled correction
   __syncthreads();
   for (int sc = sc0; sc < sc1; ++sc) {
     const int p = a.sc_part[sc];
-    if (s_pend[p]) cg_phase_x<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], s_alpha[p]);
+    cg_phase_x<T>(a, a.sc_begin[sc], a.sc_begin[sc + 1], s_pend[p] != 0, s_alpha[p]);
   }
   for (int p = threadIdx.x; p < P; p += blockDim.x)
     if (s_cg[p] == 2) s_status = 6;
@@ -543,7 +548,7 @@ cudaError_t launch_cg(fvgb_mesh_s* m, int bcset, const double* r, double inner_r
   Work<T>& w = work_of<T>(m);
   SolveArgs<T> a;
   a.N = m->topo.N;
-  a.at_nbr = g.bc[bcset].at_nbr; a.at_coef = g.bc[bcset].at_coef; a.at_diag = g.bc[bcset].at_diag;
+  a.at_nbr = g.bc[bcset].at_nbr; a.at_scoef = g.bc[bcset].at_scoef; a.at_isd = g.bc[bcset].at_isd;
   a.r_in = r;
   a.cx = w.cg_x; a.cr = w.cg_r; a.cp = w.cg_p; a.cq = w.cg_q;
   const PartsDev& pd = m->parts;
