@@ -41,14 +41,15 @@ HELD_OUT_STEPS = 40
 WORKLOAD = ("3D electron drift-diffusion + Poisson, FP64 plain method, on the 6M-cell mesh of the "
             "learned-warm-start workload: unit cube, 100^3 jittered hexes x 6 Kuhn tets (6,000,000 "
             "cells, mesh seed 301), seed at (0.5,0.5,0.9), V = 12.5 kV, Poisson to rel. residual 1e-8 "
-            "each step (FP64 defect correction + FP64 inner CG on the two-point operator reducing its "
-            "residual 5x per outer step, warm start from the previous potential)")
+            "each step (FP64 defect correction + FP64 inner CG on the Jacobi-scaled two-point operator "
+            "reducing its residual 5x per outer step, warm start from the previous potential)")
 
 
 def workload_text(args):
     text = WORKLOAD
     if args.inner > 0:
-        text = text.replace("FP64 inner CG on the two-point operator reducing its residual 5x per outer step",
+        text = text.replace("FP64 inner CG on the Jacobi-scaled two-point operator reducing its residual 5x "
+                            "per outer step",
                             f"{args.inner} multigrid V-cycles per outer step")
     if args.prec == "mixed":
         text = text.replace("FP64 plain method", "mixed precision (FP32 transport and inner solve, "
