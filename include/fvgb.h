@@ -265,7 +265,7 @@ fvgb_status fvgb_poisson_rhs(fvgb_mesh m, int32_t bcset, const double* f_dev, do
 
 typedef struct {
   double rtol;          /* stop when ||b - A phi||_2 <= rtol ||b||_2 (FP64) */
-  double inner_rtol;    /* inner CG reduces its residual by this factor (e.g. 0.1) */
+  double inner_rtol;    /* inner CG reduces its (scaled) residual by this factor (e.g. 0.1) */
   int32_t maxit_inner;  /* per inner CG solve */
   int32_t maxit_outer;  /* outer FP64 refinement steps */
   int32_t prec;         /* inner solve arithmetic: FVGB_FP64 or FVGB_FP32 (mixed) */
@@ -291,7 +291,9 @@ typedef struct {
  * operator A): r = b - A phi, stop when ||r|| <= rtol ||b||; otherwise an inner
  * conjugate-gradient solve of A_T delta = r on the symmetric positive definite
  * two-point part A_T of A (coefficient |S_f|^2 / ((x_R - x_L) . S_f) per face), in
- * opts->prec arithmetic with FP64 dot products, then phi += delta.
+ * opts->prec arithmetic with FP64 dot products, then phi += delta. The CG runs on the
+ * Jacobi-scaled system D^-1/2 A_T D^-1/2 y = D^-1/2 r (D = diag A_T), delta = D^-1/2 y:
+ * diagonally preconditioned CG, with the scaling applied once per inner solve.
  *  f_dev    [n_cell] double (NULL = 0)
  *  phi_dev  [n_cell] double, in: initial guess, out: solution
  *  info     host, may be NULL
